@@ -1,0 +1,154 @@
+/*
+ * cyc_oracle.c -- plain FP64 CPU oracle for the cyclic correlation estimator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call this
+ * file: only the tests, the package's smoke check and the bench's CPU-baseline leg do.
+ * It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (paper Sec. 2, discrete estimators; Sec. 4, Eq. (impl-corr) with
+ * x = y and m >= 0):
+ *
+ *   R_f[a][m] = (1/N_eff) * sum_{n=0}^{N_eff-1} x[n+m] * c_f(x[n]) * exp(-j 2 pi frac(a*(n0+n)))
+ *
+ *   c_CONV(z) = conj(z)   (cyclic autocorrelation, Eq. (ACF-def))
+ *   c_CONJ(z) = z         (conjugate cyclic correlation, Eq. (CCF-def))
+ *   N_eff     = max(0, T - max(lags))  (one common n-range for all lags: no zero padding)
+ *   n0        = absolute index of x[0] (phase origin n = 0 at the first sample pushed)
+ *
+ * frac(a*n) is formed without losing the low bits of a*n: p = a*n rounded, e = fma(a,n,-p)
+ * is the exact rounding error (FMA TwoProduct), so a*n = p + e exactly and
+ * frac(a*n) = (p - floor(p)) + e with one final rounding.  cos/sin come from libm.
+ *
+ * Streaming is not modelled: the streaming estimator over any chunking is, by
+ * definition, this batch estimator applied to the concatenation of all pushed samples.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction is off so that the
+ * x86 and Arm builds round identically).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { CYCO_CONV = 1, CYCO_CONJ = 2 };
+
+/* frac(a * n) in [0, 1), exact up to one rounding (see header). */
+static double frac_an(double a, int64_t n)
+{
+    double dn = (double)n;             /* exact for |n| < 2^53 */
+    double p = a * dn;
+    double e = fma(a, dn, -p);         /* a*dn - p exactly */
+    double f = (p - floor(p)) + e;     /* p - floor(p) is exact */
+    f -= floor(f);
+    if (f >= 1.0) f -= 1.0;
+    return f;
+}
+
+/* One (form, a, m) entry of the estimator; writes re, im of R. */
+static void entry(const double* x, int64_t n_eff, int form, double a, int32_t m,
+                  int64_t n0, double* re, double* im)
+{
+    double sr = 0.0, si = 0.0;
+    for (int64_t n = 0; n < n_eff; ++n) {
+        double xr = x[2 * (n + m)], xi = x[2 * (n + m) + 1];     /* x[n+m]    */
+        double yr = x[2 * n], yi = x[2 * n + 1];                 /* x[n]      */
+        if (form == CYCO_CONV) yi = -yi;                         /* conj(x[n]) */
+        double pr = xr * yr - xi * yi;                           /* lag product */
+        double pi = xr * yi + xi * yr;
+        double f = frac_an(a, n0 + n);
+        double c = cos(2.0 * M_PI * f), s = -sin(2.0 * M_PI * f);   /* exp(-j 2 pi f) */
+        sr += pr * c - pi * s;
+        si += pr * s + pi * c;
+    }
+    *re = sr / (double)n_eff;
+    *im = si / (double)n_eff;
+}
+
+static int max_lag(const int32_t* lags, int nlags, int32_t* M)
+{
+    int32_t mx = 0;
+    for (int i = 0; i < nlags; ++i) {
+        if (lags[i] < 0) return -1;
+        if (lags[i] > mx) mx = lags[i];
+    }
+    *M = mx;
+    return 0;
+}
+
+/*
+ * Full estimate.  x: T interleaved complex FP64 samples.  forms: bitmask CONV=1, CONJ=2.
+ * out: [F][nalphas][nlags][2] with F = number of forms set, CONV first.
+ * Returns 0, -1 on bad arguments, -2 when N_eff == 0 (out untouched).
+ */
+int cyco_estimate(const double* x, int64_t T, const int32_t* lags, int nlags,
+                  const double* alphas, int nalphas, int forms, int64_t n0,
+                  int nthreads, double* out, int64_t* n_eff_out)
+{
+    int32_t M;
+    if (!x || T < 0 || !lags || nlags <= 0 || !alphas || nalphas <= 0 || !out) return -1;
+    if ((forms & 3) == 0 || (forms & ~3)) return -1;
+    if (max_lag(lags, nlags, &M)) return -1;
+    int64_t n_eff = T - M;
+    if (n_eff < 0) n_eff = 0;
+    if (n_eff_out) *n_eff_out = n_eff;
+    if (n_eff == 0) return -2;
+
+    int flist[2], F = 0;
+    if (forms & CYCO_CONV) flist[F++] = CYCO_CONV;
+    if (forms & CYCO_CONJ) flist[F++] = CYCO_CONJ;
+    int64_t total = (int64_t)F * nalphas * nlags;
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int64_t t = 0; t < total; ++t) {
+        int f = (int)(t / ((int64_t)nalphas * nlags));
+        int ia = (int)((t / nlags) % nalphas);
+        int im = (int)(t % nlags);
+        entry(x, n_eff, flist[f], alphas[ia], lags[im], n0, &out[2 * t], &out[2 * t + 1]);
+    }
+    return 0;
+}
+
+/*
+ * Selected entries only (for parity at sizes where the full grid is too slow on a CPU).
+ * form[i] in {1, 2}, alphas[i], lag[i] per entry; M is the max lag of the whole
+ * configuration (it fixes N_eff).  out: [nent][2].
+ */
+int cyco_entries(const double* x, int64_t T, int32_t M, int nent, const int32_t* form,
+                 const double* alphas, const int32_t* lag, int64_t n0, int nthreads,
+                 double* out, int64_t* n_eff_out)
+{
+    if (!x || T < 0 || M < 0 || nent < 0 || !form || !alphas || !lag || !out) return -1;
+    int64_t n_eff = T - M;
+    if (n_eff < 0) n_eff = 0;
+    if (n_eff_out) *n_eff_out = n_eff;
+    if (n_eff == 0) return -2;
+    for (int i = 0; i < nent; ++i)
+        if (lag[i] < 0 || lag[i] > M || (form[i] != CYCO_CONV && form[i] != CYCO_CONJ)) return -1;
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int i = 0; i < nent; ++i)
+        entry(x, n_eff, form[i], alphas[i], lag[i], n0, &out[2 * i], &out[2 * i + 1]);
+    return 0;
+}
+
+/* R^0(0) = (1/N_eff) sum_{n<N_eff} |x[n]|^2, the normaliser of the error metric. */
+double cyco_r00(const double* x, int64_t T, int32_t M)
+{
+    int64_t n_eff = T - M;
+    if (!x || n_eff <= 0) return 0.0;
+    double s = 0.0;
+    for (int64_t n = 0; n < n_eff; ++n) s += x[2 * n] * x[2 * n] + x[2 * n + 1] * x[2 * n + 1];
+    return s / (double)n_eff;
+}
+
+int cyco_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
