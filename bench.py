@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of the streaming cyclic-correlation estimator on one GB300 (or N, one per rank).
+
+Workload (one step): a GMSK stream of 2^26 complex64 samples (BT 0.3, 8 samples/symbol,
+carrier offset 0.05, 10 dB) pushed in 2^16-sample chunks through cyc_push, lags 0..127,
+1024 cycle frequencies -0.5 + k/1024, both forms, FP64 running sums, then cyc_read.
+The input (512 MB) is resident in HBM and larger than L2.
+
+Metric: algorithmic complex MACs per second (one CMAC = one (a, m, n) term per form,
+counted over distinct a mod 1), in GMAC/s; also samples/s.  The tuned projection is
+timed beside the plain FP32 path, each with its error against the FP64 oracle on
+sampled entries, relative to R^0(0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp16|fp32]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cyclic-corr GMAC/s and Msamples/s, tuned vs plain FP32 at <=1e-4 err; p99 lat"
+UNIT = "GMAC/s"
+T_SAMPLES = 1 << 26
+CHUNK = 1 << 16
+NLAGS, NALPHAS, NFORMS = 128, 1024, 2
+FLOPS_PER_CMAC = 8                     # one complex multiply-add
+TC_PASSES = {"bf16x3": 3, "fp16": 1}   # tensor-core products per CMAC
+TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per projection launch from one ncu capture,
+# valid only for the kernel source it was taken on (sha256 prefix of the .cu file).
+TRAFFIC = {}
+
+
+def workload_config(precision):
+    return {
+        "workload": "cfg1 GMSK stream: 2^26 complex64 samples pushed in 2^16-sample chunks, "
+                    "lags 0..127, 1024 cycle freqs -0.5+k/1024, CONV+CONJ, FP64 running sums",
+        "samples_per_step": T_SAMPLES, "chunk": CHUNK, "lags": NLAGS, "cycle_freqs": NALPHAS,
+        "forms": NFORMS, "projection": precision,
+        "l2": "inputs larger than L2 (512 MB stream per step, 129 MB L2)",
+    }
+
+
+def cmac_per_step(T=T_SAMPLES):
+    return (T - (NLAGS - 1)) * NLAGS * NALPHAS * NFORMS
+
+
+def kernel_hash(precision):
+    f = "proj_fp32.cu" if precision == "fp32" else "proj_tc.cu"
+    with open(os.path.join(ROOT, "paper_2405_16911_gb300", "csrc", f), "rb") as fh:
+        return f.split(".")[0] + "@" + hashlib.sha256(fh.read()).hexdigest()[:12]
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            v = [t.strip() for t in line.split(",")]
+            if len(v) < 7:
+                continue
+            try:
+                sm.append(float(v[0]))
+                mx.append(float(v[1]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[3:7]):
+                if flag.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample_rate(x, lags, alphas, target_s=10.0, max_T=1 << 16):
+    """The FP64 oracle on a prefix of the stream with the full grid; GMAC/s."""
+    import oracle
+    M = int(np.max(lags))
+    n = 256
+    while True:
+        t0 = time.perf_counter()
+        oracle.estimate(x[:n + M], lags, alphas)
+        dt = time.perf_counter() - t0
+        if dt * 2 >= target_s or n >= max_T:
+            break
+        n = min(max_T, max(2 * n, int(n * target_s / max(dt, 1e-3) * 0.9)))
+    cmac = n * len(lags) * len(alphas) * NFORMS
+    return cmac / dt / 1e9, n, dt
+
+
+def sampled_error(R, x, lags, alphas, nent=8, seed=3):
+    import oracle
+    rng = np.random.default_rng(seed)
+    f = rng.integers(0, 2, nent)
+    ia = rng.integers(0, len(alphas), nent)
+    im = rng.integers(0, len(lags), nent)
+    M = int(np.max(lags))
+    Ro, _ = oracle.entries(x, M, f + 1, np.asarray(alphas)[ia], np.asarray(lags)[im])
+    return float(np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, M))
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import workloads
+    oracle.build()
+    T_s = 4096
+    w = workloads.config1(T=T_s + NLAGS - 1)
+    x, lags, alphas = w["x"], w["lags"], w["alphas"]
+    for _ in range(args.warmup):
+        oracle.estimate(x, lags, alphas)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.estimate(x, lags, alphas)
+    dt = (time.perf_counter() - t0) / args.steps
+    cmac = T_s * NLAGS * NALPHAS * NFORMS
+    v = cmac / dt / 1e9
+    cores = oracle.max_threads()
+    sample = "first %d committed samples of the config-1 stream, full grid (1024 a x 128 lags x 2 forms)" % T_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config("fp64 oracle"),
+        "msamples_per_s": T_s / dt / 1e6,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+
+def time_device_steps(pkg, x_dev, lags, alphas, precision, steps, warmup, world, profile):
+    import torch
+    out = torch.empty((NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
+    nchunks = x_dev.numel() // (2 * CHUNK)
+    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK) as s:
+        def step():
+            s.reset()
+            for c in range(nchunks):
+                s.push(x_dev[2 * c * CHUNK:2 * (c + 1) * CHUNK])
+            s.read(out)
+        for _ in range(warmup):
+            step()
+        s.profile(profile)
+        s.profile_read()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = ev0.elapsed_time(ev1) / steps
+        proj_ms, proj_launches, kernels = s.profile_read()
+        R = out.cpu().numpy()
+    return ms, R[..., 0] + 1j * R[..., 1], proj_ms, proj_launches, kernels
+
+
+def time_e2e(pkg, x_host_pinned, lags, alphas, precision, steps):
+    """Host buffers through the public API: H2D of every chunk and D2H of the result inside."""
+    nchunks = x_host_pinned.numel() // (2 * CHUNK)
+    res = np.empty((NFORMS, NALPHAS, NLAGS), dtype=np.complex128)
+    base = x_host_pinned.data_ptr()
+    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK) as s:
+        def step():
+            s.reset()
+            for c in range(nchunks):
+                s.push(base + c * CHUNK * 8, CHUNK, 0)
+            s.read(res)
+        step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        dt = (time.perf_counter() - t0) / steps
+    return dt, x_host_pinned.numel() * 4, res.nbytes
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2405_16911_gb300 as pkg
+    from synth import workloads
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    pkg.load()
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None else None
+    precision = args.precision
+    try:
+        pkg.Stream([0], [0.0], pkg.CYC_BOTH, precision=precision).close()
+    except pkg.CycError as e:
+        if e.code != pkg.CYC_ENOTSUP:
+            raise
+        precision = "fp32"
+
+    w = workloads.config1(replica=rank)
+    x, lags, alphas = w["x"], w["lags"], w["alphas"]
+    x_dev = torch.from_numpy(x.view(np.float32)).cuda()
+
+    sampler = ClockSampler(uuid)
+    ms, R, proj_ms, proj_launches, kernels = time_device_steps(
+        pkg, x_dev, lags, alphas, precision, args.steps, args.warmup, world, True)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms, world)
+    cmac = cmac_per_step() * world
+    value = cmac / (ms * 1e-3) / 1e9
+
+    # roofline of the projection kernel (the dominant kernel of the step)
+    nsm = props.multi_processor_count
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    cmac_launch = cmac_per_step() * args.steps / max(proj_launches, 1)
+    avg_launch_s = proj_ms * 1e-3 / max(proj_launches, 1)
+    if precision == "fp32":
+        clk = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = nsm * 128 * 2 * clk * 1e6 / 1e12
+        achieved = cmac_launch * FLOPS_PER_CMAC / avg_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA pipes: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (nsm, clk)}
+    else:
+        passes = TC_PASSES[precision]
+        if "bf16_tflops_sustained" in peaks:
+            peak, src = float(peaks["bf16_tflops_sustained"]), "measured bf16 sustained (MEASURED_PEAKS.json)"
+        else:
+            peak, src = 1700.0, "fallback bf16 sustained"
+        achieved = cmac_launch * FLOPS_PER_CMAC * passes / avg_launch_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_source": src,
+                "flops_per_cmac": FLOPS_PER_CMAC * passes}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = TRAFFIC.get(kernel_hash(precision))
+    roof["kernel_ms_avg"] = avg_launch_s * 1e3
+    roof["share_of_step"] = proj_ms / args.steps / ms
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "fp16": "f16"}[precision],
+        "data": "synthetic", "config": workload_config(precision),
+        "msamples_per_s": T_SAMPLES * world / (ms * 1e-3) / 1e6,
+        "precision": {"fp32": "fp32 CUDA-core projection", "bf16x3": "bf16 hi/lo split, 3 products, fp32 accumulate",
+                      "fp16": "fp16 single pass, fp32 accumulate"}[precision] + "; fp64 running sums",
+        "gpu_launches": kernels, "roofline": roof, "clocks": clocks,
+    }
+    if rank == 0:
+        line["err_rel_r00"] = sampled_error(R, x, lags, alphas)
+        line["err_tol"] = TOL[precision]
+
+    if rank == 0 and not args.no_e2e:
+        xh = torch.from_numpy(x.view(np.float32)).pin_memory()
+        dt, hb, db = time_e2e(pkg, xh, lags, alphas, precision, max(1, min(args.steps, 3)))
+        line["e2e"] = {"value": cmac_per_step() / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": hb,
+                       "d2h_bytes_per_step": db, "ms_per_step": dt * 1e3,
+                       "path": "cyc_push from page-locked host memory, cyc_read into host memory"}
+        del xh
+    if rank == 0 and precision != "fp32" and not args.no_plain:
+        k = max(1, min(args.steps, 2))
+        ms32, R32, pms, pl, _ = time_device_steps(pkg, x_dev, lags, alphas, "fp32", k, 1, 1, True)
+        line["plain_fp32"] = {"value": cmac_per_step() / (ms32 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms32,
+                              "steps": k, "err_rel_r00": sampled_error(R32, x, lags, alphas)}
+        line["speedup_vs_plain_fp32"] = value / world / line["plain_fp32"]["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                                "sample": "first %d committed samples of the stream, full grid "
+                                          "(1024 a x 128 lags x 2 forms), %.1f s" % (n, dt)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16x3", "fp16", "fp32"], default="bf16x3")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * cyc.h -- C ABI of libcyc, a streaming estimator of second-order cyclic statistics on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * What a stream estimates (arXiv 2405.16911, Sec. 2 discrete estimators and Sec. 4
+ * Eq. (impl-corr) with x = y and lags m >= 0), over every sample pushed so far:
+ *
+ *   R_CONV[a][m] = (1/N_eff) sum_{n=0}^{N_eff-1} x[n+m] conj(x[n]) exp(-j 2 pi a (n0+n))
+ *   R_CONJ[a][m] = (1/N_eff) sum_{n=0}^{N_eff-1} x[n+m]      x[n]  exp(-j 2 pi a (n0+n))
+ *
+ *   N_eff = max(0, T - M), T = samples pushed, M = max(lags), n0 = start index.
+ *
+ * CONV is the cyclic autocorrelation (Eq. (ACF-def)), CONJ the conjugate cyclic
+ * correlation (Eq. (CCF-def)); the paper's block attribute `conj` selects between
+ * them (Sec. 4), here a bitmask selects one or both.  a is a normalised cycle frequency
+ * in cycles/sample (Sec. 2: alpha~ = alpha / f_s); any finite value is accepted and a
+ * and a + 1 give the same result.  All lags share one n-range, so the result does not
+ * depend on how the samples are cut into pushes: the last M samples of every push wait
+ * for the next one (the paper's input buffer, Sec. 4, holds samples for the same reason).
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success, a negative CYC_E* code on failure; cyc_last_error() then
+ *    gives a thread-local message.  Nothing is half-applied on CYC_EINVAL.
+ *  - A handle is not thread-safe.  Distinct handles may be used from distinct threads.
+ *  - Samples are interleaved complex64: float re, float im (8 bytes per sample).
+ *  - Results are interleaved complex FP64, layout [form][alpha index][lag index][re, im],
+ *    forms in the order CONV then CONJ (only those selected), alphas and lags in the
+ *    order given at creation (duplicates allowed).
+ */
+#ifndef CYC_H
+#define CYC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CYC_API __attribute__((visibility("default")))
+#else
+#define CYC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CYC_OK         0
+#define CYC_EINVAL    (-1)   /* bad argument: empty list, negative lag, non-finite a, n < 0 ... */
+#define CYC_ENOMEM    (-2)   /* device or host allocation failed */
+#define CYC_ECUDA     (-3)   /* a CUDA runtime call failed (message names it) */
+#define CYC_EAGAIN    (-4)   /* server: stream not admitted (memory budget / slots), retry later */
+#define CYC_ETIMEDOUT (-5)   /* a bounded device wait gave up */
+#define CYC_ENODATA   (-6)   /* N_eff == 0: nothing to read; the output is left untouched */
+#define CYC_ENOTSUP   (-7)   /* valid request that this build does not implement */
+
+/* ---- forms (bitmask) ---- */
+#define CYC_CONV 1           /* x[n+m] conj(x[n]) */
+#define CYC_CONJ 2           /* x[n+m] x[n]       */
+#define CYC_BOTH 3
+
+/* ---- projection precision (the a-projection, Sec. 4 Set mode; sums are always FP64) ---- */
+#define CYC_P_FP32   0       /* FP32 CUDA-core complex GEMM, FP32 accumulate */
+#define CYC_P_FP16   1       /* tensor cores, FP16 operands, one pass, FP32 accumulate */
+#define CYC_P_BF16X3 2       /* tensor cores, BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+
+typedef struct cyc_stream cyc_stream;   /* opaque, owned by the library */
+
+/*
+ * Creation parameters.  Arrays are copied; the caller keeps ownership.
+ *   lags[nlags]       lags m >= 0 (Sec. 4 Set mode lists lags; negative lags -> CYC_EINVAL)
+ *   alphas[nalphas]   normalised cycle frequencies (finite doubles)
+ *   conj_flag         CYC_CONV, CYC_CONJ or CYC_BOTH
+ *   precision         CYC_P_*
+ *   n0                absolute index of the first sample (phase origin, any int64)
+ *   max_chunk         largest push handled in one device pass; longer pushes are cut.
+ *                     0 selects 1 << 20.  Device staging memory is 2 * (M + max_chunk) * 8 B.
+ *   cuda_stream       cudaStream_t the stream's work is ordered on; NULL = the legacy
+ *                     default stream of `device`
+ *   device            CUDA device ordinal
+ */
+typedef struct cyc_params {
+    const int32_t* lags;
+    int32_t        nlags;
+    const double*  alphas;
+    int32_t        nalphas;
+    int32_t        conj_flag;
+    int32_t        precision;
+    int64_t        n0;
+    int64_t        max_chunk;
+    void*          cuda_stream;
+    int32_t        device;
+} cyc_params;
+
+/* cyc_create: FP32 projection, n0 = 0, default stream of device 0.  *out receives the handle. */
+CYC_API int cyc_create(const int32_t* lags, int nlags, const double* alphas, int nalphas,
+               int conj_flag, cyc_stream** out);
+
+/* cyc_create_ex: every parameter explicit (see cyc_params). */
+CYC_API int cyc_create_ex(const cyc_params* p, cyc_stream** out);
+
+/*
+ * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
+ * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
+ * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read
+ * in stream order -- keep it unchanged until the next cyc_read / cyc_sync.
+ * on_device == 0: host memory; pageable memory is consumed before return, page-locked
+ * memory is read in stream order like device memory.  nsamples == 0 is a no-op.
+ */
+CYC_API int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device);
+
+/*
+ * cyc_read: wait for the stream's work, then write R = sums / N_eff (layout above) to
+ * `out`, which may be host or device memory of at least F * nalphas * nlags * 16 bytes.
+ * *n_eff (optional) receives N_eff.  CYC_ENODATA when N_eff == 0 (out untouched).
+ */
+CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);
+
+/* cyc_sync: wait until all work queued by this stream has finished. */
+CYC_API int cyc_sync(cyc_stream* s);
+
+/* cyc_reset: drop all samples and sums (parameters kept). */
+CYC_API int cyc_reset(cyc_stream* s);
+
+/* cyc_destroy: free the handle and its device memory (NULL is a no-op). */
+CYC_API int cyc_destroy(cyc_stream* s);
+
+/*
+ * cyc_save / cyc_load: the whole stream state (sample count, N_eff, the carried tail of
+ * up to M samples, the FP64 sums) as an opaque host blob.  cyc_save with buf == NULL
+ * stores the needed size in *len.  cyc_load restores into a handle created with the
+ * same lags, alphas, forms and n0 (CYC_EINVAL otherwise); pushing after a load gives
+ * the same result as never having stopped.
+ */
+CYC_API int cyc_save(cyc_stream* s, void* buf, size_t* len);
+CYC_API int cyc_load(cyc_stream* s, const void* buf, size_t len);
+
+/*
+ * cyc_info: sizes of a handle.  Any pointer may be NULL.
+ *   forms: number of forms F; nunique: distinct a mod 1 actually computed;
+ *   total: samples pushed; n_eff: committed terms.
+ */
+CYC_API int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, int64_t* n_eff);
+
+/*
+ * cyc_profile: enable (1) or disable (0) timing of this stream's projection kernel with
+ * CUDA events recorded on its CUDA stream around every launch.
+ * cyc_profile_read: totals since the previous cyc_profile_read (waits for the stream):
+ *   proj_ms        summed device time of the projection launches (0 when disabled)
+ *   proj_launches  projection launches
+ *   kernels        all kernel launches made by this stream (projection, sum update, read)
+ * Any output pointer may be NULL.
+ */
+CYC_API int cyc_profile(cyc_stream* s, int enable);
+CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels);
+
+/* Error text for a status code, and the calling thread's last detailed message. */
+CYC_API const char* cyc_strerror(int code);
+CYC_API const char* cyc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CYC_H */

@@ -1,0 +1,11 @@
+"""GB300-native streaming estimator of second-order cyclic statistics (arXiv 2405.16911).
+
+The compute path is libcyc.so (CUDA for sm_103a, C ABI in include/cyc.h); this package is
+its thin binding.  There is no fallback: without the built library or a GPU, calls raise.
+"""
+from ._cyc import *  # noqa: F401,F403
+from ._cyc import (CycError, Stream, load, declared_functions, LIB_PATH, HEADER,  # noqa: F401
+                   cyc_create, cyc_create_ex, cyc_push, cyc_read, cyc_sync, cyc_reset, cyc_destroy,
+                   cyc_save, cyc_load, cyc_info, cyc_profile, cyc_profile_read, cyc_strerror,
+                   cyc_last_error)
+from .build import build  # noqa: F401

@@ -1,0 +1,281 @@
+"""ctypes binding of libcyc (include/cyc.h): argument marshalling only.
+
+Every entry point of the C ABI has a Python function of the same name.  Chunks and
+outputs may be torch tensors (device or host), numpy arrays, or raw integer pointers.
+All arithmetic happens in the CUDA library; if it is missing or no GPU is present,
+``load()`` raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcyc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cyc.h")
+
+CYC_OK, CYC_EINVAL, CYC_ENOMEM, CYC_ECUDA, CYC_EAGAIN, CYC_ETIMEDOUT, CYC_ENODATA, CYC_ENOTSUP = \
+    0, -1, -2, -3, -4, -5, -6, -7
+CYC_CONV, CYC_CONJ, CYC_BOTH = 1, 2, 3
+CYC_P_FP32, CYC_P_FP16, CYC_P_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": CYC_P_FP32, "fp16": CYC_P_FP16, "bf16x3": CYC_P_BF16X3}
+
+
+class CycError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_strerror_py(code), code, msg))
+        self.code = code
+
+
+def _strerror_py(code):
+    return {0: "success", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
+            -4: "not admitted", -5: "timed out", -6: "no data", -7: "not supported"}.get(code, "error")
+
+
+class cyc_params(ctypes.Structure):
+    _fields_ = [("lags", ctypes.c_void_p), ("nlags", ctypes.c_int32),
+                ("alphas", ctypes.c_void_p), ("nalphas", ctypes.c_int32),
+                ("conj_flag", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n0", ctypes.c_int64), ("max_chunk", ctypes.c_int64),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the entry points declared in include/cyc.h."""
+    with open(header) as f:
+        return re.findall(r"CYC_API\s+[\w\s\*]+?\b(cyc_\w+)\s*\(", f.read())
+
+
+def load(path: str = LIB_PATH):
+    """Load libcyc.so (built in-tree by ``paper_2405_16911_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libcyc.so is not built (%s); run paper_2405_16911_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I32, I64, I = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "cyc_create": ([P, I, P, I, I, P], I),
+        "cyc_create_ex": ([P, P], I),
+        "cyc_push": ([P, P, I64, I], I),
+        "cyc_read": ([P, P, P], I),
+        "cyc_sync": ([P], I),
+        "cyc_reset": ([P], I),
+        "cyc_destroy": ([P], I),
+        "cyc_save": ([P, P, P], I),
+        "cyc_load": ([P, P, ctypes.c_size_t], I),
+        "cyc_info": ([P, P, P, P, P], I),
+        "cyc_profile": ([P, I], I),
+        "cyc_profile_read": ([P, P, P, P], I),
+        "cyc_strerror": ([I], ctypes.c_char_p),
+        "cyc_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CycError(rc, _lib.cyc_last_error().decode())
+    return rc
+
+
+def _ptr_info(obj):
+    """(address, nbytes, on_device, keepalive) for a torch tensor, numpy array or int."""
+    if isinstance(obj, int):
+        return obj, None, None, None
+    if isinstance(obj, np.ndarray):
+        if not obj.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return obj.ctypes.data, obj.nbytes, 0, obj
+    mod = type(obj).__module__
+    if mod.startswith("torch"):
+        if not obj.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return obj.data_ptr(), obj.numel() * obj.element_size(), 1 if obj.is_cuda else 0, obj
+    raise TypeError("expected a torch tensor, numpy array or integer address, got %r" % type(obj))
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def _nforms(conj_flag: int) -> int:
+    return (1 if conj_flag & CYC_CONV else 0) + (1 if conj_flag & CYC_CONJ else 0)
+
+
+def cyc_create(lags, alphas, conj_flag: int = CYC_BOTH) -> int:
+    lib = load()
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    h = ctypes.c_void_p()
+    _check(lib.cyc_create(lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, conj_flag, ctypes.byref(h)))
+    _shapes[h.value] = (_nforms(conj_flag), alphas.size, lags.size)
+    return h.value
+
+
+def cyc_create_ex(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
+                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0) -> int:
+    lib = load()
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    p = cyc_params(lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, conj_flag, precision,
+                   int(n0), int(max_chunk), cuda_stream or None, device)
+    h = ctypes.c_void_p()
+    _check(lib.cyc_create_ex(ctypes.byref(p), ctypes.byref(h)))
+    _shapes[h.value] = (_nforms(conj_flag), alphas.size, lags.size)
+    return h.value
+
+
+def cyc_push(h: int, chunk, nsamples: int | None = None, on_device: int | None = None) -> None:
+    addr, nbytes, dev, _keep = _ptr_info(chunk)
+    if nsamples is None:
+        if nbytes is None:
+            raise ValueError("nsamples is required with a raw address")
+        nsamples = nbytes // 8
+    if on_device is None:
+        if dev is None:
+            raise ValueError("on_device is required with a raw address")
+        on_device = dev
+    _check(load().cyc_push(h, addr, int(nsamples), int(on_device)))
+
+
+def cyc_read(h: int, out=None):
+    """Write R into `out` (torch/numpy, complex128 or float64 view) or return a new
+    complex128 numpy array [F][A][L].  Returns (R, n_eff)."""
+    lib = load()
+    F, A, L = cyc_shape(h)
+    neff = ctypes.c_int64(0)
+    if out is None:
+        out = np.empty((F, A, L), dtype=np.complex128)
+    addr, nbytes, _dev, _keep = _ptr_info(out)
+    if nbytes is not None and nbytes < F * A * L * 16:
+        raise ValueError("output buffer too small")
+    _check(lib.cyc_read(h, addr, ctypes.byref(neff)))
+    return out, int(neff.value)
+
+
+def cyc_sync(h: int) -> None:
+    _check(load().cyc_sync(h))
+
+
+def cyc_reset(h: int) -> None:
+    _check(load().cyc_reset(h))
+
+
+def cyc_destroy(h: int) -> None:
+    if h:
+        _shapes.pop(h, None)
+        _check(load().cyc_destroy(h))
+
+
+def cyc_save(h: int) -> bytes:
+    lib = load()
+    n = ctypes.c_size_t(0)
+    _check(lib.cyc_save(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.cyc_save(h, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def cyc_load(h: int, blob: bytes) -> None:
+    _check(load().cyc_load(h, blob, len(blob)))
+
+
+def cyc_info(h: int):
+    """(forms, unique cycle frequencies, samples pushed, N_eff)."""
+    f, u = ctypes.c_int(0), ctypes.c_int(0)
+    t, n = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().cyc_info(h, ctypes.byref(f), ctypes.byref(u), ctypes.byref(t), ctypes.byref(n)))
+    return f.value, u.value, t.value, n.value
+
+
+def cyc_profile(h: int, enable: bool = True) -> None:
+    _check(load().cyc_profile(h, int(bool(enable))))
+
+
+def cyc_profile_read(h: int):
+    """(projection ms, projection launches, all kernel launches) since the last call."""
+    ms, pl, kl = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().cyc_profile_read(h, ctypes.byref(ms), ctypes.byref(pl), ctypes.byref(kl)))
+    return ms.value, pl.value, kl.value
+
+
+def cyc_strerror(code: int) -> str:
+    return load().cyc_strerror(code).decode()
+
+
+def cyc_last_error() -> str:
+    return load().cyc_last_error().decode()
+
+
+# shapes are tracked on the Python side for cyc_read's default output
+_shapes: dict[int, tuple[int, int, int]] = {}
+
+
+def cyc_shape(h: int):
+    return _shapes[h]
+
+
+class Stream:
+    """Owning wrapper: ``with Stream(lags, alphas, ...) as s: s.push(x); R, n = s.read()``."""
+
+    def __init__(self, lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
+                 max_chunk: int = 0, cuda_stream: int = 0, device: int = 0):
+        self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device)
+        self.shape = _shapes[self.h]
+
+    def push(self, chunk, nsamples=None, on_device=None):
+        cyc_push(self.h, chunk, nsamples, on_device)
+
+    def read(self, out=None):
+        return cyc_read(self.h, out)
+
+    def sync(self):
+        cyc_sync(self.h)
+
+    def reset(self):
+        cyc_reset(self.h)
+
+    def save(self) -> bytes:
+        return cyc_save(self.h)
+
+    def load(self, blob: bytes):
+        cyc_load(self.h, blob)
+
+    def info(self):
+        return cyc_info(self.h)
+
+    def profile(self, enable: bool = True):
+        cyc_profile(self.h, enable)
+
+    def profile_read(self):
+        return cyc_profile_read(self.h)
+
+    def close(self):
+        if self.h:
+            cyc_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

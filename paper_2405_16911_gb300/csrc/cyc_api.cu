@@ -1,0 +1,546 @@
+// cyc_api.cu -- host side of libcyc: stream state, ingest with the carried tail, the
+// projection passes, FP64 running sums, read-out, save/load.  Declared in include/cyc.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+
+#include "cyc_impl.h"
+
+using namespace cyc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? CYC_ENOMEM : CYC_ECUDA,         \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Makes the handle's device current for the duration of an entry point.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int64_t kDefaultChunk = 1 << 20;
+constexpr int64_t kMaxChunk = 1ll << 28;
+constexpr int32_t kMaxLag = 1 << 20;
+constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
+constexpr uint32_t kBlobVersion = 1;
+
+// a (cycles/sample) -> round(frac(a) * 2^64) mod 2^64.  frac(a) = a - floor(a) is exact
+// for every double, and scaling by 2^64 is exact; only the final rounding to an integer
+// can move the value, by at most 2^-65 cycles/sample.
+uint64_t alpha_to_phi(double a)
+{
+    double fr = a - floor(a);
+    double y = ldexp(fr, 64);
+    double r = nearbyint(y);
+    if (r >= 18446744073709551616.0) return 0;
+    return (uint64_t)r;
+}
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+struct BlobHeader {
+    char     magic[8];
+    uint32_t version;
+    int32_t  F, L, A, Au;
+    int32_t  conj_flag;
+    int64_t  n0, T, n_eff, held;
+    uint64_t fingerprint;
+};
+
+}  // namespace
+
+struct cyc_stream {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int num_sms = 1;
+    int precision = CYC_P_FP32;
+    int conj_flag = 0;
+    int F = 0;
+    int forms[2] = {0, 0};
+    std::vector<int32_t> lags;
+    int L = 0;
+    int32_t M = 0;
+    std::vector<double> alphas;
+    int A = 0;
+    std::vector<uint64_t> phi_u;
+    std::vector<int32_t> amap;
+    int Au = 0;
+    int ncols = 0;
+    int64_t n0 = 0, T = 0, n_eff = 0, held = 0, max_chunk = kDefaultChunk;
+    uint64_t fingerprint = 0;
+    // device state
+    float2* stage[2] = {nullptr, nullptr};
+    int cur = 0;
+    double2* sums = nullptr;
+    uint64_t* d_phi = nullptr;
+    int32_t* d_amap = nullptr;
+    int32_t* d_col_lag = nullptr;
+    int8_t* d_col_conj = nullptr;
+    float2* part = nullptr;
+    size_t part_elems = 0;
+    double2* d_out = nullptr;
+    // profiling
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0, kernel_launches = 0;
+
+    void free_events()
+    {
+        for (auto& e : ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        for (auto& e : ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        ev_pending.clear();
+        ev_free.clear();
+    }
+
+    void free_all()
+    {
+        free_events();
+        void* ps[] = {stage[0], stage[1], sums, d_phi, d_amap, d_col_lag, d_col_conj, part, d_out};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+        stage[0] = stage[1] = nullptr;
+        sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
+        d_col_conj = nullptr; part = nullptr; d_out = nullptr;
+    }
+};
+
+namespace {
+
+int check_params(const cyc_params* p)
+{
+    if (!p) return fail(CYC_EINVAL, "cyc_create_ex: params is NULL");
+    if (!p->lags || p->nlags <= 0) return fail(CYC_EINVAL, "lag list is empty");
+    if (!p->alphas || p->nalphas <= 0) return fail(CYC_EINVAL, "cycle-frequency list is empty");
+    for (int i = 0; i < p->nlags; ++i) {
+        if (p->lags[i] < 0) return fail(CYC_EINVAL, "lag %d is negative (%d); lags must be >= 0", i, p->lags[i]);
+        if (p->lags[i] > kMaxLag) return fail(CYC_EINVAL, "lag %d exceeds %d", p->lags[i], kMaxLag);
+    }
+    for (int i = 0; i < p->nalphas; ++i)
+        if (!isfinite(p->alphas[i])) return fail(CYC_EINVAL, "cycle frequency %d is not finite", i);
+    if (p->conj_flag < 1 || p->conj_flag > 3) return fail(CYC_EINVAL, "conj_flag must be 1, 2 or 3");
+    if (p->precision < CYC_P_FP32 || p->precision > CYC_P_BF16X3)
+        return fail(CYC_EINVAL, "unknown precision %d", p->precision);
+    if (p->max_chunk < 0 || p->max_chunk > kMaxChunk)
+        return fail(CYC_EINVAL, "max_chunk must be in [0, 2^28]");
+    if ((int64_t)p->nlags * 2 > (1 << 24) || (int64_t)p->nalphas > (1 << 24))
+        return fail(CYC_EINVAL, "too many lags or cycle frequencies");
+    return CYC_OK;
+}
+
+int alloc_state(cyc_stream* s)
+{
+    size_t stage_n = (size_t)(s->M + s->max_chunk + kStagePad);
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaMalloc(&s->stage[b], stage_n * sizeof(float2)));
+        CK(cudaMemset(s->stage[b], 0, stage_n * sizeof(float2)));
+    }
+    CK(cudaMalloc(&s->sums, (size_t)s->Au * s->ncols * sizeof(double2)));
+    CK(cudaMemset(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2)));
+    CK(cudaMalloc(&s->d_phi, s->Au * sizeof(uint64_t)));
+    CK(cudaMemcpy(s->d_phi, s->phi_u.data(), s->Au * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&s->d_amap, s->A * sizeof(int32_t)));
+    CK(cudaMemcpy(s->d_amap, s->amap.data(), s->A * sizeof(int32_t), cudaMemcpyHostToDevice));
+    std::vector<int32_t> cl(s->ncols);
+    std::vector<int8_t> cc(s->ncols);
+    for (int f = 0; f < s->F; ++f)
+        for (int l = 0; l < s->L; ++l) {
+            cl[f * s->L + l] = s->lags[l];
+            cc[f * s->L + l] = s->forms[f] == CYC_CONJ ? 1 : 0;
+        }
+    CK(cudaMalloc(&s->d_col_lag, s->ncols * sizeof(int32_t)));
+    CK(cudaMemcpy(s->d_col_lag, cl.data(), s->ncols * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&s->d_col_conj, s->ncols * sizeof(int8_t)));
+    CK(cudaMemcpy(s->d_col_conj, cc.data(), s->ncols * sizeof(int8_t), cudaMemcpyHostToDevice));
+    s->part_elems = s->precision == CYC_P_FP32 ? fp32_max_partials(s->Au, s->ncols, s->num_sms)
+                                               : tc_max_partials(s->Au, s->ncols, s->num_sms);
+    CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
+    CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
+    return CYC_OK;
+}
+
+// One device pass over view = stage[cur][0 .. held + c): nc committed terms.
+int project(cyc_stream* s, int64_t nc)
+{
+    ProjArgs a;
+    a.x = s->stage[s->cur];
+    a.nc = nc;
+    a.nbase = (uint64_t)s->n0 + (uint64_t)s->n_eff;
+    a.phi = s->d_phi;
+    a.Au = s->Au;
+    a.col_lag = s->d_col_lag;
+    a.col_conj = s->d_col_conj;
+    a.ncols = s->ncols;
+    a.part = s->part;
+    ProjPlan pl = s->precision == CYC_P_FP32 ? fp32_plan(s->Au, s->ncols, nc, s->num_sms)
+                                             : tc_plan(s->Au, s->ncols, nc, s->num_sms);
+    a.nsplit = pl.nsplit;
+    a.split_len = pl.split_len;
+    if ((size_t)pl.nsplit * s->Au * s->ncols > s->part_elems)
+        return fail(CYC_ECUDA, "internal: partial buffer too small (%d splits)", pl.nsplit);
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (s->prof) {
+        if (!s->ev_free.empty()) {
+            ev = s->ev_free.back();
+            s->ev_free.pop_back();
+        } else {
+            CK(cudaEventCreate(&ev.first));
+            CK(cudaEventCreate(&ev.second));
+        }
+        CK(cudaEventRecord(ev.first, s->st));
+    }
+    CK(s->precision == CYC_P_FP32 ? fp32_launch(a, s->st) : tc_launch(a, s->precision, s->st));
+    if (s->prof) {
+        CK(cudaEventRecord(ev.second, s->st));
+        s->ev_pending.push_back(ev);
+    }
+    s->prof_launches++;
+    CK(reduce_partials(s->part, pl.nsplit, s->Au * s->ncols, s->sums, s->st));
+    s->kernel_launches += 2;
+    return CYC_OK;
+}
+
+bool is_device_ptr(const void* p, int device, bool* wrong_device)
+{
+    cudaPointerAttributes at;
+    *wrong_device = false;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        if (at.type == cudaMemoryTypeDevice && at.device != device) *wrong_device = true;
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cyc_create(const int32_t* lags, int nlags, const double* alphas, int nalphas, int conj_flag,
+               cyc_stream** out)
+{
+    cyc_params p;
+    memset(&p, 0, sizeof p);
+    p.lags = lags;
+    p.nlags = nlags;
+    p.alphas = alphas;
+    p.nalphas = nalphas;
+    p.conj_flag = conj_flag;
+    p.precision = CYC_P_FP32;
+    return cyc_create_ex(&p, out);
+}
+
+int cyc_create_ex(const cyc_params* p, cyc_stream** out)
+{
+    if (!out) return fail(CYC_EINVAL, "cyc_create_ex: out is NULL");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return fail(CYC_ECUDA, "no CUDA device is available");
+    }
+    if (p->device < 0 || p->device >= ndev) return fail(CYC_EINVAL, "device %d out of range", p->device);
+
+    cyc_stream* s = new (std::nothrow) cyc_stream();
+    if (!s) return fail(CYC_ENOMEM, "host allocation failed");
+    s->device = p->device;
+    s->st = (cudaStream_t)p->cuda_stream;
+    s->precision = p->precision;
+    s->conj_flag = p->conj_flag;
+    if (p->conj_flag & CYC_CONV) s->forms[s->F++] = CYC_CONV;
+    if (p->conj_flag & CYC_CONJ) s->forms[s->F++] = CYC_CONJ;
+    s->lags.assign(p->lags, p->lags + p->nlags);
+    s->L = p->nlags;
+    for (int32_t m : s->lags) s->M = m > s->M ? m : s->M;
+    s->alphas.assign(p->alphas, p->alphas + p->nalphas);
+    s->A = p->nalphas;
+    std::map<uint64_t, int> uniq;
+    s->amap.resize(s->A);
+    for (int i = 0; i < s->A; ++i) {
+        uint64_t ph = alpha_to_phi(s->alphas[i]);
+        auto it = uniq.find(ph);
+        if (it == uniq.end()) {
+            it = uniq.emplace(ph, (int)s->phi_u.size()).first;
+            s->phi_u.push_back(ph);
+        }
+        s->amap[i] = it->second;
+    }
+    s->Au = (int)s->phi_u.size();
+    s->ncols = s->F * s->L;
+    s->n0 = p->n0;
+    s->max_chunk = p->max_chunk > 0 ? p->max_chunk : kDefaultChunk;
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, s->lags.data(), s->lags.size() * sizeof(int32_t));
+    h = fnv1a(h, s->phi_u.data(), s->phi_u.size() * sizeof(uint64_t));
+    h = fnv1a(h, s->amap.data(), s->amap.size() * sizeof(int32_t));
+    h = fnv1a(h, &s->conj_flag, sizeof s->conj_flag);
+    h = fnv1a(h, &s->n0, sizeof s->n0);
+    s->fingerprint = h;
+
+    if (s->precision != CYC_P_FP32 && !tc_supported(s->ncols)) {
+        delete s;
+        return fail(CYC_ENOTSUP, "tensor-core projection does not support %d columns", p->nlags);
+    }
+    DeviceGuard g(s->device);
+    if (!g.ok) { delete s; return fail(CYC_ECUDA, "cudaSetDevice(%d) failed", p->device); }
+    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+        delete s;
+        return fail(CYC_ECUDA, "cannot query the SM count");
+    }
+    rc = alloc_state(s);
+    if (rc) {
+        s->free_all();
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return CYC_OK;
+}
+
+int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_push: handle is NULL");
+    if (nsamples < 0) return fail(CYC_EINVAL, "cyc_push: nsamples < 0");
+    if (nsamples == 0) return CYC_OK;
+    if (!chunk) return fail(CYC_EINVAL, "cyc_push: chunk is NULL");
+    DeviceGuard g(s->device);
+    if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
+    if (on_device) {
+        bool wrong = false;
+        if (!is_device_ptr(chunk, s->device, &wrong) || wrong)
+            return fail(CYC_EINVAL, "cyc_push: on_device set but chunk is not memory of device %d", s->device);
+    }
+    const float2* src = (const float2*)chunk;
+    int64_t left = nsamples;
+    while (left > 0) {
+        int64_t c = left < s->max_chunk ? left : s->max_chunk;
+        float2* view = s->stage[s->cur];
+        // a1: the view is [carried tail (held samples) | new samples]
+        CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, s->st));
+        int64_t nview = s->held + c;
+        int64_t nc = nview - s->M;
+        if (nc > 0) {
+            int rc = project(s, nc);
+            if (rc) return rc;
+        } else {
+            nc = 0;
+        }
+        s->n_eff += nc;
+        s->T += c;
+        int64_t keep = s->T < s->M ? s->T : s->M;
+        // the last `keep` samples of the view become the next view's head
+        if (keep > 0)
+            CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
+                               cudaMemcpyDeviceToDevice, s->st));
+        s->cur ^= 1;
+        s->held = keep;
+        src += c;
+        left -= c;
+    }
+    return CYC_OK;
+}
+
+int cyc_sync(cyc_stream* s)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_sync: handle is NULL");
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->st));
+    return CYC_OK;
+}
+
+int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_read: handle is NULL");
+    if (n_eff) *n_eff = s->n_eff;
+    if (s->n_eff == 0) return fail(CYC_ENODATA, "cyc_read: N_eff is 0 (fewer than max(lags) + 1 samples)");
+    if (!out) return fail(CYC_EINVAL, "cyc_read: out is NULL");
+    DeviceGuard g(s->device);
+    bool wrong = false;
+    bool dev = is_device_ptr(out, s->device, &wrong);
+    if (wrong) return fail(CYC_EINVAL, "cyc_read: out is memory of another device");
+    double2* dst = dev ? (double2*)out : s->d_out;
+    CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st));
+    s->kernel_launches++;
+    if (!dev)
+        CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return CYC_OK;
+}
+
+int cyc_reset(cyc_stream* s)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_reset: handle is NULL");
+    DeviceGuard g(s->device);
+    CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->T = s->n_eff = s->held = 0;
+    return CYC_OK;
+}
+
+int cyc_destroy(cyc_stream* s)
+{
+    if (!s) return CYC_OK;
+    {
+        DeviceGuard g(s->device);
+        cudaStreamSynchronize(s->st);
+        s->free_all();
+    }
+    delete s;
+    return CYC_OK;
+}
+
+int cyc_save(cyc_stream* s, void* buf, size_t* len)
+{
+    if (!s || !len) return fail(CYC_EINVAL, "cyc_save: NULL argument");
+    size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
+    size_t need = sizeof(BlobHeader) + (size_t)s->held * sizeof(float2) + sums_b;
+    if (!buf) { *len = need; return CYC_OK; }
+    if (*len < need) { *len = need; return fail(CYC_EINVAL, "cyc_save: buffer too small (%zu < %zu)", *len, need); }
+    DeviceGuard g(s->device);
+    BlobHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "CYCSTAT1", 8);
+    h.version = kBlobVersion;
+    h.F = s->F; h.L = s->L; h.A = s->A; h.Au = s->Au;
+    h.conj_flag = s->conj_flag;
+    h.n0 = s->n0; h.T = s->T; h.n_eff = s->n_eff; h.held = s->held;
+    h.fingerprint = s->fingerprint;
+    unsigned char* b = (unsigned char*)buf;
+    memcpy(b, &h, sizeof h);
+    CK(cudaStreamSynchronize(s->st));
+    if (s->held)
+        CK(cudaMemcpy(b + sizeof h, s->stage[s->cur], (size_t)s->held * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b + sizeof h + (size_t)s->held * sizeof(float2), s->sums, sums_b, cudaMemcpyDeviceToHost));
+    *len = need;
+    return CYC_OK;
+}
+
+int cyc_load(cyc_stream* s, const void* buf, size_t len)
+{
+    if (!s || !buf) return fail(CYC_EINVAL, "cyc_load: NULL argument");
+    BlobHeader h;
+    if (len < sizeof h) return fail(CYC_EINVAL, "cyc_load: blob too short");
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "CYCSTAT1", 8) || h.version != kBlobVersion)
+        return fail(CYC_EINVAL, "cyc_load: not a libcyc state blob of version %u", kBlobVersion);
+    if (h.fingerprint != s->fingerprint || h.F != s->F || h.L != s->L || h.A != s->A || h.Au != s->Au ||
+        h.conj_flag != s->conj_flag || h.n0 != s->n0)
+        return fail(CYC_EINVAL, "cyc_load: blob was saved by a stream with other lags, cycle frequencies, forms or n0");
+    if (h.held < 0 || h.held > s->M || h.T < 0 || h.n_eff < 0 || h.held > h.T)
+        return fail(CYC_EINVAL, "cyc_load: inconsistent counters in blob");
+    size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
+    size_t need = sizeof h + (size_t)h.held * sizeof(float2) + sums_b;
+    if (len < need) return fail(CYC_EINVAL, "cyc_load: blob truncated (%zu < %zu)", len, need);
+    DeviceGuard g(s->device);
+    const unsigned char* b = (const unsigned char*)buf;
+    CK(cudaStreamSynchronize(s->st));
+    if (h.held)
+        CK(cudaMemcpy(s->stage[s->cur], b + sizeof h, (size_t)h.held * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->sums, b + sizeof h + (size_t)h.held * sizeof(float2), sums_b, cudaMemcpyHostToDevice));
+    s->T = h.T;
+    s->n_eff = h.n_eff;
+    s->held = h.held;
+    return CYC_OK;
+}
+
+int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, int64_t* n_eff)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_info: handle is NULL");
+    if (forms) *forms = s->F;
+    if (nunique) *nunique = s->Au;
+    if (total) *total = s->T;
+    if (n_eff) *n_eff = s->n_eff;
+    return CYC_OK;
+}
+
+int cyc_profile(cyc_stream* s, int enable)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_profile: handle is NULL");
+    s->prof = enable != 0;
+    return CYC_OK;
+}
+
+int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_profile_read: handle is NULL");
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->st));
+    for (auto& e : s->ev_pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        s->prof_ms += ms;
+        s->ev_free.push_back(e);
+    }
+    s->ev_pending.clear();
+    if (proj_ms) *proj_ms = s->prof_ms;
+    if (proj_launches) *proj_launches = s->prof_launches;
+    if (kernels) *kernels = s->kernel_launches;
+    s->prof_ms = 0.0;
+    s->prof_launches = 0;
+    s->kernel_launches = 0;
+    return CYC_OK;
+}
+
+const char* cyc_strerror(int code)
+{
+    switch (code) {
+    case CYC_OK: return "success";
+    case CYC_EINVAL: return "invalid argument";
+    case CYC_ENOMEM: return "out of memory";
+    case CYC_ECUDA: return "CUDA error";
+    case CYC_EAGAIN: return "not admitted, try again";
+    case CYC_ETIMEDOUT: return "bounded device wait timed out";
+    case CYC_ENODATA: return "no data (N_eff == 0)";
+    case CYC_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+const char* cyc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

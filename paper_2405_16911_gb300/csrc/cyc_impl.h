@@ -1,0 +1,56 @@
+// cyc_impl.h -- internal declarations shared by the host API and the kernel files of libcyc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cyc.h"
+
+namespace cyc {
+
+// One projection pass over a contiguous view of the stream (Sec. 4, Eq. (impl-corr)):
+//   part[s][u][c] = sum over n in split s of  W(u, n) * P_c(n)
+// with W(u, n) = exp(-j 2 pi phi_u (nbase + n) / 2^64) and P_c the lag product of column c
+// (c = form * L + lag index).  The caller folds the splits into the FP64 sums.
+struct ProjArgs {
+    const float2*   x;          // view x[0 .. nc + M)
+    int64_t         nc;         // committed n in this pass (0 <= n < nc)
+    uint64_t        nbase;      // absolute index of x[0], mod 2^64
+    const uint64_t* phi;        // [Au] cycle frequencies as u64 fixed point (cycles * 2^64)
+    int             Au;
+    const int32_t*  col_lag;    // [ncols] lag of each column
+    const int8_t*   col_conj;   // [ncols] 1: CONJ column (x[n+m] x[n]), 0: CONV (x[n+m] x*[n])
+    int             ncols;
+    int             nsplit;     // number of n-splits (partials)
+    int64_t         split_len;  // samples per split
+    float2*         part;       // [nsplit][Au][ncols]
+};
+
+// Launch geometry chosen by a kernel family for one pass.
+struct ProjPlan {
+    int     nsplit;
+    int64_t split_len;
+};
+
+// FP32 CUDA-core projection (proj_fp32.cu).
+ProjPlan    fp32_plan(int Au, int ncols, int64_t nc, int num_sms);
+cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st);
+size_t      fp32_max_partials(int Au, int ncols, int num_sms);   // float2 elements
+
+// Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu).
+bool        tc_supported(int ncols);
+ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);
+cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
+size_t      tc_max_partials(int Au, int ncols, int num_sms);
+
+// Helpers (cyc_kernels.cu).
+// sums[u][c] += sum_s part[s][u][c]  (FP64)
+cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* sums, cudaStream_t st);
+// out[f][a][l] = sums[amap[a]][f * L + l] / n_eff
+cudaError_t read_sums(const double2* sums, const int32_t* amap, int F, int A, int L, int ncols,
+                      double inv_n, double2* out, cudaStream_t st);
+
+}  // namespace cyc

@@ -1,0 +1,204 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU only).
+
+Error metric: max over (form, a, m) of |R_gpu - R_oracle| / R^0(0), with R^0(0) the
+oracle's mean power over the committed samples.  Tolerances: FP32 1e-5, BF16x3 1e-4,
+FP16 1e-2 (relative to R^0(0)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
+CONV, CONJ, BOTH = 1, 2, 3
+
+
+def rel_err(R, Ro, x, M):
+    return float(np.max(np.abs(R - Ro)) / oracle.r00(x, M))
+
+
+def run_gpu(cyc, x, lags, alphas, forms=BOTH, precision="fp32", chunks=None, n0=0, device_input=True,
+            max_chunk=0):
+    import torch
+    with cyc.Stream(lags, alphas, forms, precision=precision, n0=n0, max_chunk=max_chunk) as s:
+        xt = torch.from_numpy(x.view(np.float32).copy()).cuda() if device_input else None
+        pos = 0
+        for c in (chunks or [x.size]):
+            if device_input:
+                s.push(xt[2 * pos:2 * (pos + c)])
+            else:
+                s.push(np.ascontiguousarray(x[pos:pos + c]))
+            pos += c
+        assert pos == x.size
+        R, neff = s.read()
+    return R, neff
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_ragged_small_parity(cyc, precision):
+    x = synth.white(5003, seed=101).astype(np.complex64)
+    lags = np.array([0, 1, 2, 3, 5, 8, 13, 21, 34])
+    alphas = np.random.default_rng(1).uniform(-0.5, 0.5, 37)
+    R, neff = run_gpu(cyc, x, lags, alphas, precision=precision)
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert neff == no == 5003 - 34
+    assert rel_err(R, Ro, x, 34) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_several_tiles_each_way(cyc, precision):
+    # 300 cycle frequencies (3 tiles of 128, ragged) x 2 forms x 70 lags (140 columns)
+    x = synth.white(20011, seed=102).astype(np.complex64)
+    lags = np.arange(70)
+    alphas = -0.5 + np.arange(300) / 300.0
+    R, neff = run_gpu(cyc, x, lags, alphas, precision=precision)
+    Ro, _ = oracle.estimate(x, lags, alphas)
+    assert rel_err(R, Ro, x, 69) < TOL[precision]
+
+
+def test_single_form_and_order(cyc):
+    x = synth.white(3000, seed=103).astype(np.complex64)
+    lags = np.array([7, 0, 3, 7])               # unsorted with a duplicate
+    alphas = np.array([0.25, -0.1, 0.3333])
+    for forms in (CONV, CONJ):
+        R, _ = run_gpu(cyc, x, lags, alphas, forms=forms)
+        Ro, _ = oracle.estimate(x, lags, alphas, forms)
+        assert R.shape == (1, 3, 4)
+        assert rel_err(R, Ro, x, 7) < 1e-5
+        assert np.array_equal(R[0, :, 0], R[0, :, 3])
+
+
+def test_chunk_split_invariance(cyc):
+    x = synth.white(9000, seed=104).astype(np.complex64)
+    lags = np.arange(0, 40, 3)              # M = 39
+    alphas = np.linspace(-0.5, 0.5, 23, endpoint=False)
+    R1, n1 = run_gpu(cyc, x, lags, alphas)
+    splits = [1, 38, 39, 40, 2, 7, 997, 13, 4096, 1, 1]
+    splits.append(x.size - sum(splits))
+    R2, n2 = run_gpu(cyc, x, lags, alphas, chunks=splits)
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert n1 == n2 == no
+    assert rel_err(R2, Ro, x, 39) < 1e-5
+    assert rel_err(R2, R1, x, 39) < 2e-6
+    # pushes longer than max_chunk are cut inside the library
+    R3, _ = run_gpu(cyc, x, lags, alphas, max_chunk=1000)
+    assert rel_err(R3, Ro, x, 39) < 1e-5
+
+
+def test_large_start_index(cyc):
+    x = synth.white(4000, seed=105).astype(np.complex64)
+    lags = np.arange(6)
+    alphas = np.array([0.1, -0.33, 0.123456789, 0.5, 1 / 3.0, 0.0])
+    n0 = (1 << 40) + 12345
+    R, _ = run_gpu(cyc, x, lags, alphas, n0=n0)
+    Ro, _ = oracle.estimate(x, lags, alphas, n0=n0)
+    assert rel_err(R, Ro, x, 5) < 1e-5
+
+
+def test_aliases_are_deduplicated(cyc):
+    x = synth.white(2500, seed=106).astype(np.complex64)
+    alphas = np.array([0.125, 1.125, -0.875, 0.25, 0.125])
+    R, _ = run_gpu(cyc, x, [0, 2], alphas)
+    assert np.array_equal(R[:, 0], R[:, 1]) and np.array_equal(R[:, 0], R[:, 2]) and np.array_equal(R[:, 0], R[:, 4])
+    h = cyc.cyc_create_ex([0, 2], alphas)
+    try:
+        assert cyc.cyc_info(h)[1] == 2
+    finally:
+        cyc.cyc_destroy(h)
+
+
+def test_host_device_inputs_and_outputs(cyc):
+    import torch
+    x = synth.white(6000, seed=107).astype(np.complex64)
+    lags, alphas = np.arange(9), np.array([0.0, 0.2, -0.45])
+    Rd, _ = run_gpu(cyc, x, lags, alphas, device_input=True, chunks=[1000, 5000])
+    Rh, _ = run_gpu(cyc, x, lags, alphas, device_input=False, chunks=[1000, 5000])
+    assert np.array_equal(Rd, Rh)
+    with cyc.Stream(lags, alphas) as s:
+        s.push(np.ascontiguousarray(x))
+        out = torch.zeros((2, 3, 9, 2), dtype=torch.float64, device="cuda")
+        _, neff = s.read(out)
+        torch.cuda.synchronize()
+        Rdev = out.cpu().numpy()
+    assert neff == 6000 - 8
+    assert np.array_equal(Rdev[..., 0] + 1j * Rdev[..., 1], Rh)
+
+
+def test_save_load_resume(cyc):
+    x = synth.white(7000, seed=108).astype(np.complex64)
+    lags, alphas = np.arange(0, 30, 2), np.linspace(-0.5, 0.5, 11)
+    Rfull, _ = run_gpu(cyc, x, lags, alphas, chunks=[2500, 4500])
+    with cyc.Stream(lags, alphas) as s:
+        s.push(np.ascontiguousarray(x[:2500]))
+        blob = s.save()
+    with cyc.Stream(lags, alphas) as s2:
+        s2.load(blob)
+        s2.push(np.ascontiguousarray(x[2500:]))
+        R2, _ = s2.read()
+    assert np.array_equal(R2, Rfull)
+    with cyc.Stream(lags, alphas[:5]) as s3:
+        with pytest.raises(cyc.CycError) as e:
+            s3.load(blob)
+        assert e.value.code == -1
+
+
+def test_reset_and_nodata_and_errors(cyc):
+    x = synth.white(100, seed=109).astype(np.complex64)
+    with cyc.Stream([0, 50], [0.1]) as s:
+        s.push(np.ascontiguousarray(x[:40]))
+        out = np.full((2, 1, 2), 7.0 + 7.0j)
+        with pytest.raises(cyc.CycError) as e:
+            s.read(out)
+        assert e.value.code == -6 and np.all(out == 7.0 + 7.0j)
+        s.push(np.ascontiguousarray(x[40:]))
+        R1, n = s.read()
+        assert n == 50
+        s.reset()
+        assert s.info()[2:] == (0, 0)
+        s.push(np.ascontiguousarray(x))
+        R2, _ = s.read()
+        assert np.array_equal(R1, R2)
+        with pytest.raises(cyc.CycError):
+            s.push(np.ascontiguousarray(x), nsamples=-1)
+    for bad in (dict(lags=[-1, 2], alphas=[0.1]), dict(lags=[], alphas=[0.1]), dict(lags=[1], alphas=[]),
+                dict(lags=[1], alphas=[float("nan")]), dict(lags=[1], alphas=[0.1], conj_flag=4)):
+        with pytest.raises(cyc.CycError) as e:
+            cyc.cyc_create_ex(**bad)
+        assert e.value.code == -1
+
+
+def test_config0_full_grid(cyc):
+    w = workloads.config0()
+    x, lags = w["x"], w["lags"]
+    for forms, al in ((CONV, w["alphas_conv"]), (CONJ, w["alphas_conj"])):
+        R, neff = run_gpu(cyc, x, lags, al, forms=forms)
+        Ro, no = oracle.estimate(x, lags, al, forms)
+        assert neff == no == 65536 - 31
+        assert rel_err(R, Ro, x, 31) < 1e-5
+
+
+def test_config1_full_size_sampled(cyc):
+    """2^26 samples in 2^16 chunks, 1024 cycle frequencies, 128 lags, both forms; the
+    oracle recomputes 12 sampled entries over all 2^26 - 127 terms."""
+    w = workloads.config1()
+    x, lags, alphas = w["x"], w["lags"], w["alphas"]
+    C = w["chunk"]
+    R, neff = run_gpu(cyc, x, lags, alphas, chunks=[C] * (x.size // C))
+    assert neff == x.size - 127
+    rng = np.random.default_rng(7)
+    f = rng.integers(0, 2, 12)
+    ia = rng.integers(0, 1024, 12)
+    im = rng.integers(0, 128, 12)
+    f[0], ia[0], im[0] = 0, 512, 0                  # a = 0, m = 0: the mean power itself
+    f[1], ia[1], im[1] = 0, 1023, 127               # last row, last column
+    Ro, _ = oracle.entries(x, 127, f + 1, alphas[ia], lags[im])
+    r00 = oracle.r00(x, 127)
+    err = np.max(np.abs(R[f, ia, im] - Ro)) / r00
+    assert err < 1e-5
+    assert abs(R[0, 512, 0] - r00) / r00 < 1e-5
