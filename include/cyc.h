@@ -153,6 +153,14 @@ CYC_API int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, in
 CYC_API int cyc_profile(cyc_stream* s, int enable);
 CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels);
 
+/*
+ * cyc_phase_increment: the fixed-point form in which a stream holds cycle frequency a:
+ * *phi = round(a * 2^64) mod 2^64, so the phase of sample n is phi * n mod 2^64 in units
+ * of 2^-64 cycles (exact for any n; Sec. 2's exp(-j 2 pi a~ n)).  Host-only, no GPU
+ * needed.  CYC_EINVAL if a is not finite or phi is NULL.
+ */
+CYC_API int cyc_phase_increment(double a, uint64_t* phi);
+
 /* Error text for a status code, and the calling thread's last detailed message. */
 CYC_API const char* cyc_strerror(int code);
 CYC_API const char* cyc_last_error(void);

@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
         "cyc_save": ([P, P, P], I),
         "cyc_load": ([P, P, ctypes.c_size_t], I),
         "cyc_info": ([P, P, P, P, P], I),
+        "cyc_phase_increment": ([ctypes.c_double, P], I),
         "cyc_profile": ([P, I], I),
         "cyc_profile_read": ([P, P, P, P], I),
         "cyc_strerror": ([I], ctypes.c_char_p),
@@ -199,6 +200,13 @@ def cyc_info(h: int):
     t, n = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(load().cyc_info(h, ctypes.byref(f), ctypes.byref(u), ctypes.byref(t), ctypes.byref(n)))
     return f.value, u.value, t.value, n.value
+
+
+def cyc_phase_increment(a: float) -> int:
+    """round(a * 2^64) mod 2^64: the u64 phase step the library uses for cycle frequency a."""
+    v = ctypes.c_uint64(0)
+    _check(load().cyc_phase_increment(float(a), ctypes.byref(v)))
+    return v.value
 
 
 def cyc_profile(h: int, enable: bool = True) -> None:

@@ -59,16 +59,24 @@ constexpr int32_t kMaxLag = 1 << 20;
 constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
 constexpr uint32_t kBlobVersion = 1;
 
-// a (cycles/sample) -> round(frac(a) * 2^64) mod 2^64.  frac(a) = a - floor(a) is exact
-// for every double, and scaling by 2^64 is exact; only the final rounding to an integer
-// can move the value, by at most 2^-65 cycles/sample.
+// a (cycles/sample) -> round(a * 2^64) mod 2^64, exactly.  a = m * 2^e with m the 53-bit
+// integer significand, so a * 2^64 = m * 2^(e+64): a left shift (bits beyond 2^64 are
+// whole cycles and drop out) or a rounded right shift, then two's-complement negation
+// for a < 0.  (a - floor(a) would not do: for negative a it rounds.)  The result is off
+// from a by at most 2^-65 cycles/sample, and only when a has bits below 2^-64.
 uint64_t alpha_to_phi(double a)
 {
-    double fr = a - floor(a);
-    double y = ldexp(fr, 64);
-    double r = nearbyint(y);
-    if (r >= 18446744073709551616.0) return 0;
-    return (uint64_t)r;
+    if (a == 0.0) return 0;
+    int ex = 0;
+    double fr = frexp(fabs(a), &ex);                  // |a| = fr * 2^ex, fr in [0.5, 1)
+    uint64_t m = (uint64_t)ldexp(fr, 53);             // exact, < 2^53
+    int sh = ex - 53 + 64;
+    uint64_t phi;
+    if (sh >= 64) phi = 0;
+    else if (sh >= 0) phi = m << sh;
+    else if (sh < -54) phi = 0;
+    else phi = (m + (1ull << (-sh - 1))) >> (-sh);
+    return a < 0 ? (~phi + 1ull) : phi;
 }
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t n)
@@ -495,6 +503,13 @@ int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, int64_t* n
     if (nunique) *nunique = s->Au;
     if (total) *total = s->T;
     if (n_eff) *n_eff = s->n_eff;
+    return CYC_OK;
+}
+
+int cyc_phase_increment(double a, uint64_t* phi)
+{
+    if (!phi || !isfinite(a)) return fail(CYC_EINVAL, "cyc_phase_increment: a must be finite, phi non-NULL");
+    *phi = alpha_to_phi(a);
     return CYC_OK;
 }
 

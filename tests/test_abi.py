@@ -74,3 +74,23 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_cyc, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _cyc.load(str(tmp_path / "nope.so"))
+
+
+def test_phase_increment_is_exact_rounding(lib):
+    """round(a * 2^64) mod 2^64 in exact rational arithmetic, for awkward doubles."""
+    from fractions import Fraction
+    import numpy as np
+    rng = np.random.default_rng(0)
+    vals = [0.0, -0.0, 0.5, -0.5, 0.1, -0.33, 1.0 / 3.0, -1.0 / 3.0, 1e-30, -1e-30, 2.0 ** -64,
+            2.0 ** -65, 3 * 2.0 ** -66, 12345.678, -98765.4321, 2.0 ** 60 + 0.5 * 2 ** 8, -0.875, 1 - 2 ** -53]
+    vals += list(rng.uniform(-3, 3, 200)) + list(rng.uniform(-1e-12, 1e-12, 50))
+    for a in vals:
+        exact = Fraction(a) * (1 << 64)
+        fl = exact.numerator // exact.denominator
+        rem = exact - fl
+        want = (fl + (1 if rem > Fraction(1, 2) else 0 if rem < Fraction(1, 2) else 1)) % (1 << 64)
+        got = pkg.cyc_phase_increment(a)
+        # ties (only possible for a with a bit at 2^-65) may round either way
+        assert got == want or (rem == Fraction(1, 2) and got == (fl % (1 << 64))), a
+    with pytest.raises(pkg.CycError):
+        pkg.cyc_phase_increment(float("inf"))
