@@ -191,10 +191,11 @@ int alloc_state(cyc_stream* s)
     CK(cudaMemcpy(s->d_amap, s->amap.data(), s->A * sizeof(int32_t), cudaMemcpyHostToDevice));
     std::vector<int32_t> cl(s->ncols);
     std::vector<int8_t> cc(s->ncols);
+    // column c = lag index * F + form index: both forms of a lag are neighbours
     for (int f = 0; f < s->F; ++f)
         for (int l = 0; l < s->L; ++l) {
-            cl[f * s->L + l] = s->lags[l];
-            cc[f * s->L + l] = s->forms[f] == CYC_CONJ ? 1 : 0;
+            cl[l * s->F + f] = s->lags[l];
+            cc[l * s->F + f] = s->forms[f] == CYC_CONJ ? 1 : 0;
         }
     CK(cudaMalloc(&s->d_col_lag, s->ncols * sizeof(int32_t)));
     CK(cudaMemcpy(s->d_col_lag, cl.data(), s->ncols * sizeof(int32_t), cudaMemcpyHostToDevice));

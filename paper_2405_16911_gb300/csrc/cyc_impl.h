@@ -14,7 +14,7 @@ namespace cyc {
 // One projection pass over a contiguous view of the stream (Sec. 4, Eq. (impl-corr)):
 //   part[s][u][c] = sum over n in split s of  W(u, n) * P_c(n)
 // with W(u, n) = exp(-j 2 pi phi_u (nbase + n) / 2^64) and P_c the lag product of column c
-// (c = form * L + lag index).  The caller folds the splits into the FP64 sums.
+// (c = lag index * F + form index).  The caller folds the splits into the FP64 sums.
 struct ProjArgs {
     const float2*   x;          // view x[0 .. nc + M)
     int64_t         nc;         // committed n in this pass (0 <= n < nc)
@@ -49,7 +49,7 @@ size_t      tc_max_partials(int Au, int ncols, int num_sms);
 // Helpers (cyc_kernels.cu).
 // sums[u][c] += sum_s part[s][u][c]  (FP64)
 cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* sums, cudaStream_t st);
-// out[f][a][l] = sums[amap[a]][f * L + l] / n_eff
+// out[f][a][l] = sums[amap[a]][l * F + f] / n_eff
 cudaError_t read_sums(const double2* sums, const int32_t* amap, int F, int A, int L, int ncols,
                       double inv_n, double2* out, cudaStream_t st);
 

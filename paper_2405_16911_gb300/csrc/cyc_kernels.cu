@@ -22,7 +22,7 @@ __global__ void reduce_partials_kernel(const float2* __restrict__ part, int nspl
     sums[e] = o;
 }
 
-// out[f][a][l] = sums[amap[a]][f * L + l] * inv_n   (normalisation by N_eff, Sec. 4)
+// out[f][a][l] = sums[amap[a]][l * F + f] * inv_n   (normalisation by N_eff, Sec. 4)
 __global__ void read_sums_kernel(const double2* __restrict__ sums, const int32_t* __restrict__ amap,
                                  int F, int A, int L, int ncols, double inv_n, double2* __restrict__ out)
 {
@@ -32,7 +32,7 @@ __global__ void read_sums_kernel(const double2* __restrict__ sums, const int32_t
     int l = (int)(e % L);
     int a = (int)((e / L) % A);
     int f = (int)(e / ((int64_t)A * L));
-    double2 v = sums[(size_t)amap[a] * ncols + f * L + l];
+    double2 v = sums[(size_t)amap[a] * ncols + l * F + f];
     out[e] = make_double2(v.x * inv_n, v.y * inv_n);
 }
 

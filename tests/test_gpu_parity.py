@@ -121,7 +121,8 @@ def test_host_device_inputs_and_outputs(cyc):
     Rh, _ = run_gpu(cyc, x, lags, alphas, device_input=False, chunks=[1000, 5000])
     assert np.array_equal(Rd, Rh)
     with cyc.Stream(lags, alphas) as s:
-        s.push(np.ascontiguousarray(x))
+        s.push(np.ascontiguousarray(x[:1000]))
+        s.push(np.ascontiguousarray(x[1000:]))
         out = torch.zeros((2, 3, 9, 2), dtype=torch.float64, device="cuda")
         _, neff = s.read(out)
         torch.cuda.synchronize()
