@@ -161,6 +161,35 @@ CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launc
  */
 CYC_API int cyc_phase_increment(double a, uint64_t* phi);
 
+/*
+ * cyc_estimate_static: a one-shot estimate over x[0..T) that allocates no memory at all.
+ * The paper has no counterpart; it exists for callers that cannot call cudaMalloc when
+ * they need an estimate -- a real-time signal-processing callback that must not
+ * allocate (device allocation can synchronise the whole device and take unbounded time),
+ * or a plug-in whose host application has already reserved the device memory in its
+ * own pool.
+ *   x        device memory of the current device: T interleaved complex64 samples
+ *   lags, alphas, conj_flag, n0   as in cyc_params (host arrays, read before return)
+ *   out      device memory of the current device, F * nalphas * nlags * 16 bytes: R as
+ *            interleaved FP64 [form][alpha][lag] (same layout and value as cyc_read)
+ *   n_eff    optional, receives T - max(lags) (or 0)
+ *   cuda_stream   cudaStream_t the work is queued on (NULL = legacy default stream); the
+ *            call returns once the work is queued, synchronise that stream before
+ *            reading `out`.
+ * It runs the FP32 projection with its scratch -- the cycle-frequency and column tables
+ * and the FP32 partial sums -- in one fixed file-scope device array of about 8.1 MiB,
+ * which every GPU that loads the library holds until the process exits.  Limits:
+ * nalphas <= 4096, nlags * F <= 2048 and nalphas * nlags * F <= 2^20; larger requests
+ * fail with CYC_EINVAL and queue nothing.  Duplicate cycle frequencies are computed
+ * separately.  The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares the array:
+ * calls whose GPU work can overlap (different CUDA streams) race and give wrong results;
+ * calls on one stream are ordered and safe.  CYC_ENODATA when T <= max(lags).
+ */
+CYC_API int cyc_estimate_static(const void* x, int64_t T, const int32_t* lags, int nlags,
+                                const double* alphas, int nalphas, int conj_flag, int64_t n0,
+                                double* out, int64_t* n_eff, void* cuda_stream);
+
 /* Error text for a status code, and the calling thread's last detailed message. */
 CYC_API const char* cyc_strerror(int code);
 CYC_API const char* cyc_last_error(void);

@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "cyc_load": ([P, P, ctypes.c_size_t], I),
         "cyc_info": ([P, P, P, P, P], I),
         "cyc_phase_increment": ([ctypes.c_double, P], I),
+        "cyc_estimate_static": ([P, I64, P, I, P, I, I, I64, P, P, P], I),
         "cyc_profile": ([P, I], I),
         "cyc_profile_read": ([P, P, P, P], I),
         "cyc_strerror": ([I], ctypes.c_char_p),
@@ -200,6 +201,21 @@ def cyc_info(h: int):
     t, n = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(load().cyc_info(h, ctypes.byref(f), ctypes.byref(u), ctypes.byref(t), ctypes.byref(n)))
     return f.value, u.value, t.value, n.value
+
+
+def cyc_estimate_static(x, T: int, lags, alphas, conj_flag: int, n0: int, out, cuda_stream: int = 0) -> int:
+    """One-shot estimate with no allocation inside the library (see include/cyc.h).
+    x, out: device tensors (or addresses) of the current device; returns N_eff.  The work
+    is queued on `cuda_stream`; synchronise it before reading `out`."""
+    lib = load()
+    xa, _, _, _kx = _ptr_info(x)
+    oa, _, _, _ko = _ptr_info(out)
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    neff = ctypes.c_int64(0)
+    _check(lib.cyc_estimate_static(xa, int(T), lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size,
+                                   int(conj_flag), int(n0), oa, ctypes.byref(neff), cuda_stream or None))
+    return neff.value
 
 
 def cyc_phase_increment(a: float) -> int:

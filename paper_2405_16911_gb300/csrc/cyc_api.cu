@@ -97,6 +97,8 @@ struct BlobHeader {
 
 }  // namespace
 
+void cyc::record_error(const char* msg) { g_err = msg; }
+
 struct cyc_stream {
     int device = 0;
     cudaStream_t st = nullptr;

@@ -46,6 +46,9 @@ ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
 size_t      tc_max_partials(int Au, int ncols, int num_sms);
 
+// Sets the calling thread's message returned by cyc_last_error() (cyc_api.cu).
+void record_error(const char* msg);
+
 // Helpers (cyc_kernels.cu).
 // sums[u][c] += sum_s part[s][u][c]  (FP64)
 cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* sums, cudaStream_t st);
