@@ -47,16 +47,19 @@ TRAFFIC = {}
 
 def workload_config(precision):
     return {
-        "workload": "cfg1 GMSK stream: 2^26 complex64 samples pushed in 2^16-sample chunks, "
-                    "lags 0..127, 1024 cycle freqs -0.5+k/1024, CONV+CONJ, FP64 running sums",
-        "samples_per_step": T_SAMPLES, "chunk": CHUNK, "lags": NLAGS, "cycle_freqs": NALPHAS,
+        "workload": "cfg1 GMSK stream: %d complex64 samples pushed in 2^16-sample chunks, "
+                    "lags 0..127, 1024 cycle freqs -0.5+k/1024, CONV+CONJ, FP64 running sums" % ARGS_SAMPLES[0],
+        "samples_per_step": ARGS_SAMPLES[0], "chunk": CHUNK, "lags": NLAGS, "cycle_freqs": NALPHAS,
         "forms": NFORMS, "projection": precision,
         "l2": "inputs larger than L2 (512 MB stream per step, 129 MB L2)",
     }
 
 
-def cmac_per_step(T=T_SAMPLES):
-    return (T - (NLAGS - 1)) * NLAGS * NALPHAS * NFORMS
+def cmac_per_step(T=None):
+    return ((T or ARGS_SAMPLES[0]) - (NLAGS - 1)) * NLAGS * NALPHAS * NFORMS
+
+
+ARGS_SAMPLES = [T_SAMPLES]
 
 
 def kernel_hash(precision):
@@ -272,7 +275,7 @@ def run_ours(args):
             raise
         precision = "fp32"
 
-    w = workloads.config1(replica=rank)
+    w = workloads.config1(T=args.samples, replica=rank)
     x, lags, alphas = w["x"], w["lags"], w["alphas"]
     x_dev = torch.from_numpy(x.view(np.float32)).cuda()
 
@@ -319,7 +322,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "fp16": "f16"}[precision],
         "data": "synthetic", "config": workload_config(precision),
-        "msamples_per_s": T_SAMPLES * world / (ms * 1e-3) / 1e6,
+        "msamples_per_s": ARGS_SAMPLES[0] * world / (ms * 1e-3) / 1e6,
         "precision": {"fp32": "fp32 CUDA-core projection", "bf16x3": "bf16 hi/lo split, 3 products, fp32 accumulate",
                       "fp16": "fp16 single pass, fp32 accumulate"}[precision] + "; fp64 running sums",
         "gpu_launches": kernels, "roofline": roof, "clocks": clocks,
@@ -366,9 +369,14 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--samples", type=int, default=T_SAMPLES,
+                    help="stream length per step (multiple of 2^16); smaller values only for profiling")
     args = ap.parse_args()
+    if args.samples % CHUNK or args.samples < CHUNK:
+        ap.error("--samples must be a positive multiple of %d" % CHUNK)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    ARGS_SAMPLES[0] = args.samples
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -129,6 +129,7 @@ struct cyc_stream {
     float2* part = nullptr;
     size_t part_elems = 0;
     double2* d_out = nullptr;
+    int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
     // profiling
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -146,12 +147,12 @@ struct cyc_stream {
     void free_all()
     {
         free_events();
-        void* ps[] = {stage[0], stage[1], sums, d_phi, d_amap, d_col_lag, d_col_conj, part, d_out};
+        void* ps[] = {stage[0], stage[1], sums, d_phi, d_amap, d_col_lag, d_col_conj, part, d_out, d_err};
         for (void* p : ps)
             if (p) cudaFree(p);
         stage[0] = stage[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
-        d_col_conj = nullptr; part = nullptr; d_out = nullptr;
+        d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr;
     }
 };
 
@@ -207,6 +208,8 @@ int alloc_state(cyc_stream* s)
                                                : tc_max_partials(s->Au, s->ncols, s->num_sms);
     CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
     CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
+    CK(cudaMalloc(&s->d_err, sizeof(int)));
+    CK(cudaMemset(s->d_err, 0, sizeof(int)));
     return CYC_OK;
 }
 
@@ -223,6 +226,7 @@ int project(cyc_stream* s, int64_t nc)
     a.col_conj = s->d_col_conj;
     a.ncols = s->ncols;
     a.part = s->part;
+    a.err = s->d_err;
     ProjPlan pl = s->precision == CYC_P_FP32 ? fp32_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : tc_plan(s->Au, s->ncols, nc, s->num_sms);
     a.nsplit = pl.nsplit;
@@ -248,6 +252,18 @@ int project(cyc_stream* s, int64_t nc)
     s->prof_launches++;
     CK(reduce_partials(s->part, pl.nsplit, s->Au * s->ncols, s->sums, s->st));
     s->kernel_launches += 2;
+    return CYC_OK;
+}
+
+// After a stream synchronisation: did a kernel's bounded wait give up?
+int check_device_status(cyc_stream* s)
+{
+    int flag = 0;
+    CK(cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(s->d_err, 0, sizeof(int)));
+        return fail(CYC_ETIMEDOUT, "a projection kernel gave up waiting (code %d); the sums are unreliable", flag);
+    }
     return CYC_OK;
 }
 
@@ -401,7 +417,7 @@ int cyc_sync(cyc_stream* s)
     if (!s) return fail(CYC_EINVAL, "cyc_sync: handle is NULL");
     DeviceGuard g(s->device);
     CK(cudaStreamSynchronize(s->st));
-    return CYC_OK;
+    return check_device_status(s);
 }
 
 int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
@@ -420,7 +436,7 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     if (!dev)
         CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
-    return CYC_OK;
+    return check_device_status(s);
 }
 
 int cyc_reset(cyc_stream* s)

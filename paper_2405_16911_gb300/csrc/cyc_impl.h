@@ -27,6 +27,7 @@ struct ProjArgs {
     int             nsplit;     // number of n-splits (partials)
     int64_t         split_len;  // samples per split
     float2*         part;       // [nsplit][Au][ncols]
+    int*            err = nullptr;  // device status word: a bounded wait that gave up sets it
 };
 
 // Launch geometry chosen by a kernel family for one pass.

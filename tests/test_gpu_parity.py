@@ -40,7 +40,15 @@ def run_gpu(cyc, x, lags, alphas, forms=BOTH, precision="fp32", chunks=None, n0=
     return R, neff
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+PRECS = ["fp32", "bf16x3", "fp16"]
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return workloads.config1()
+
+
+@pytest.mark.parametrize("precision", PRECS)
 def test_ragged_small_parity(cyc, precision):
     x = synth.white(5003, seed=101).astype(np.complex64)
     lags = np.array([0, 1, 2, 3, 5, 8, 13, 21, 34])
@@ -51,7 +59,7 @@ def test_ragged_small_parity(cyc, precision):
     assert rel_err(R, Ro, x, 34) < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", PRECS)
 def test_several_tiles_each_way(cyc, precision):
     # 300 cycle frequencies (3 tiles of 128, ragged) x 2 forms x 70 lags (140 columns)
     x = synth.white(20011, seed=102).astype(np.complex64)
@@ -62,43 +70,47 @@ def test_several_tiles_each_way(cyc, precision):
     assert rel_err(R, Ro, x, 69) < TOL[precision]
 
 
-def test_single_form_and_order(cyc):
+@pytest.mark.parametrize("precision", PRECS)
+def test_single_form_and_order(cyc, precision):
     x = synth.white(3000, seed=103).astype(np.complex64)
-    lags = np.array([7, 0, 3, 7])               # unsorted with a duplicate
+    lags = np.array([7, 0, 3, 7, 1])            # unsorted, a duplicate, odd column count
     alphas = np.array([0.25, -0.1, 0.3333])
     for forms in (CONV, CONJ):
-        R, _ = run_gpu(cyc, x, lags, alphas, forms=forms)
+        R, _ = run_gpu(cyc, x, lags, alphas, forms=forms, precision=precision)
         Ro, _ = oracle.estimate(x, lags, alphas, forms)
-        assert R.shape == (1, 3, 4)
-        assert rel_err(R, Ro, x, 7) < 1e-5
+        assert R.shape == (1, 3, 5)
+        assert rel_err(R, Ro, x, 7) < TOL[precision]
         assert np.array_equal(R[0, :, 0], R[0, :, 3])
 
 
-def test_chunk_split_invariance(cyc):
+@pytest.mark.parametrize("precision", PRECS)
+def test_chunk_split_invariance(cyc, precision):
     x = synth.white(9000, seed=104).astype(np.complex64)
     lags = np.arange(0, 40, 3)              # M = 39
     alphas = np.linspace(-0.5, 0.5, 23, endpoint=False)
-    R1, n1 = run_gpu(cyc, x, lags, alphas)
+    R1, n1 = run_gpu(cyc, x, lags, alphas, precision=precision)
     splits = [1, 38, 39, 40, 2, 7, 997, 13, 4096, 1, 1]
     splits.append(x.size - sum(splits))
-    R2, n2 = run_gpu(cyc, x, lags, alphas, chunks=splits)
+    R2, n2 = run_gpu(cyc, x, lags, alphas, chunks=splits, precision=precision)
     Ro, no = oracle.estimate(x, lags, alphas)
     assert n1 == n2 == no
-    assert rel_err(R2, Ro, x, 39) < 1e-5
-    assert rel_err(R2, R1, x, 39) < 2e-6
+    tol = TOL[precision]
+    assert rel_err(R2, Ro, x, 39) < tol
+    assert rel_err(R2, R1, x, 39) < tol / 5
     # pushes longer than max_chunk are cut inside the library
-    R3, _ = run_gpu(cyc, x, lags, alphas, max_chunk=1000)
-    assert rel_err(R3, Ro, x, 39) < 1e-5
+    R3, _ = run_gpu(cyc, x, lags, alphas, max_chunk=1000, precision=precision)
+    assert rel_err(R3, Ro, x, 39) < tol
 
 
-def test_large_start_index(cyc):
+@pytest.mark.parametrize("precision", PRECS)
+def test_large_start_index(cyc, precision):
     x = synth.white(4000, seed=105).astype(np.complex64)
     lags = np.arange(6)
     alphas = np.array([0.1, -0.33, 0.123456789, 0.5, 1 / 3.0, 0.0])
     n0 = (1 << 40) + 12345
-    R, _ = run_gpu(cyc, x, lags, alphas, n0=n0)
+    R, _ = run_gpu(cyc, x, lags, alphas, n0=n0, precision=precision)
     Ro, _ = oracle.estimate(x, lags, alphas, n0=n0)
-    assert rel_err(R, Ro, x, 5) < 1e-5
+    assert rel_err(R, Ro, x, 5) < TOL[precision]
 
 
 def test_aliases_are_deduplicated(cyc):
@@ -184,13 +196,14 @@ def test_config0_full_grid(cyc):
         assert rel_err(R, Ro, x, 31) < 1e-5
 
 
-def test_config1_full_size_sampled(cyc):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_config1_full_size_sampled(cyc, cfg1, precision):
     """2^26 samples in 2^16 chunks, 1024 cycle frequencies, 128 lags, both forms; the
     oracle recomputes 12 sampled entries over all 2^26 - 127 terms."""
-    w = workloads.config1()
+    w = cfg1
     x, lags, alphas = w["x"], w["lags"], w["alphas"]
     C = w["chunk"]
-    R, neff = run_gpu(cyc, x, lags, alphas, chunks=[C] * (x.size // C))
+    R, neff = run_gpu(cyc, x, lags, alphas, chunks=[C] * (x.size // C), precision=precision)
     assert neff == x.size - 127
     rng = np.random.default_rng(7)
     f = rng.integers(0, 2, 12)
@@ -201,5 +214,26 @@ def test_config1_full_size_sampled(cyc):
     Ro, _ = oracle.entries(x, 127, f + 1, alphas[ia], lags[im])
     r00 = oracle.r00(x, 127)
     err = np.max(np.abs(R[f, ia, im] - Ro)) / r00
-    assert err < 1e-5
-    assert abs(R[0, 512, 0] - r00) / r00 < 1e-5
+    assert err < TOL[precision]
+    assert abs(R[0, 512, 0] - r00) / r00 < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_config2_full_size_sampled(cyc, precision):
+    """One 2^20-sample block, 4096 cycle frequencies, 256 lags, both forms (two column
+    tiles for the tensor-core path); 24 sampled entries plus the strongest conjugate line."""
+    w = workloads.config2()
+    x, lags, alphas = w["x"], w["lags"], w["alphas"]
+    R, neff = run_gpu(cyc, x, lags, alphas, precision=precision)
+    assert neff == x.size - 255
+    rng = np.random.default_rng(11)
+    f = rng.integers(0, 2, 24)
+    ia = rng.integers(0, 4096, 24)
+    im = rng.integers(0, 256, 24)
+    # conjugate line of GMSK at 4 sps: 2 f0 + 1/8 -> nearest grid index
+    k = int(round(((2 * w["f0"] + 0.125 + 0.5) % 1.0) * 4096)) % 4096
+    f[0], ia[0], im[0] = 1, k, 0
+    f[1], ia[1], im[1] = 1, 4095, 255
+    Ro, _ = oracle.entries(x, 255, f + 1, alphas[ia], lags[im])
+    err = np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, 255)
+    assert err < TOL[precision], err
