@@ -4,22 +4,50 @@
 namespace cyc {
 namespace {
 
-// sums[e] += sum_s part[s][e], e = (u, c) flattened; FP32 partials widened to FP64.
+// sums[e] += sum_s part[s][e], e = (u, c) flattened.  The splits are added in FP32 (a few
+// dozen terms, each already a sum over thousands of samples) and the total once in FP64:
+// FP64 arithmetic is scarce on this GPU, so it is kept to one add per value and push.
+// Each thread folds two neighbouring elements with one 16-byte load per split and keeps
+// four loads in flight.
 __global__ void reduce_partials_kernel(const float2* __restrict__ part, int nsplit, int n_uc,
                                        double2* __restrict__ sums)
 {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= n_uc) return;
-    double sr = 0.0, si = 0.0;
-    for (int s = 0; s < nsplit; ++s) {
-        float2 v = part[(size_t)s * n_uc + e];
-        sr += (double)v.x;
-        si += (double)v.y;
+    if (e + 1 < n_uc && (n_uc & 1) == 0) {
+        const float4* p = reinterpret_cast<const float4*>(part + e);
+        const size_t stride = (size_t)n_uc / 2;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int s = 0;
+        for (; s + 4 <= nsplit; s += 4) {
+            float4 v0 = __ldg(p + (size_t)(s + 0) * stride);
+            float4 v1 = __ldg(p + (size_t)(s + 1) * stride);
+            float4 v2 = __ldg(p + (size_t)(s + 2) * stride);
+            float4 v3 = __ldg(p + (size_t)(s + 3) * stride);
+            acc.x += (v0.x + v1.x) + (v2.x + v3.x);
+            acc.y += (v0.y + v1.y) + (v2.y + v3.y);
+            acc.z += (v0.z + v1.z) + (v2.z + v3.z);
+            acc.w += (v0.w + v1.w) + (v2.w + v3.w);
+        }
+        for (; s < nsplit; ++s) {
+            float4 v = __ldg(p + (size_t)s * stride);
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+        double2 o0 = sums[e], o1 = sums[e + 1];
+        sums[e] = make_double2(o0.x + (double)acc.x, o0.y + (double)acc.y);
+        sums[e + 1] = make_double2(o1.x + (double)acc.z, o1.y + (double)acc.w);
+        return;
     }
-    double2 o = sums[e];
-    o.x += sr;
-    o.y += si;
-    sums[e] = o;
+    for (int k = 0; k < 2 && e + k < n_uc; ++k) {
+        float sr = 0.f, si = 0.f;
+        for (int s = 0; s < nsplit; ++s) {
+            float2 v = part[(size_t)s * n_uc + e + k];
+            sr += v.x;
+            si += v.y;
+        }
+        double2 o = sums[e + k];
+        sums[e + k] = make_double2(o.x + (double)sr, o.y + (double)si);
+    }
 }
 
 // out[f][a][l] = sums[amap[a]][l * F + f] * inv_n   (normalisation by N_eff, Sec. 4)
@@ -41,7 +69,8 @@ __global__ void read_sums_kernel(const double2* __restrict__ sums, const int32_t
 cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* sums, cudaStream_t st)
 {
     if (n_uc <= 0) return cudaSuccess;
-    reduce_partials_kernel<<<(n_uc + 255) / 256, 256, 0, st>>>(part, nsplit, n_uc, sums);
+    int pairs = (n_uc + 1) / 2;
+    reduce_partials_kernel<<<(pairs + 255) / 256, 256, 0, st>>>(part, nsplit, n_uc, sums);
     return cudaGetLastError();
 }
 

@@ -10,12 +10,13 @@
 // with the absolute sample index, so the whole n-range accumulates in TMEM without any
 // per-tile rotation; the epilogue writes one FP32 partial per CTA.
 //
-// Warp roles (288 threads):
-//   warps 0-3  P producers: thread t forms the lag products of tile columns 2t and 2t+1
-//              (with lag-major columns, both forms of one lag) -> B-operand rows t, t+128
-//   warps 4-7  W producers: thread t forms W for cycle frequency row t; afterwards they
-//              are the epilogue (TMEM lane quadrant = warp % 4 = row / 32)
-//   warp 8     TMEM allocation; lane 0 issues every tcgen05.mma and commit
+// Warp roles (544 threads): two producer sets, set k producing the groups g = k mod 2, so
+// that one set's load and sine latencies hide behind the other's work.  In set k:
+//   warps 8k+0..3  P producers: thread t forms the lag products of tile columns 2t and 2t+1
+//                  (with lag-major columns, both forms of one lag) -> B-operand rows t, t+128
+//   warps 8k+4..7  W producers: thread t forms W for cycle frequency row t; those of set 0
+//                  are afterwards the epilogue (TMEM lane quadrant = warp % 4 = row / 32)
+//   warp 16        TMEM allocation; lane 0 issues every tcgen05.mma and commit
 // Operands go through an NSTAGE ring of shared-memory stages (one 8-sample group each),
 // guarded by "full" (producers -> MMA) and "empty" (tcgen05.commit -> producers) mbarriers.
 // Operand layout: K-major, no swizzle, 8-row x 16-byte core matrices.
@@ -37,8 +38,9 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int GS = 8;                    // samples per group (one K = 16 step)
-constexpr int NTHREADS = 288;
-constexpr int MMA_WARP = 8;
+constexpr int NSET = 2;                  // producer sets
+constexpr int NTHREADS = (8 * NSET + 1) * 32;
+constexpr int MMA_WARP = 8 * NSET;
 constexpr int P_BYTES = 8192, W_BYTES = 6144;
 constexpr uint32_t P_LBO = 128, P_SBO = 256, W_LBO = 128, W_SBO = 384;
 constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
@@ -142,16 +144,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
     tc::tc_fence_after();
     const uint32_t tmem = bars->tmem;
 
-    if (warp < 4) {
+    const int pset = warp < MMA_WARP ? warp / 8 : 0;       // producer set
+    const int role = warp % 8;                              // 0-3 P, 4-7 W
+    if (warp < MMA_WARP && role < 4) {
         // ------------------------------------------------------------ P producers
-        const int t = tid;                                  // 0..127
+        const int t = tid - pset * 256;                     // 0..127
         const int jA = 2 * t, jB = 2 * t + 1;               // tile-local columns
         const bool okA = c0 + jA < a.ncols, okB = c0 + jB < a.ncols;
         const int mA = okA ? a.col_lag[c0 + jA] : 0, mB = okB ? a.col_lag[c0 + jB] : 0;
         const bool cjA = okA && a.col_conj[c0 + jA], cjB = okB && a.col_conj[c0 + jB];
         const uint32_t offA = (t / 8) * P_SBO + (t % 8) * 16;               // B-operand row t
         const uint32_t offB = ((t + 128) / 8) * P_SBO + (t % 8) * 16;       // row t + 128
-        for (int g = 0; g < ngroups; ++g) {
+        const bool same_lag = okB && mA == mB;
+        for (int g = pset; g < ngroups; g += NSET) {
             const int s = g % C::NSTAGE;
             if (g >= C::NSTAGE && !tc::mbar_wait(&bars->empty[s], ((g / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
                 flag_error(a, bars, 1);
@@ -164,8 +169,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
                 float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
                 if (n + i < n_end) {
                     float2 x0 = __ldg(&a.x[n + i]);
-                    if (okA) pA = lag_product(__ldg(&a.x[n + i + mA]), x0, cjA);
-                    if (okB) pB = lag_product(__ldg(&a.x[n + i + mB]), x0, cjB);
+                    float2 xa = okA ? __ldg(&a.x[n + i + mA]) : make_float2(0.f, 0.f);
+                    float2 xb = same_lag ? xa : (okB ? __ldg(&a.x[n + i + mB]) : make_float2(0.f, 0.f));
+                    if (okA) pA = lag_product(xa, x0, cjA);
+                    if (okB) pB = lag_product(xb, x0, cjB);
                 }
                 prA[i] = pA.x; piA[i] = pA.y; prB[i] = pB.x; piB[i] = pB.y;
             }
@@ -187,23 +194,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bars->full[s]);
         }
-    } else if (warp < 8) {
+    } else if (warp < MMA_WARP) {
         // ------------------------------------------------------------ W producers
-        const int t = tid - 128;                            // row 0..127
+        const int t = tid - pset * 256 - 128;               // row 0..127
         const bool ok = u0 + t < a.Au;
         const uint64_t phi = ok ? a.phi[u0 + t] : 0ull;
-        // R_i = exp(-j 2 pi phi i / 2^64), i < 8, from the exact u64 phase in FP64
-        float rr[8], ri[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            int64_t th = (int64_t)(phi * (uint64_t)i);       // two's complement: [-1/2, 1/2) cycles
-            double sd, cd;
-            sincospi((double)th * 0x1p-63, &sd, &cd);
-            rr[i] = (float)cd;
-            ri[i] = (float)-sd;
-        }
         const uint32_t offW = (t / 8) * W_SBO + (t % 8) * 16;
-        for (int g = 0; g < ngroups; ++g) {
+        for (int g = pset; g < ngroups; g += NSET) {
             const int s = g % C::NSTAGE;
             if (g >= C::NSTAGE && !tc::mbar_wait(&bars->empty[s], ((g / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
                 flag_error(a, bars, 1);
@@ -211,12 +208,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
             }
             float wr[8], wi[8];
             if (ok) {
+                // each weight straight from the exact u64 phase phi * n mod 2^64
                 const uint64_t n = a.nbase + (uint64_t)(n_beg + (int64_t)g * GS);
-                float2 w0 = phase_rot(phi, n);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    wr[i] = w0.x * rr[i] - w0.y * ri[i];
-                    wi[i] = w0.x * ri[i] + w0.y * rr[i];
+                    float2 w = phase_rot(phi, n + (uint64_t)i);
+                    wr[i] = w.x;
+                    wi[i] = w.y;
                 }
             } else {
 #pragma unroll
