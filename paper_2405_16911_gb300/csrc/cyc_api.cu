@@ -227,6 +227,8 @@ int project(cyc_stream* s, int64_t nc)
     a.ncols = s->ncols;
     a.part = s->part;
     a.err = s->d_err;
+    a.M = s->M;
+    a.x_avail = (s->M + s->max_chunk + kStagePad) & ~(int64_t)1;
     ProjPlan pl = s->precision == CYC_P_FP32 ? fp32_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : tc_plan(s->Au, s->ncols, nc, s->num_sms);
     a.nsplit = pl.nsplit;
@@ -349,9 +351,10 @@ int cyc_create_ex(const cyc_params* p, cyc_stream** out)
     h = fnv1a(h, &s->n0, sizeof s->n0);
     s->fingerprint = h;
 
-    if (s->precision != CYC_P_FP32 && !tc_supported(s->ncols)) {
+    if (s->precision != CYC_P_FP32 && !tc_supported(s->ncols, s->M)) {
         delete s;
-        return fail(CYC_ENOTSUP, "tensor-core projection does not support %d columns", p->nlags);
+        return fail(CYC_ENOTSUP, "the tensor-core projection supports lags up to 2560 (max lag %d); use CYC_P_FP32",
+                    s->M);
     }
     DeviceGuard g(s->device);
     if (!g.ok) { delete s; return fail(CYC_ECUDA, "cudaSetDevice(%d) failed", p->device); }

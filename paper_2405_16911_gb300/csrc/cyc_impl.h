@@ -28,6 +28,8 @@ struct ProjArgs {
     int64_t         split_len;  // samples per split
     float2*         part;       // [nsplit][Au][ncols]
     int*            err = nullptr;  // device status word: a bounded wait that gave up sets it
+    int             M = 0;          // max lag (halo of every staged block of samples)
+    int64_t         x_avail = 0;    // samples readable from x (allocation bound, even)
 };
 
 // Launch geometry chosen by a kernel family for one pass.
@@ -42,7 +44,7 @@ cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st);
 size_t      fp32_max_partials(int Au, int ncols, int num_sms);   // float2 elements
 
 // Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu).
-bool        tc_supported(int ncols);
+bool        tc_supported(int ncols, int M);
 ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
 size_t      tc_max_partials(int Au, int ncols, int num_sms);

@@ -17,6 +17,9 @@
 //   warps 8k+4..7  W producers: thread t forms W for cycle frequency row t; those of set 0
 //                  are afterwards the epilogue (TMEM lane quadrant = warp % 4 = row / 32)
 //   warp 16        TMEM allocation; lane 0 issues every tcgen05.mma and commit
+//   warp 17        lane 0 streams the samples into shared memory: blocks of XB samples plus
+//                  the M-sample halo, by TMA bulk copy into a ring of two slots ("xfull":
+//                  transaction-counted, "xempty": released by the eight P warps)
 // Operands go through an NSTAGE ring of shared-memory stages (one 8-sample group each),
 // guarded by "full" (producers -> MMA) and "empty" (tcgen05.commit -> producers) mbarriers.
 // Operand layout: K-major, no swizzle, 8-row x 16-byte core matrices.
@@ -39,8 +42,11 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int GS = 8;                    // samples per group (one K = 16 step)
 constexpr int NSET = 2;                  // producer sets
-constexpr int NTHREADS = (8 * NSET + 1) * 32;
 constexpr int MMA_WARP = 8 * NSET;
+constexpr int LOAD_WARP = MMA_WARP + 1;
+constexpr int NTHREADS = (LOAD_WARP + 1) * 32;
+constexpr int XSLOT = 3072;              // samples per staging slot (block + halo)
+constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
 constexpr int P_BYTES = 8192, W_BYTES = 6144;
 constexpr uint32_t P_LBO = 128, P_SBO = 256, W_LBO = 128, W_SBO = 384;
 constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
@@ -61,7 +67,9 @@ struct Cfg<CYC_P_BF16X3> {
 template <int PREC>
 __host__ __device__ constexpr int stage_bytes() { return Cfg<PREC>::NLEV * (P_BYTES + W_BYTES); }
 template <int PREC>
-__host__ __device__ constexpr int smem_bytes() { return Cfg<PREC>::NSTAGE * stage_bytes<PREC>() + 1024; }
+__host__ __device__ constexpr int xslots_off() { return Cfg<PREC>::NSTAGE * stage_bytes<PREC>(); }
+template <int PREC>
+__host__ __device__ constexpr int smem_bytes() { return xslots_off<PREC>() + 2 * XSLOT * 8 + 1024; }
 
 // ---- packing: 8 floats -> 16 bytes of FP16 / BF16 (+ BF16 remainders) --------------------
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -103,6 +111,8 @@ __device__ __forceinline__ void st16(unsigned char* p, uint4 v) { *reinterpret_c
 struct Bars {
     uint64_t full[16];
     uint64_t empty[16];
+    uint64_t xfull[2];
+    uint64_t xempty[2];
     uint64_t done;
     uint32_t tmem;
     int abort;
@@ -119,7 +129,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
 {
     using C = Cfg<PREC>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    Bars* bars = reinterpret_cast<Bars*>(smem + C::NSTAGE * stage_bytes<PREC>());
+    Bars* bars = reinterpret_cast<Bars*>(smem + xslots_off<PREC>() + 2 * XSLOT * 8);
+    float2* xs = reinterpret_cast<float2*>(smem + xslots_off<PREC>());     // two slots of XSLOT samples
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int u0 = blockIdx.x * BM;
@@ -128,11 +139,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
     int64_t n_end = n_beg + a.split_len;
     if (n_end > a.nc) n_end = a.nc;
     const int ngroups = n_end > n_beg ? (int)((n_end - n_beg + GS - 1) / GS) : 0;
+    const int mpad = (a.M + 1) & ~1;
+    const int XB = (XSLOT - mpad) & ~(GS - 1);            // samples per staged block
+    const int nblocks = (ngroups * GS + XB - 1) / XB;
 
     if (tid == 0) {
         for (int s = 0; s < C::NSTAGE; ++s) {
             tc::mbar_init(&bars->full[s], 8);      // one arrival per producer warp
             tc::mbar_init(&bars->empty[s], 1);     // one tcgen05.commit
+        }
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(&bars->xfull[k], 1);     // loader's arrive.expect_tx (+ bytes)
+            tc::mbar_init(&bars->xempty[k], 4 * NSET);
         }
         tc::mbar_init(&bars->done, 1);
         bars->abort = 0;
@@ -156,23 +174,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
         const uint32_t offA = (t / 8) * P_SBO + (t % 8) * 16;               // B-operand row t
         const uint32_t offB = ((t + 128) / 8) * P_SBO + (t % 8) * 16;       // row t + 128
         const bool same_lag = okB && mA == mB;
+        int cur_b = -1;
         for (int g = pset; g < ngroups; g += NSET) {
             const int s = g % C::NSTAGE;
             if (g >= C::NSTAGE && !tc::mbar_wait(&bars->empty[s], ((g / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
                 flag_error(a, bars, 1);
                 break;
             }
+            const int b = (g * GS) / XB;
+            if (b != cur_b) {
+                __syncwarp();
+                if (cur_b >= 0 && lane == 0) tc::mbar_arrive(&bars->xempty[cur_b & 1]);
+                if (!tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET)) {
+                    flag_error(a, bars, 4);
+                    break;
+                }
+                cur_b = b;
+            }
+            const float2* xb = xs + (b & 1) * XSLOT + (g * GS - b * XB);   // sample n_beg + 8g
             float prA[8], piA[8], prB[8], piB[8];
             const int64_t n = n_beg + (int64_t)g * GS;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
                 if (n + i < n_end) {
-                    float2 x0 = __ldg(&a.x[n + i]);
-                    float2 xa = okA ? __ldg(&a.x[n + i + mA]) : make_float2(0.f, 0.f);
-                    float2 xb = same_lag ? xa : (okB ? __ldg(&a.x[n + i + mB]) : make_float2(0.f, 0.f));
+                    float2 x0 = xb[i];
+                    float2 xa = okA ? xb[i + mA] : make_float2(0.f, 0.f);
+                    float2 xv = same_lag ? xa : (okB ? xb[i + mB] : make_float2(0.f, 0.f));
                     if (okA) pA = lag_product(xa, x0, cjA);
-                    if (okB) pB = lag_product(xb, x0, cjB);
+                    if (okB) pB = lag_product(xv, x0, cjB);
                 }
                 prA[i] = pA.x; piA[i] = pA.y; prB[i] = pB.x; piB[i] = pB.y;
             }
@@ -237,7 +267,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bars->full[s]);
         }
-    } else if (lane == 0) {
+    } else if (warp == LOAD_WARP && lane == 0) {
+        // ------------------------------------------------------------ sample loader (TMA)
+        int last = -1;
+        for (int b = 0; b < nblocks; ++b) {
+            const int slot = b & 1;
+            if (b >= 2 && !tc::mbar_wait(&bars->xempty[slot], ((b >> 1) - 1) & 1, WAIT_BUDGET)) {
+                flag_error(a, bars, 5);
+                break;
+            }
+            const int64_t ns = n_beg + (int64_t)b * XB;
+            int64_t cnt = (int64_t)XB + mpad;
+            if (cnt > a.x_avail - ns) cnt = a.x_avail - ns;
+            cnt &= ~(int64_t)1;
+            tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)(cnt * 8));
+            tc::bulk_g2s(xs + slot * XSLOT, a.x + ns, (uint32_t)(cnt * 8), &bars->xfull[slot]);
+            last = b;
+        }
+        // no copy may still be landing when the CTA exits
+        for (int b = last > 0 ? last - 1 : 0; b <= last; ++b)
+            if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET);
+    } else if (warp == MMA_WARP && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         constexpr uint32_t idesc = tc::idesc_f16(BM, BN, C::BF);
         const uint32_t base = tc::smem_u32(smem);
@@ -331,7 +381,7 @@ cudaError_t launch(const ProjArgs& a, cudaStream_t st)
 
 }  // namespace
 
-bool tc_supported(int ncols) { return ncols > 0; }
+bool tc_supported(int ncols, int M) { return ncols > 0 && M >= 0 && M <= MAX_LAG; }
 
 ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms)
 {

@@ -237,3 +237,19 @@ def test_config2_full_size_sampled(cyc, precision):
     Ro, _ = oracle.entries(x, 255, f + 1, alphas[ia], lags[im])
     err = np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, 255)
     assert err < TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16"])
+def test_tensor_core_lag_limit(cyc, precision):
+    """Lags up to 2560 stage through shared memory in blocks with their halo; beyond that
+    the tensor-core projection declines (CYC_ENOTSUP) and FP32 serves."""
+    x = synth.white(30011, seed=110).astype(np.complex64)
+    lags = np.array([0, 1, 999, 2560, 7])
+    alphas = np.array([0.0, 0.21, -0.4, 0.33])
+    R, neff = run_gpu(cyc, x, lags, alphas, precision=precision, chunks=[5000, 9000, 16011])
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert neff == no
+    assert rel_err(R, Ro, x, 2560) < TOL[precision]
+    with pytest.raises(cyc.CycError) as e:
+        cyc.Stream([0, 2561], [0.1], cyc.CYC_BOTH, precision=precision)
+    assert e.value.code == cyc.CYC_ENOTSUP
