@@ -161,6 +161,76 @@ CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launc
  */
 CYC_API int cyc_phase_increment(double a, uint64_t* phi);
 
+/* ======================================================================================
+ * Serving: many concurrent streams, continuously batched.
+ *
+ * A server owns a device, a memory budget and an engine thread.  Streams are opened
+ * (admitted only if their device memory fits the budget and a slot is free), chunks are
+ * submitted from any thread, and the engine repeatedly forms a batch from every open
+ * stream that has new samples: the new committed n-range of each stream becomes work
+ * items (128 cycle frequencies x 128 columns x at most item_samples terms) for one
+ * persistent tensor-core kernel, followed by an FP64 fold into each stream's sums, both
+ * replayed from a captured CUDA graph.  Chunks that arrive while a batch runs join the
+ * next one, so streams of very different rates share the GPU.  Each stream computes the
+ * same estimate as a cyc_stream with the same parameters (Sec. 4, Eq. (impl-corr)).
+ * ====================================================================================== */
+typedef struct cyc_server cyc_server;
+
+typedef struct cyc_server_params {
+    int32_t  max_streams;   /* open streams at most (slots); 0 selects 256 */
+    int32_t  precision;     /* CYC_P_BF16X3 or CYC_P_FP16 */
+    uint64_t mem_budget;    /* device bytes for stream state; 0 selects half the free memory */
+    int64_t  ring_samples;  /* per-stream sample ring (rounded up to a power of two); 0: 1 << 22 */
+    int32_t  max_items;     /* work items per batch; 0 selects 4096 */
+    int64_t  item_samples;  /* committed terms per work item at most; 0 selects 65536 */
+    int32_t  device;        /* CUDA device ordinal */
+} cyc_server_params;
+
+/* One finished chunk: its contribution is in the stream's sums (everything that the
+ * samples up to the chunk's end allow; the last M samples still wait for the next chunk).
+ * Times are host monotonic seconds: when cyc_server_submit returned, and when the engine
+ * saw the batch that completed the chunk finish. */
+typedef struct cyc_done {
+    int32_t  sid;
+    int32_t  status;        /* 0 or a CYC_E* code */
+    uint64_t tag;
+    int64_t  nsamples;
+    double   submit_s;
+    double   done_s;
+} cyc_done;
+
+/* Create a server (engine thread started) / stop it and free everything. */
+CYC_API int cyc_server_create(const cyc_server_params* p, cyc_server** out);
+CYC_API int cyc_server_destroy(cyc_server* srv);
+
+/* Open a stream (lags >= 0, max lag <= 2560; arrays copied).  CYC_EAGAIN when no slot is
+ * free or its device memory would exceed the budget: retry after a close. */
+CYC_API int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const double* alphas,
+                            int nalphas, int conj_flag, int64_t n0, int* sid);
+
+/* Queue nsamples host samples (interleaved complex64) of stream sid; they are on the
+ * device when the call returns, so the buffer may be reused.  CYC_EAGAIN when the
+ * stream's ring has no room yet (earlier chunks still being processed): retry. */
+CYC_API int cyc_server_submit(cyc_server* srv, int sid, const void* chunk, int64_t nsamples, uint64_t tag);
+
+/* Up to `max` finished chunks, oldest first, without waiting; *ndone receives the count. */
+CYC_API int cyc_server_poll(cyc_server* srv, cyc_done* done, int max, int* ndone);
+
+/* Wait until every submitted chunk is finished (CYC_ETIMEDOUT after timeout_s seconds). */
+CYC_API int cyc_server_drain(cyc_server* srv, double timeout_s);
+
+/* R of stream sid (layout and meaning as cyc_read; host or device `out`), after all of its
+ * submitted samples are in the sums.  CYC_ENODATA when N_eff == 0. */
+CYC_API int cyc_server_read(cyc_server* srv, int sid, double* out, int64_t* n_eff);
+
+/* Close stream sid once its work is done; its memory returns to the budget. */
+CYC_API int cyc_server_close(cyc_server* srv, int sid);
+
+/* Counters since creation: batches run, work items run, device busy milliseconds
+ * (sum of batch durations), bytes held by open streams.  Any pointer may be NULL. */
+CYC_API int cyc_server_stats(cyc_server* srv, int64_t* batches, int64_t* items, double* busy_ms,
+                             uint64_t* bytes_held);
+
 /*
  * cyc_estimate_static: a one-shot estimate over x[0..T) that allocates no memory at all.
  * The paper has no counterpart; it exists for callers that cannot call cudaMalloc when

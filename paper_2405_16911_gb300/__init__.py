@@ -8,4 +8,7 @@ from ._cyc import (CycError, Stream, load, declared_functions, LIB_PATH, HEADER,
                    cyc_create, cyc_create_ex, cyc_push, cyc_read, cyc_sync, cyc_reset, cyc_destroy,
                    cyc_save, cyc_load, cyc_info, cyc_phase_increment, cyc_estimate_static, cyc_profile, cyc_profile_read, cyc_strerror,
                    cyc_last_error)
+from ._cyc import (Server, cyc_server_create, cyc_server_destroy, cyc_server_open,  # noqa: F401
+                   cyc_server_submit, cyc_server_poll, cyc_server_drain, cyc_server_read, cyc_server_close,
+                   cyc_server_stats)
 from .build import build  # noqa: F401

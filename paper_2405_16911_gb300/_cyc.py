@@ -43,6 +43,18 @@ class cyc_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32)]
 
 
+class cyc_server_params(ctypes.Structure):
+    _fields_ = [("max_streams", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("mem_budget", ctypes.c_uint64), ("ring_samples", ctypes.c_int64),
+                ("max_items", ctypes.c_int32), ("item_samples", ctypes.c_int64),
+                ("device", ctypes.c_int32)]
+
+
+class cyc_done(ctypes.Structure):
+    _fields_ = [("sid", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_uint64),
+                ("nsamples", ctypes.c_int64), ("submit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -76,6 +88,15 @@ def load(path: str = LIB_PATH):
         "cyc_estimate_static": ([P, I64, P, I, P, I, I, I64, P, P, P], I),
         "cyc_profile": ([P, I], I),
         "cyc_profile_read": ([P, P, P, P], I),
+        "cyc_server_create": ([P, P], I),
+        "cyc_server_destroy": ([P], I),
+        "cyc_server_open": ([P, P, I, P, I, I, I64, P], I),
+        "cyc_server_submit": ([P, I, P, I64, ctypes.c_uint64], I),
+        "cyc_server_poll": ([P, P, I, P], I),
+        "cyc_server_drain": ([P, ctypes.c_double], I),
+        "cyc_server_read": ([P, I, P, P], I),
+        "cyc_server_close": ([P, I], I),
+        "cyc_server_stats": ([P, P, P, P, P], I),
         "cyc_strerror": ([I], ctypes.c_char_p),
         "cyc_last_error": ([], ctypes.c_char_p),
     }
@@ -242,6 +263,131 @@ def cyc_strerror(code: int) -> str:
 
 def cyc_last_error() -> str:
     return load().cyc_last_error().decode()
+
+
+# ----------------------------------------------------------------------------- serving
+
+_srv_shapes: dict[tuple[int, int], tuple[int, int, int]] = {}
+
+
+def cyc_server_create(max_streams: int = 256, precision="bf16x3", mem_budget: int = 0, ring_samples: int = 0,
+                      max_items: int = 0, item_samples: int = 0, device: int = 0) -> int:
+    lib = load()
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p = cyc_server_params(max_streams, precision, mem_budget, ring_samples, max_items, item_samples, device)
+    h = ctypes.c_void_p()
+    _check(lib.cyc_server_create(ctypes.byref(p), ctypes.byref(h)))
+    return h.value
+
+
+def cyc_server_destroy(srv: int) -> None:
+    if srv:
+        for k in [k for k in _srv_shapes if k[0] == srv]:
+            del _srv_shapes[k]
+        _check(load().cyc_server_destroy(srv))
+
+
+def cyc_server_open(srv: int, lags, alphas, conj_flag: int = CYC_BOTH, n0: int = 0) -> int:
+    lib = load()
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    sid = ctypes.c_int(0)
+    _check(lib.cyc_server_open(srv, lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, conj_flag,
+                               int(n0), ctypes.byref(sid)))
+    _srv_shapes[(srv, sid.value)] = (_nforms(conj_flag), alphas.size, lags.size)
+    return sid.value
+
+
+def cyc_server_submit(srv: int, sid: int, chunk, nsamples: int | None = None, tag: int = 0) -> None:
+    addr, nbytes, _dev, _keep = _ptr_info(chunk)
+    if nsamples is None:
+        if nbytes is None:
+            raise ValueError("nsamples is required with a raw address")
+        nsamples = nbytes // 8
+    _check(load().cyc_server_submit(srv, sid, addr, int(nsamples), int(tag)))
+
+
+def cyc_server_poll(srv: int, max_done: int = 4096):
+    """Finished chunks as a list of (sid, status, tag, nsamples, submit_s, done_s)."""
+    buf = (cyc_done * max_done)()
+    n = ctypes.c_int(0)
+    _check(load().cyc_server_poll(srv, buf, max_done, ctypes.byref(n)))
+    return [(d.sid, d.status, d.tag, d.nsamples, d.submit_s, d.done_s) for d in buf[:n.value]]
+
+
+def cyc_server_drain(srv: int, timeout_s: float = 60.0) -> None:
+    _check(load().cyc_server_drain(srv, float(timeout_s)))
+
+
+def cyc_server_read(srv: int, sid: int, out=None):
+    F, A, L = _srv_shapes[(srv, sid)]
+    if out is None:
+        out = np.empty((F, A, L), dtype=np.complex128)
+    addr, nbytes, _dev, _keep = _ptr_info(out)
+    if nbytes is not None and nbytes < F * A * L * 16:
+        raise ValueError("output buffer too small")
+    neff = ctypes.c_int64(0)
+    _check(load().cyc_server_read(srv, sid, addr, ctypes.byref(neff)))
+    return out, int(neff.value)
+
+
+def cyc_server_close(srv: int, sid: int) -> None:
+    _srv_shapes.pop((srv, sid), None)
+    _check(load().cyc_server_close(srv, sid))
+
+
+def cyc_server_stats(srv: int):
+    """(batches, items, busy ms, device bytes held by open streams)."""
+    b, i = ctypes.c_int64(0), ctypes.c_int64(0)
+    ms, by = ctypes.c_double(0), ctypes.c_uint64(0)
+    _check(load().cyc_server_stats(srv, ctypes.byref(b), ctypes.byref(i), ctypes.byref(ms), ctypes.byref(by)))
+    return b.value, i.value, ms.value, by.value
+
+
+class Server:
+    """Owning wrapper of a continuous-batching server."""
+
+    def __init__(self, **kw):
+        self.h = cyc_server_create(**kw)
+
+    def open(self, lags, alphas, conj_flag: int = CYC_BOTH, n0: int = 0) -> int:
+        return cyc_server_open(self.h, lags, alphas, conj_flag, n0)
+
+    def submit(self, sid, chunk, nsamples=None, tag=0):
+        cyc_server_submit(self.h, sid, chunk, nsamples, tag)
+
+    def poll(self, max_done=4096):
+        return cyc_server_poll(self.h, max_done)
+
+    def drain(self, timeout_s=60.0):
+        cyc_server_drain(self.h, timeout_s)
+
+    def read(self, sid, out=None):
+        return cyc_server_read(self.h, sid, out)
+
+    def close_stream(self, sid):
+        cyc_server_close(self.h, sid)
+
+    def stats(self):
+        return cyc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            cyc_server_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # shapes are tracked on the Python side for cyc_read's default output

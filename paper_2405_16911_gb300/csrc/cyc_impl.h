@@ -32,6 +32,24 @@ struct ProjArgs {
     int64_t         x_avail = 0;    // samples readable from x (allocation bound, even)
 };
 
+// One work item of the tensor-core projection: 128 cycle frequencies x 128 columns x an
+// n-range of one stream.  Sample n of the stream is x[n & xmask] (xmask = ring capacity - 1,
+// or all ones for a linear view with x_avail readable samples).  Result element (row r,
+// tile column j) goes to out[r * out_stride + j] for u0 + r < Au and c0 + j < ncols.
+struct TcItem {
+    const float2*   x;
+    uint64_t        xmask;
+    int64_t         x_avail;
+    uint64_t        nbase;      // absolute index of stream sample 0, mod 2^64
+    int64_t         n_beg, n_end;
+    const uint64_t* phi;
+    const int32_t*  col_lag;
+    const int8_t*   col_conj;
+    float2*         out;
+    int             out_stride;
+    int             u0, Au, c0, ncols, M;
+};
+
 // Launch geometry chosen by a kernel family for one pass.
 struct ProjPlan {
     int     nsplit;
@@ -48,6 +66,12 @@ bool        tc_supported(int ncols, int M);
 ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
 size_t      tc_max_partials(int Au, int ncols, int num_sms);
+int         tc_tile_rows();     // cycle frequencies per work item
+int         tc_tile_cols();     // columns per work item
+// Persistent launch over a device list of work items (taken with an atomic counter that
+// the caller zeroes before the launch); `grid` CTAs, one per SM.
+cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision,
+                            int* err, cudaStream_t st);
 
 // Sets the calling thread's message returned by cyc_last_error() (cyc_api.cu).
 void record_error(const char* msg);

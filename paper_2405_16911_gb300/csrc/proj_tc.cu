@@ -1,33 +1,40 @@
 // proj_tc.cu -- tensor-core a-projection (tcgen05, sm_103a): FP16 single pass and the
-// BF16 three-product split, FP32 accumulation in tensor memory.
+// BF16 three-product split, FP32 accumulation in tensor memory (TMEM).
 //
-// Per CTA: 128 cycle frequencies (MMA M) x 256 columns (MMA N) x one n-split.  The complex
-// GEMM  S[u][c] = sum_n W[u][n] P_c(n)  (Sec. 4 Set mode: the per-alpha projection of the
-// lag products; W = exp(-j 2 pi a n), P = x[n+m] x*[n] or x[n+m] x[n], Eqs. (ACF-def),
-// (CCF-def)) is run as two real GEMMs over K = (re, im) of 8 samples per K=16 step:
+// A work item is 128 cycle frequencies (MMA M) x 256 columns (MMA N) x a range of committed
+// n.  The complex GEMM  S[u][c] = sum_n W[u][n] P_c(n)  (Sec. 4 Set mode: the per-alpha
+// projection of the lag products; W = exp(-j 2 pi a n), P = x[n+m] x*[n] or x[n+m] x[n],
+// Eqs. (ACF-def), (CCF-def)) runs as two real GEMMs over K = (re, im) of 8 samples per
+// K = 16 step:
 //     D_r += [Wr | -Wi] . [Pr ; Pi]        D_i += [Wi | Wr] . [Pr ; Pi]
-// D_r and D_i live in TMEM columns [0, 256) and [256, 512).  The phase is folded into W
-// with the absolute sample index, so the whole n-range accumulates in TMEM without any
-// per-tile rotation; the epilogue writes one FP32 partial per CTA.
-//
-// Warp roles (544 threads): two producer sets, set k producing the groups g = k mod 2, so
-// that one set's load and sine latencies hide behind the other's work.  In set k:
-//   warps 8k+0..3  P producers: thread t forms the lag products of tile columns 2t and 2t+1
-//                  (with lag-major columns, both forms of one lag) -> B-operand rows t, t+128
-//   warps 8k+4..7  W producers: thread t forms W for cycle frequency row t; those of set 0
-//                  are afterwards the epilogue (TMEM lane quadrant = warp % 4 = row / 32)
-//   warp 16        TMEM allocation; lane 0 issues every tcgen05.mma and commit
-//   warp 17        lane 0 streams the samples into shared memory: blocks of XB samples plus
-//                  the M-sample halo, by TMA bulk copy into a ring of two slots ("xfull":
-//                  transaction-counted, "xempty": released by the eight P warps)
-// Operands go through an NSTAGE ring of shared-memory stages (one 8-sample group each),
-// guarded by "full" (producers -> MMA) and "empty" (tcgen05.commit -> producers) mbarriers.
-// Operand layout: K-major, no swizzle, 8-row x 16-byte core matrices.
+// D_r and D_i live in TMEM columns [0, 256) and [256, 512).  The weights carry the absolute
+// sample index, so the whole n-range of an item accumulates in TMEM without any per-tile
+// rotation; the epilogue writes one FP32 partial tile per item.
+// Operands go through a ring of shared-memory stages (one 8-sample group each), K-major,
+// no swizzle, 8-row x 16-byte core matrices:
 //   P block: row r (column), chunk k (0: Pr, 1: Pi) at (r/8)*256 + k*128 + (r%8)*16
 //   W block: row r (cycle freq), chunk k (0: Wi, 1: Wr, 2: -Wi) at (r/8)*384 + k*128 + (r%8)*16
 // so that [Wr | -Wi] starts at chunk 1 and [Wi | Wr] at chunk 0, both with LBO = 128.
-// BF16x3 keeps a hi and a lo copy of each block: v = hi + lo, hi = bf16(v), lo = bf16(v - hi),
-// and issues hi.hi, hi.lo, lo.hi.
+// The samples x[n .. n + XB + M) of each block are staged in shared memory by TMA bulk
+// copies (a ring of two slots), so that the lag-product warps read shared memory only.
+// BF16x3: v = hi + lo, hi = bf16(v), lo = bf16(v - hi); products hi.hi, hi.lo, lo.hi.
+//
+// Warp roles (576 threads).  Two producer sets; set k produces the groups G = k mod 2 of
+// the CTA's running group counter G, so one set's latencies hide behind the other's work:
+//   set k, warps 8k+0..3  P warps: thread t forms tile columns 2t, 2t+1 (with lag-major
+//                         columns both forms of one lag) -> B rows t and t + 128
+//   set k, warps 8k+4..7  W warps: thread t forms the weights of cycle-frequency row t;
+//                         set 0's are also the epilogue (TMEM lane quadrant = warp % 4)
+//   warp 16  TMEM allocation; lane 0 issues every tcgen05.mma and commit
+//   warp 17  lane 0: the TMA sample loader
+// Items may start at any sample; the staged block then starts one sample earlier (bulk
+// copies need 16-byte alignment) and readers skip it.  The linear view needs x_avail even.
+// Barriers: full[s] (8 producer warps -> MMA), empty[s] (tcgen05.commit -> producers),
+// xfull/xempty for the sample slots, done (last MMA of an item -> epilogue).  Every wait is
+// bounded; a wait that gives up sets the caller's status word and the CTA winds down.
+//
+// Two launch modes share the code: one item per CTA derived from the grid (cyc_push), and a
+// persistent list of items taken with an atomic counter (the multi-stream server).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,13 +49,15 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int GS = 8;                    // samples per group (one K = 16 step)
 constexpr int NSET = 2;                  // producer sets
-constexpr int MMA_WARP = 8 * NSET;
+constexpr int P_WARPS = 4, W_WARPS = 4, SET_WARPS = P_WARPS + W_WARPS;
+constexpr int MMA_WARP = NSET * SET_WARPS;
 constexpr int LOAD_WARP = MMA_WARP + 1;
 constexpr int NTHREADS = (LOAD_WARP + 1) * 32;
-constexpr int XSLOT = 3072;              // samples per staging slot (block + halo)
-constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
 constexpr int P_BYTES = 8192, W_BYTES = 6144;
 constexpr uint32_t P_LBO = 128, P_SBO = 256, W_LBO = 128, W_SBO = 384;
+constexpr int XSLOT = 3072;              // samples per staging slot (block + halo)
+constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
+constexpr uint32_t TM_DR = 0, TM_DI = 256;
 constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
 
 template <int PREC>
@@ -88,25 +97,19 @@ __device__ __forceinline__ uint32_t pack_b2(float a, float b, uint32_t* lo)
 }
 
 template <bool BF>
-__device__ __forceinline__ void pack8(const float (&v)[8], uint4& hi, uint4& lo)
+__device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&hi)[4], uint32_t (&lo)[4])
 {
-    if constexpr (BF) {
-        hi.x = pack_b2(v[0], v[1], &lo.x);
-        hi.y = pack_b2(v[2], v[3], &lo.y);
-        hi.z = pack_b2(v[4], v[5], &lo.z);
-        hi.w = pack_b2(v[6], v[7], &lo.w);
-    } else {
-        hi = make_uint4(pack_h2(v[0], v[1]), pack_h2(v[2], v[3]), pack_h2(v[4], v[5]), pack_h2(v[6], v[7]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (BF) hi[k] = pack_b2(v[2 * k], v[2 * k + 1], &lo[k]);
+        else hi[k] = pack_h2(v[2 * k], v[2 * k + 1]);
     }
 }
 
-__device__ __forceinline__ uint4 neg8(uint4 v)
+__device__ __forceinline__ void st16(unsigned char* p, const uint32_t (&v)[4])
 {
-    const uint32_t s = 0x80008000u;
-    return make_uint4(v.x ^ s, v.y ^ s, v.z ^ s, v.w ^ s);
+    *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
 }
-
-__device__ __forceinline__ void st16(unsigned char* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
 
 struct Bars {
     uint64_t full[16];
@@ -115,42 +118,59 @@ struct Bars {
     uint64_t xempty[2];
     uint64_t done;
     uint32_t tmem;
+    int item;
     int abort;
+    TcItem it;
 };
 
-__device__ __forceinline__ void flag_error(const ProjArgs& a, Bars* b, int code)
+__device__ __forceinline__ void give_up(int* err, Bars* b, int code)
 {
     b->abort = 1;
-    if (a.err) atomicCAS(a.err, 0, code);
+    if (err) atomicCAS(err, 0, code);
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
+// The item of CTA (bx, by, bz) for a single cyc_push pass.
+__device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, int bz)
+{
+    TcItem it;
+    it.x = a.x;
+    it.xmask = ~0ull;
+    it.x_avail = a.x_avail;
+    it.nbase = a.nbase;
+    it.n_beg = (int64_t)bz * a.split_len;
+    it.n_end = it.n_beg + a.split_len < a.nc ? it.n_beg + a.split_len : a.nc;
+    it.phi = a.phi;
+    it.col_lag = a.col_lag;
+    it.col_conj = a.col_conj;
+    it.u0 = bx * BM;
+    it.c0 = by * BN;
+    it.Au = a.Au;
+    it.ncols = a.ncols;
+    it.M = a.M;
+    it.out = a.part + ((size_t)bz * a.Au + (size_t)it.u0) * a.ncols + it.c0;
+    it.out_stride = a.ncols;
+    return it;
+}
+
+template <int PREC, bool LIST>
+__global__ void __launch_bounds__(NTHREADS, 1)
+proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restrict__ nitems, int* counter, int* err)
 {
     using C = Cfg<PREC>;
     extern __shared__ __align__(1024) unsigned char smem[];
     Bars* bars = reinterpret_cast<Bars*>(smem + xslots_off<PREC>() + 2 * XSLOT * 8);
-    float2* xs = reinterpret_cast<float2*>(smem + xslots_off<PREC>());     // two slots of XSLOT samples
+    float2* xs = reinterpret_cast<float2*>(smem + xslots_off<PREC>());
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    const int u0 = blockIdx.x * BM;
-    const int c0 = blockIdx.y * BN;
-    const int64_t n_beg = (int64_t)blockIdx.z * a.split_len;
-    int64_t n_end = n_beg + a.split_len;
-    if (n_end > a.nc) n_end = a.nc;
-    const int ngroups = n_end > n_beg ? (int)((n_end - n_beg + GS - 1) / GS) : 0;
-    const int mpad = (a.M + 1) & ~1;
-    const int XB = (XSLOT - mpad) & ~(GS - 1);            // samples per staged block
-    const int nblocks = (ngroups * GS + XB - 1) / XB;
+    if (!LIST) err = pa.err;
 
     if (tid == 0) {
         for (int s = 0; s < C::NSTAGE; ++s) {
-            tc::mbar_init(&bars->full[s], 8);      // one arrival per producer warp
-            tc::mbar_init(&bars->empty[s], 1);     // one tcgen05.commit
+            tc::mbar_init(&bars->full[s], SET_WARPS);
+            tc::mbar_init(&bars->empty[s], 1);
         }
         for (int k = 0; k < 2; ++k) {
-            tc::mbar_init(&bars->xfull[k], 1);     // loader's arrive.expect_tx (+ bytes)
-            tc::mbar_init(&bars->xempty[k], 4 * NSET);
+            tc::mbar_init(&bars->xfull[k], 1);
+            tc::mbar_init(&bars->xempty[k], NSET * P_WARPS);
         }
         tc::mbar_init(&bars->done, 1);
         bars->abort = 0;
@@ -162,196 +182,269 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
     tc::tc_fence_after();
     const uint32_t tmem = bars->tmem;
 
-    const int pset = warp < MMA_WARP ? warp / 8 : 0;       // producer set
-    const int role = warp % 8;                              // 0-3 P, 4-7 W
-    if (warp < MMA_WARP && role < 4) {
-        // ------------------------------------------------------------ P producers
-        const int t = tid - pset * 256;                     // 0..127
-        const int jA = 2 * t, jB = 2 * t + 1;               // tile-local columns
-        const bool okA = c0 + jA < a.ncols, okB = c0 + jB < a.ncols;
-        const int mA = okA ? a.col_lag[c0 + jA] : 0, mB = okB ? a.col_lag[c0 + jB] : 0;
-        const bool cjA = okA && a.col_conj[c0 + jA], cjB = okB && a.col_conj[c0 + jB];
-        const uint32_t offA = (t / 8) * P_SBO + (t % 8) * 16;               // B-operand row t
-        const uint32_t offB = ((t + 128) / 8) * P_SBO + (t % 8) * 16;       // row t + 128
-        const bool same_lag = okB && mA == mB;
-        int cur_b = -1;
-        for (int g = pset; g < ngroups; g += NSET) {
-            const int s = g % C::NSTAGE;
-            if (g >= C::NSTAGE && !tc::mbar_wait(&bars->empty[s], ((g / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
-                flag_error(a, bars, 1);
-                break;
+    const int pset = warp < MMA_WARP ? warp / SET_WARPS : 0;
+    const int role = warp % SET_WARPS;              // 0-1 P, 2-5 W
+    uint32_t G = 0;                                 // groups this CTA has run (all items)
+    uint32_t Bk = 0;                                // sample blocks this CTA has staged
+    uint32_t nit = 0;                               // items this CTA has run
+    int lastb = -1;                                 // loader: last block issued (running count)
+
+    for (;;) {
+        // ---- next item (thread 0 fetches; everybody reads it after the barrier) ----
+        if (tid == 0) {
+            int idx = -1;
+            if (!bars->abort) {
+                if (LIST) {
+                    idx = atomicAdd(counter, 1);
+                    if (idx >= *nitems) idx = -1;
+                    else bars->it = items[idx];
+                } else if (nit == 0) {
+                    idx = 0;
+                    bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
+                }
             }
-            const int b = (g * GS) / XB;
-            if (b != cur_b) {
-                __syncwarp();
-                if (cur_b >= 0 && lane == 0) tc::mbar_arrive(&bars->xempty[cur_b & 1]);
-                if (!tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET)) {
-                    flag_error(a, bars, 4);
+            bars->item = idx;
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+        if (bars->item < 0) break;
+        const TcItem& it = bars->it;
+        const int64_t n_beg = it.n_beg, n_end = it.n_end;
+        const int64_t span = n_end - n_beg;
+        const int ngroups = span > 0 ? (int)((span + GS - 1) / GS) : 0;
+        const int mpad = (it.M + 1) & ~1;
+        const int XB = (XSLOT - mpad - 2) & ~(GS - 1);          // samples per staged block
+        const int nblocks = (ngroups * GS + XB - 1) / XB;
+        const int xoff = (int)(n_beg & 1);    // bulk copies start at an even sample (16-byte aligned)
+
+        if (warp < MMA_WARP && role < P_WARPS) {
+            // -------------------------------------------------------- P warps (lag products)
+            const int t = (warp - pset * SET_WARPS) * 32 + lane;     // 0..127
+            const int c0 = it.c0, ncols = it.ncols;
+            const int jA = 2 * t, jB = 2 * t + 1;
+            const bool okA = c0 + jA < ncols, okB = c0 + jB < ncols;
+            const int mA = okA ? it.col_lag[c0 + jA] : 0, mB = okB ? it.col_lag[c0 + jB] : 0;
+            const bool cjA = okA && it.col_conj[c0 + jA], cjB = okB && it.col_conj[c0 + jB];
+            const bool same_lag = okB && mA == mB;
+            const uint32_t offA = (t / 8) * P_SBO + (t % 8) * 16;             // B row t
+            const uint32_t offB = ((t + 128) / 8) * P_SBO + (t % 8) * 16;     // B row t + 128
+            bool run = true;
+            for (int b = 0; b < nblocks && run; ++b) {
+                const uint32_t bg = Bk + b;
+                if (!tc::mbar_wait(&bars->xfull[bg & 1], (bg >> 1) & 1, WAIT_BUDGET)) {
+                    give_up(err, bars, 4);
                     break;
                 }
-                cur_b = b;
+                const float2* xsl = xs + (bg & 1) * XSLOT;
+                const int g_lo = b * (XB / GS), g_hi = min(ngroups, (b + 1) * (XB / GS));
+                for (int g = g_lo; g < g_hi; ++g) {
+                    const uint32_t Gg = G + g;
+                    if ((int)(Gg % NSET) != pset) continue;
+                    const int s = Gg % C::NSTAGE;
+                    if (Gg >= (uint32_t)C::NSTAGE &&
+                        !tc::mbar_wait(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
+                        give_up(err, bars, 1);
+                        run = false;
+                        break;
+                    }
+                    const float2* xb = xsl + xoff + (g * GS - b * XB);
+                    const int64_t n = n_beg + (int64_t)g * GS;
+                    float prA[8], piA[8], prB[8], piB[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
+                        if (n + i < n_end) {
+                            float2 x0 = xb[i];
+                            float2 xa = okA ? xb[i + mA] : make_float2(0.f, 0.f);
+                            float2 xv = same_lag ? xa : (okB ? xb[i + mB] : make_float2(0.f, 0.f));
+                            if (okA) pA = lag_product(xa, x0, cjA);
+                            if (okB) pB = lag_product(xv, x0, cjB);
+                        }
+                        prA[i] = pA.x; piA[i] = pA.y; prB[i] = pB.x; piB[i] = pB.y;
+                    }
+                    unsigned char* st = smem + s * stage_bytes<PREC>();
+                    unsigned char* sl = st + P_BYTES + W_BYTES;             // lo level
+                    uint32_t h[4], l[4];
+                    pack8<C::BF>(prA, h, l);
+                    st16(st + offA, h);
+                    if (C::BF) st16(sl + offA, l);
+                    pack8<C::BF>(piA, h, l);
+                    st16(st + offA + P_LBO, h);
+                    if (C::BF) st16(sl + offA + P_LBO, l);
+                    pack8<C::BF>(prB, h, l);
+                    st16(st + offB, h);
+                    if (C::BF) st16(sl + offB, l);
+                    pack8<C::BF>(piB, h, l);
+                    st16(st + offB + P_LBO, h);
+                    if (C::BF) st16(sl + offB + P_LBO, l);
+                    tc::fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bars->full[s]);
+                }
+                __syncwarp();
+                if (run && lane == 0) tc::mbar_arrive(&bars->xempty[bg & 1]);
             }
-            const float2* xb = xs + (b & 1) * XSLOT + (g * GS - b * XB);   // sample n_beg + 8g
-            float prA[8], piA[8], prB[8], piB[8];
-            const int64_t n = n_beg + (int64_t)g * GS;
+        } else if (warp < MMA_WARP) {
+            // -------------------------------------------------------- W warps (weights)
+            const int row = (warp - pset * SET_WARPS - P_WARPS) * 32 + lane;   // 0..127
+            const bool ok = it.u0 + row < it.Au;
+            const uint64_t phi = ok ? it.phi[it.u0 + row] : 0ull;
+            const uint64_t nb = it.nbase + (uint64_t)n_beg;
+            const uint32_t offW = (row / 8) * W_SBO + (row % 8) * 16;
+            // R_i = exp(-j 2 pi phi i / 2^64): the weights of a group are its anchor W_0 (from
+            // the exact u64 phase) times R_i, one sine/cosine pair per group instead of eight
+            float rr[8], ri[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
-                if (n + i < n_end) {
-                    float2 x0 = xb[i];
-                    float2 xa = okA ? xb[i + mA] : make_float2(0.f, 0.f);
-                    float2 xv = same_lag ? xa : (okB ? xb[i + mB] : make_float2(0.f, 0.f));
-                    if (okA) pA = lag_product(xa, x0, cjA);
-                    if (okB) pB = lag_product(xv, x0, cjB);
+                float2 r = phase_rot(phi, (uint64_t)i);
+                rr[i] = r.x;
+                ri[i] = r.y;
+            }
+            for (int g = 0; g < ngroups; ++g) {
+                const uint32_t Gg = G + g;
+                if ((int)(Gg % NSET) != pset) continue;
+                const int s = Gg % C::NSTAGE;
+                if (Gg >= (uint32_t)C::NSTAGE &&
+                    !tc::mbar_wait(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
+                    give_up(err, bars, 1);
+                    break;
                 }
-                prA[i] = pA.x; piA[i] = pA.y; prB[i] = pB.x; piB[i] = pB.y;
-            }
-            unsigned char* st = smem + s * stage_bytes<PREC>();
-            uint4 h, l;
-            pack8<C::BF>(prA, h, l);
-            st16(st + offA, h);
-            if (C::BF) st16(st + P_BYTES + W_BYTES + offA, l);
-            pack8<C::BF>(piA, h, l);
-            st16(st + offA + P_LBO, h);
-            if (C::BF) st16(st + P_BYTES + W_BYTES + offA + P_LBO, l);
-            pack8<C::BF>(prB, h, l);
-            st16(st + offB, h);
-            if (C::BF) st16(st + P_BYTES + W_BYTES + offB, l);
-            pack8<C::BF>(piB, h, l);
-            st16(st + offB + P_LBO, h);
-            if (C::BF) st16(st + P_BYTES + W_BYTES + offB + P_LBO, l);
-            tc::fence_async_smem();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&bars->full[s]);
-        }
-    } else if (warp < MMA_WARP) {
-        // ------------------------------------------------------------ W producers
-        const int t = tid - pset * 256 - 128;               // row 0..127
-        const bool ok = u0 + t < a.Au;
-        const uint64_t phi = ok ? a.phi[u0 + t] : 0ull;
-        const uint32_t offW = (t / 8) * W_SBO + (t % 8) * 16;
-        for (int g = pset; g < ngroups; g += NSET) {
-            const int s = g % C::NSTAGE;
-            if (g >= C::NSTAGE && !tc::mbar_wait(&bars->empty[s], ((g / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
-                flag_error(a, bars, 1);
-                break;
-            }
-            float wr[8], wi[8];
-            if (ok) {
-                // each weight straight from the exact u64 phase phi * n mod 2^64
-                const uint64_t n = a.nbase + (uint64_t)(n_beg + (int64_t)g * GS);
+                float wr[8], wi[8];
+                if (ok) {
+                    const float2 w0 = phase_rot(phi, nb + (uint64_t)g * GS);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    float2 w = phase_rot(phi, n + (uint64_t)i);
-                    wr[i] = w.x;
-                    wi[i] = w.y;
+                    for (int i = 0; i < 8; ++i) {
+                        wr[i] = w0.x * rr[i] - w0.y * ri[i];
+                        wi[i] = w0.x * ri[i] + w0.y * rr[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) { wr[i] = 0.f; wi[i] = 0.f; }
                 }
-            } else {
+                uint32_t rh[4], rl[4], ih[4], il[4], nh[4], nl[4];
+                pack8<C::BF>(wr, rh, rl);
+                pack8<C::BF>(wi, ih, il);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) { wr[i] = 0.f; wi[i] = 0.f; }
+                for (int k = 0; k < 4; ++k) {           // -Wi: round-to-nearest is odd-symmetric
+                    nh[k] = ih[k] ^ 0x80008000u;
+                    nl[k] = il[k] ^ 0x80008000u;
+                }
+                unsigned char* st = smem + s * stage_bytes<PREC>() + P_BYTES;
+                st16(st + offW + 0 * W_LBO, ih);
+                st16(st + offW + 1 * W_LBO, rh);
+                st16(st + offW + 2 * W_LBO, nh);
+                if (C::BF) {
+                    unsigned char* sl = st + P_BYTES + W_BYTES;
+                    st16(sl + offW + 0 * W_LBO, il);
+                    st16(sl + offW + 1 * W_LBO, rl);
+                    st16(sl + offW + 2 * W_LBO, nl);
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bars->full[s]);
             }
-            unsigned char* st = smem + s * stage_bytes<PREC>() + P_BYTES;
-            uint4 rh, rl, ih, il;
-            pack8<C::BF>(wr, rh, rl);
-            pack8<C::BF>(wi, ih, il);
-            st16(st + offW + 0 * W_LBO, ih);
-            st16(st + offW + 1 * W_LBO, rh);
-            st16(st + offW + 2 * W_LBO, neg8(ih));
-            if (C::BF) {
-                unsigned char* sl = st + P_BYTES + W_BYTES;
-                st16(sl + offW + 0 * W_LBO, il);
-                st16(sl + offW + 1 * W_LBO, rl);
-                st16(sl + offW + 2 * W_LBO, neg8(il));
+        } else if (warp == LOAD_WARP && lane == 0) {
+            // -------------------------------------------------------- sample loader (TMA)
+            for (int b = 0; b < nblocks; ++b) {
+                const uint32_t bg = Bk + b;
+                const int slot = bg & 1;
+                if (bg >= 2 && !tc::mbar_wait(&bars->xempty[slot], ((bg >> 1) - 1) & 1, WAIT_BUDGET)) {
+                    give_up(err, bars, 5);
+                    break;
+                }
+                const int64_t ns = n_beg + (int64_t)b * XB - xoff;   // even
+                int64_t cnt = ((int64_t)XB + mpad + xoff + 1) & ~(int64_t)1;
+                if (cnt > it.x_avail - ns) cnt = it.x_avail - ns;
+                tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)(cnt * 8));
+                const uint64_t pos = (uint64_t)ns & it.xmask;
+                const uint64_t room = it.xmask - pos + 1;       // samples before the ring wraps
+                if (it.xmask == ~0ull || (uint64_t)cnt <= room) {
+                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(cnt * 8), &bars->xfull[slot]);
+                } else {
+                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(room * 8), &bars->xfull[slot]);
+                    tc::bulk_g2s(xs + slot * XSLOT + room, it.x, (uint32_t)((cnt - room) * 8), &bars->xfull[slot]);
+                }
+                lastb = (int)bg;
             }
-            tc::fence_async_smem();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&bars->full[s]);
+        } else if (warp == MMA_WARP && lane == 0) {
+            // -------------------------------------------------------- MMA issuer
+            constexpr uint32_t idesc = tc::idesc_f16(BM, BN, C::BF);
+            const uint32_t pbase = tc::smem_u32(smem);
+            for (int g = 0; g < ngroups; ++g) {
+                const uint32_t Gg = G + g;
+                const int s = Gg % C::NSTAGE;
+                if (!tc::mbar_wait(&bars->full[s], (Gg / C::NSTAGE) & 1, WAIT_BUDGET)) {
+                    give_up(err, bars, 2);
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t sb = pbase + s * stage_bytes<PREC>();
+#pragma unroll
+                for (int p = 0; p < C::NPASS; ++p) {
+                    const int la = (p == 2) ? 1 : 0, lb = (p == 1) ? 1 : 0;
+                    const uint32_t pb = sb + lb * (P_BYTES + W_BYTES);
+                    const uint32_t wb = sb + la * (P_BYTES + W_BYTES) + P_BYTES;
+                    const uint64_t bdesc = tc::smem_desc(pb, P_LBO, P_SBO);
+                    const uint64_t ar = tc::smem_desc(wb + 1 * W_LBO, W_LBO, W_SBO);
+                    const uint64_t ai = tc::smem_desc(wb + 0 * W_LBO, W_LBO, W_SBO);
+                    const uint32_t acc = (g > 0 || p > 0) ? 1u : 0u;
+                    tc::mma_f16(tmem + TM_DR, ar, bdesc, idesc, acc);
+                    tc::mma_f16(tmem + TM_DI, ai, bdesc, idesc, acc);
+                }
+                tc::mma_commit(&bars->empty[s]);
+            }
+            tc::mma_commit(&bars->done);
         }
-    } else if (warp == LOAD_WARP && lane == 0) {
-        // ------------------------------------------------------------ sample loader (TMA)
-        int last = -1;
-        for (int b = 0; b < nblocks; ++b) {
-            const int slot = b & 1;
-            if (b >= 2 && !tc::mbar_wait(&bars->xempty[slot], ((b >> 1) - 1) & 1, WAIT_BUDGET)) {
-                flag_error(a, bars, 5);
-                break;
-            }
-            const int64_t ns = n_beg + (int64_t)b * XB;
-            int64_t cnt = (int64_t)XB + mpad;
-            if (cnt > a.x_avail - ns) cnt = a.x_avail - ns;
-            cnt &= ~(int64_t)1;
-            tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)(cnt * 8));
-            tc::bulk_g2s(xs + slot * XSLOT, a.x + ns, (uint32_t)(cnt * 8), &bars->xfull[slot]);
-            last = b;
-        }
-        // no copy may still be landing when the CTA exits
-        for (int b = last > 0 ? last - 1 : 0; b <= last; ++b)
-            if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET);
-    } else if (warp == MMA_WARP && lane == 0) {
-        // ------------------------------------------------------------ MMA issuer
-        constexpr uint32_t idesc = tc::idesc_f16(BM, BN, C::BF);
-        const uint32_t base = tc::smem_u32(smem);
-        for (int g = 0; g < ngroups; ++g) {
-            const int s = g % C::NSTAGE;
-            if (!tc::mbar_wait(&bars->full[s], (g / C::NSTAGE) & 1, WAIT_BUDGET)) {
-                flag_error(a, bars, 2);
-                break;
-            }
+
+        // ------------------------------------------------------------ epilogue (set 0 W warps)
+        if (warp >= P_WARPS && warp < SET_WARPS) {
+            const bool got = tc::mbar_wait(&bars->done, nit & 1, WAIT_BUDGET);
+            if (!got) give_up(err, bars, 3);
             tc::tc_fence_after();
-            const uint32_t sb = base + s * stage_bytes<PREC>();
+            const int q = warp & 3;
+            const int row = q * 32 + lane;
+            const bool live = got && ngroups > 0 && !bars->abort;
+            const bool vec = (it.out_stride & 1) == 0;
+            float2* out = it.out + (size_t)row * it.out_stride;
+            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+            for (int cb = 0; cb < 8; ++cb) {
+                uint32_t dr0[16], di0[16], dr1[16], di1[16];
+                tc::tmem_ld16(lane_addr + TM_DR + cb * 16, dr0);
+                tc::tmem_ld16(lane_addr + TM_DI + cb * 16, di0);
+                tc::tmem_ld16(lane_addr + TM_DR + 128 + cb * 16, dr1);
+                tc::tmem_ld16(lane_addr + TM_DI + 128 + cb * 16, di1);
+                tc::tmem_ld_wait();
+                if (it.u0 + row >= it.Au) continue;
 #pragma unroll
-            for (int p = 0; p < C::NPASS; ++p) {
-                const int la = (p == 2) ? 1 : 0, lb = (p == 1) ? 1 : 0;
-                const uint32_t pb = sb + lb * (P_BYTES + W_BYTES);
-                const uint32_t wb = sb + la * (P_BYTES + W_BYTES) + P_BYTES;
-                const uint64_t bdesc = tc::smem_desc(pb, P_LBO, P_SBO);
-                const uint64_t ar = tc::smem_desc(wb + 1 * W_LBO, W_LBO, W_SBO);
-                const uint64_t ai = tc::smem_desc(wb + 0 * W_LBO, W_LBO, W_SBO);
-                const uint32_t acc = (g > 0 || p > 0) ? 1u : 0u;
-                tc::mma_f16(tmem, ar, bdesc, idesc, acc);
-                tc::mma_f16(tmem + 256, ai, bdesc, idesc, acc);
+                for (int j = 0; j < 16; ++j) {
+                    const int r = cb * 16 + j;               // B rows r, r + 128 <-> tile columns 2r, 2r+1
+                    const int c = 2 * r;
+                    float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
+                                                  __uint_as_float(dr1[j]), __uint_as_float(di1[j]))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (vec && it.c0 + c + 1 < it.ncols) {
+                        *reinterpret_cast<float4*>(&out[c]) = v;
+                    } else {
+                        if (it.c0 + c < it.ncols) out[c] = make_float2(v.x, v.y);
+                        if (it.c0 + c + 1 < it.ncols) out[c + 1] = make_float2(v.z, v.w);
+                    }
+                }
             }
-            tc::mma_commit(&bars->empty[s]);
         }
-        tc::mma_commit(&bars->done);
+        G += ngroups;
+        Bk += nblocks;
+        ++nit;
+        // everybody is done with this item's descriptor before thread 0 replaces it
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
     }
 
-    // ---------------------------------------------------------------- epilogue (warps 4-7)
-    if (warp >= 4 && warp < 8) {
-        const bool got = tc::mbar_wait(&bars->done, 0, WAIT_BUDGET);
-        if (!got) flag_error(a, bars, 3);
-        tc::tc_fence_after();
-        const int q = warp & 3;                  // TMEM lane quadrant
-        const int row = q * 32 + lane;
-        const int u = u0 + row;
-        float2* out = a.part + ((size_t)blockIdx.z * a.Au + (size_t)(u < a.Au ? u : 0)) * a.ncols;
-        const bool vec = (a.ncols & 1) == 0;     // rows start 16-byte aligned
-        for (int cb = 0; cb < 8; ++cb) {
-            uint32_t dr0[16], di0[16], dr1[16], di1[16];
-            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-            tc::tmem_ld16(lane_addr + cb * 16, dr0);
-            tc::tmem_ld16(lane_addr + 256 + cb * 16, di0);
-            tc::tmem_ld16(lane_addr + 128 + cb * 16, dr1);
-            tc::tmem_ld16(lane_addr + 384 + cb * 16, di1);
-            tc::tmem_ld_wait();
-            if (u >= a.Au) continue;
-            const bool live = got && ngroups > 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int r = cb * 16 + j;               // B-operand rows r, r + 128 <-> columns 2r, 2r+1
-                const int c = c0 + 2 * r;
-                float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                              __uint_as_float(dr1[j]), __uint_as_float(di1[j]))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (vec && c + 1 < a.ncols) {
-                    *reinterpret_cast<float4*>(&out[c]) = v;
-                } else {
-                    if (c < a.ncols) out[c] = make_float2(v.x, v.y);
-                    if (c + 1 < a.ncols) out[c + 1] = make_float2(v.z, v.w);
-                }
-            }
-        }
-    }
+    // no sample copy may still be landing when the CTA exits
+    if (warp == LOAD_WARP && lane == 0)
+        for (int b = lastb > 0 ? lastb - 1 : 0; b <= lastb; ++b)
+            if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == MMA_WARP) {
@@ -362,26 +455,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) proj_tc_kernel(ProjArgs a)
 
 int tiles_of(int Au, int ncols) { return ((Au + BM - 1) / BM) * ((ncols + BN - 1) / BN); }
 
-template <int PREC>
-cudaError_t launch(const ProjArgs& a, cudaStream_t st)
+template <int PREC, bool LIST>
+cudaError_t set_smem()
 {
-    static bool attr_set[64] = {false};
+    static bool done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_bytes<PREC>());
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
+    if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes<PREC>());
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+template <int PREC>
+cudaError_t launch_grid(const ProjArgs& a, cudaStream_t st)
+{
+    cudaError_t e = set_smem<PREC, false>();
+    if (e != cudaSuccess) return e;
     dim3 grid((a.Au + BM - 1) / BM, (a.ncols + BN - 1) / BN, a.nsplit);
-    proj_tc_kernel<PREC><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(a);
+    proj_tc_kernel<PREC, false><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(a, nullptr, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_list(const TcItem* items, const int* nitems, int* counter, int grid, int* err, cudaStream_t st)
+{
+    cudaError_t e = set_smem<PREC, true>();
+    if (e != cudaSuccess) return e;
+    ProjArgs none;
+    none.x = nullptr; none.nc = 0; none.nbase = 0; none.phi = nullptr; none.Au = 0; none.col_lag = nullptr;
+    none.col_conj = nullptr; none.ncols = 0; none.nsplit = 0; none.split_len = 0; none.part = nullptr;
+    proj_tc_kernel<PREC, true><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(none, items, nitems, counter, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_supported(int ncols, int M) { return ncols > 0 && M >= 0 && M <= MAX_LAG; }
+
+int tc_tile_rows() { return BM; }
+int tc_tile_cols() { return BN; }
 
 ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms)
 {
@@ -406,8 +520,16 @@ size_t tc_max_partials(int Au, int ncols, int num_sms)
 
 cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st)
 {
-    if (precision == CYC_P_FP16) return launch<CYC_P_FP16>(a, st);
-    if (precision == CYC_P_BF16X3) return launch<CYC_P_BF16X3>(a, st);
+    if (precision == CYC_P_FP16) return launch_grid<CYC_P_FP16>(a, st);
+    if (precision == CYC_P_BF16X3) return launch_grid<CYC_P_BF16X3>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision,
+                            int* err, cudaStream_t st)
+{
+    if (precision == CYC_P_FP16) return launch_list<CYC_P_FP16>(items, nitems, counter, grid, err, st);
+    if (precision == CYC_P_BF16X3) return launch_list<CYC_P_BF16X3>(items, nitems, counter, grid, err, st);
     return cudaErrorInvalidValue;
 }
 

@@ -45,6 +45,22 @@ def test_params_struct_layout_matches_c(tmp_path):
                    P.cuda_stream.offset, P.device.offset]
 
 
+def test_server_structs_match_c(tmp_path):
+    src = tmp_path / "lay2.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cyc.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cyc_server_params),'
+                   'offsetof(cyc_server_params, mem_budget), offsetof(cyc_server_params, ring_samples),'
+                   'offsetof(cyc_server_params, max_items), offsetof(cyc_server_params, item_samples),'
+                   'offsetof(cyc_server_params, device), sizeof(cyc_done), offsetof(cyc_done, tag),'
+                   'offsetof(cyc_done, done_s)); return 0; }\n')
+    exe = tmp_path / "lay2"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    P, D = _cyc.cyc_server_params, _cyc.cyc_done
+    assert got == [ctypes.sizeof(P), P.mem_budget.offset, P.ring_samples.offset, P.max_items.offset,
+                   P.item_samples.offset, P.device.offset, ctypes.sizeof(D), D.tag.offset, D.done_s.offset]
+
+
 def test_status_strings_and_no_device_error(lib):
     assert pkg.cyc_strerror(-1) == "invalid argument"
     assert pkg.cyc_strerror(-6).startswith("no data")
