@@ -169,6 +169,104 @@ def sampled_error(R, x, lags, alphas, nent=8, seed=3):
     return float(np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, M))
 
 
+# --------------------------------------------------------------------------- serving leg
+
+SRV_STREAMS, SRV_LAGS, SRV_ALPHAS = 256, 64, 512
+SRV_CMAC_PER_SAMPLE = SRV_LAGS * SRV_ALPHAS * 2
+
+
+def serving_leg(pkg, seconds=3.0, loads=(0.5, 0.9), nbase=16, blen=3 << 19):
+    """Config 3: 256 streams of mixed GMSK / RRC-PSK signals, lags 0..63, 512 cycle
+    frequencies, both forms, continuously batched.  Chunk lengths are log-uniform in
+    [4096, 2^20]; per-stream rates are log-uniform over 100x and arrivals Poisson.  A
+    saturation run measures capacity, then runs at fractions of it give submit-to-done
+    latency percentiles.  Stream s draws its chunks from base signal s % 16."""
+    import heapq
+
+    import torch
+    from synth import workloads
+    bases = [torch.from_numpy(workloads.mix_stream(b, blen).view(np.float32)).pin_memory() for b in range(nbase)]
+    lags = np.arange(SRV_LAGS)
+    alphas = -0.5 + np.arange(SRV_ALPHAS) / SRV_ALPHAS
+    rng = np.random.default_rng(0xC7C1_0003)
+    w = 100.0 ** rng.uniform(0.0, 1.0, SRV_STREAMS)
+    w /= w.sum()
+    lo, hi = np.log(4096.0), np.log(float(1 << 20))
+    mean_chunk = (np.exp(hi) - np.exp(lo)) / (hi - lo)
+    out = {"streams": SRV_STREAMS, "lags": SRV_LAGS, "cycle_freqs": SRV_ALPHAS, "forms": 2,
+           "precision": "bf16x3", "chunk": "log-uniform [4096, 1048576]", "rates": "log-uniform over 100x, Poisson"}
+    with pkg.Server(max_streams=SRV_STREAMS, precision="bf16x3", ring_samples=1 << 22) as srv:
+        sids = [srv.open(lags, alphas, pkg.CYC_BOTH) for _ in range(SRV_STREAMS)]
+        pos = [0] * SRV_STREAMS
+
+        def submit(i, n, tag):
+            b = bases[i % nbase]
+            off = pos[i] % (blen - (1 << 20))
+            pos[i] += n
+            srv.submit(sids[i], b.data_ptr() + 8 * off, n, tag)
+
+        def run(rate_chunks, dur):
+            """rate_chunks None: saturation (every stream always has work queued)."""
+            t0 = time.perf_counter()
+            done, subm, eagain, tag = [], 0, 0, 0
+            events = []
+            if rate_chunks is not None:
+                for i in range(SRV_STREAMS):
+                    heapq.heappush(events, (t0 + rng.exponential(1.0 / (rate_chunks * w[i])), i))
+            b0 = srv.stats()
+            while True:
+                now = time.perf_counter()
+                if now - t0 > dur:
+                    break
+                if rate_chunks is None:
+                    i = int(rng.choice(SRV_STREAMS, p=w))
+                else:
+                    t_ev, i = events[0]
+                    if t_ev > now:
+                        done += srv.poll()
+                        time.sleep(min(0.0005, t_ev - now))
+                        continue
+                    heapq.heapreplace(events, (t_ev + rng.exponential(1.0 / (rate_chunks * w[i])), i))
+                n = int(np.exp(rng.uniform(lo, hi)))
+                try:
+                    submit(i, n, tag)
+                    subm += 1
+                    tag += 1
+                except pkg.CycError as e:
+                    if e.code != pkg.CYC_EAGAIN:
+                        raise
+                    eagain += 1
+                    done += srv.poll()
+                if tag % 64 == 0:
+                    done += srv.poll()
+            srv.drain(300)
+            t1 = time.perf_counter()
+            done += srv.poll(1 << 20)
+            b1 = srv.stats()
+            lat = np.array([d[5] - d[4] for d in done]) * 1e3
+            nsamp = sum(d[3] for d in done)
+            busy = (b1[2] - b0[2]) / 1e3
+            return {"seconds": t1 - t0, "chunks": len(done), "submitted": subm, "eagain": eagain,
+                    "msamples_s": nsamp / (t1 - t0) / 1e6, "gmac_s": nsamp * SRV_CMAC_PER_SAMPLE / (t1 - t0) / 1e9,
+                    "gpu_busy_frac": busy / (t1 - t0), "batches": b1[0] - b0[0], "items": b1[1] - b0[1],
+                    "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                    "p99_ms": float(np.percentile(lat, 99)) if lat.size else None}
+
+        run(None, 0.5)                                   # warm-up
+        sat = run(None, seconds)
+        out["saturation"] = sat
+        cap = sat["msamples_s"] * 1e6
+        out["capacity_msamples_s"] = sat["msamples_s"]
+        res = []
+        for ld in loads:
+            r = run(ld * cap / mean_chunk, seconds)
+            r["offered_load"] = ld
+            r["offered_msamples_s"] = ld * cap / 1e6
+            res.append(r)
+        out["loads"] = res
+    return out
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -344,6 +442,9 @@ def run_ours(args):
         line["plain_fp32"] = {"value": cmac_per_step() / (ms32 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms32,
                               "steps": k, "err_rel_r00": sampled_error(R32, x, lags, alphas)}
         line["speedup_vs_plain_fp32"] = value / world / line["plain_fp32"]["value"]
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_leg(pkg, seconds=args.serving_seconds)
+        line["p99_ms"] = line["serving"]["loads"][-1]["p99_ms"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
@@ -369,6 +470,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=3.0)
+    ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")
     args = ap.parse_args()
@@ -377,6 +481,13 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     ARGS_SAMPLES[0] = args.samples
+    if args.serving_only:
+        import torch
+        import paper_2405_16911_gb300 as pkg
+        torch.cuda.set_device(0)
+        pkg.load()
+        print(json.dumps(serving_leg(pkg, seconds=args.serving_seconds)))
+        return 0
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -204,8 +204,12 @@ int alloc_state(cyc_stream* s)
     CK(cudaMemcpy(s->d_col_lag, cl.data(), s->ncols * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&s->d_col_conj, s->ncols * sizeof(int8_t)));
     CK(cudaMemcpy(s->d_col_conj, cc.data(), s->ncols * sizeof(int8_t), cudaMemcpyHostToDevice));
-    s->part_elems = s->precision == CYC_P_FP32 ? fp32_max_partials(s->Au, s->ncols, s->num_sms)
-                                               : tc_max_partials(s->Au, s->ncols, s->num_sms);
+    if (s->precision != CYC_P_FP32)
+        s->part_elems = tc_max_partials(s->Au, s->ncols, s->num_sms);
+    else if (small_supported(s->Au))
+        s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
+    else
+        s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
     CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
     CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
     CK(cudaMalloc(&s->d_err, sizeof(int)));
@@ -229,8 +233,11 @@ int project(cyc_stream* s, int64_t nc)
     a.err = s->d_err;
     a.M = s->M;
     a.x_avail = (s->M + s->max_chunk + kStagePad) & ~(int64_t)1;
-    ProjPlan pl = s->precision == CYC_P_FP32 ? fp32_plan(s->Au, s->ncols, nc, s->num_sms)
-                                             : tc_plan(s->Au, s->ncols, nc, s->num_sms);
+    // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
+    const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
+    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms)
+                  : small                    ? small_plan(s->Au, s->ncols, nc, s->num_sms)
+                                             : fp32_plan(s->Au, s->ncols, nc, s->num_sms);
     a.nsplit = pl.nsplit;
     a.split_len = pl.split_len;
     if ((size_t)pl.nsplit * s->Au * s->ncols > s->part_elems)
@@ -246,7 +253,9 @@ int project(cyc_stream* s, int64_t nc)
         }
         CK(cudaEventRecord(ev.first, s->st));
     }
-    CK(s->precision == CYC_P_FP32 ? fp32_launch(a, s->st) : tc_launch(a, s->precision, s->st));
+    CK(s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->st)
+       : small                    ? small_launch(a, s->st)
+                                  : fp32_launch(a, s->st));
     if (s->prof) {
         CK(cudaEventRecord(ev.second, s->st));
         s->ev_pending.push_back(ev);

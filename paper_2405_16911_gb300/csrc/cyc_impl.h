@@ -61,6 +61,13 @@ ProjPlan    fp32_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st);
 size_t      fp32_max_partials(int Au, int ncols, int num_sms);   // float2 elements
 
+// FP32 projection for at most 16 distinct cycle frequencies: per-thread register sums and
+// a warp-shuffle fold (proj_small.cu).
+bool        small_supported(int Au);
+ProjPlan    small_plan(int Au, int ncols, int64_t nc, int num_sms);
+cudaError_t small_launch(const ProjArgs& a, cudaStream_t st);
+size_t      small_max_partials(int Au, int ncols, int num_sms);
+
 // Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu).
 bool        tc_supported(int ncols, int M);
 ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);

@@ -1,0 +1,138 @@
+// proj_small.cu -- FP32 a-projection for a handful of distinct cycle frequencies.
+//
+// When only a few a are distinct (Au <= 16), a 128-row GEMM tile would be almost empty.
+// Here every thread keeps the complex sums of all Au cycle frequencies x CB columns in
+// registers while it walks its own strided samples (x[n] and x[n+m] are read once per
+// sample for all of them), and the block then folds its threads' sums with warp shuffles
+// and shared memory into one FP32 partial per (split, a, column).  Same arithmetic as the
+// GEMM path: lag products of Eqs. (ACF-def)/(CCF-def), weights exp(-j 2 pi phi n / 2^64)
+// from the exact u64 phase (Sec. 4 Set mode, per-alpha projection).
+#include "cyc_device.cuh"
+#include "cyc_impl.h"
+
+namespace cyc {
+namespace {
+
+constexpr int NT = 256;
+
+template <int AU, int CB>
+__global__ void __launch_bounds__(NT) proj_small_kernel(ProjArgs a)
+{
+    __shared__ float red[NT / 32][2 * AU * CB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.x * CB;
+    const int64_t n_beg = (int64_t)blockIdx.y * a.split_len;
+    int64_t n_end = n_beg + a.split_len;
+    if (n_end > a.nc) n_end = a.nc;
+
+    uint64_t phi[AU];
+#pragma unroll
+    for (int u = 0; u < AU; ++u) phi[u] = u < a.Au ? a.phi[u] : 0ull;
+    int lag[CB];
+    bool cj[CB], okc[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+        okc[j] = c0 + j < a.ncols;
+        lag[j] = okc[j] ? a.col_lag[c0 + j] : 0;
+        cj[j] = okc[j] && a.col_conj[c0 + j];
+    }
+    float sr[AU][CB], si[AU][CB];
+#pragma unroll
+    for (int u = 0; u < AU; ++u)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) { sr[u][j] = 0.f; si[u][j] = 0.f; }
+
+    for (int64_t n = n_beg + tid; n < n_end; n += NT) {
+        const float2 x0 = __ldg(&a.x[n]);
+        float2 p[CB];
+#pragma unroll
+        for (int j = 0; j < CB; ++j)
+            p[j] = okc[j] ? lag_product(__ldg(&a.x[n + lag[j]]), x0, cj[j]) : make_float2(0.f, 0.f);
+        const uint64_t nabs = a.nbase + (uint64_t)n;
+#pragma unroll
+        for (int u = 0; u < AU; ++u) {
+            const float2 w = phase_rot(phi[u], nabs);
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                sr[u][j] = fmaf(w.x, p[j].x, fmaf(-w.y, p[j].y, sr[u][j]));
+                si[u][j] = fmaf(w.x, p[j].y, fmaf(w.y, p[j].x, si[u][j]));
+            }
+        }
+    }
+    // fold the block: warp shuffles, then the eight warps through shared memory
+#pragma unroll
+    for (int u = 0; u < AU; ++u)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            float vr = sr[u][j], vi = si[u][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vr += __shfl_xor_sync(0xffffffffu, vr, o);
+                vi += __shfl_xor_sync(0xffffffffu, vi, o);
+            }
+            if (lane == 0) {
+                red[warp][2 * (u * CB + j)] = vr;
+                red[warp][2 * (u * CB + j) + 1] = vi;
+            }
+        }
+    __syncthreads();
+    for (int e = tid; e < AU * CB; e += NT) {
+        const int u = e / CB, j = e % CB;
+        if (u >= a.Au || !(c0 + j < a.ncols)) continue;
+        float vr = 0.f, vi = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            vr += red[w][2 * e];
+            vi += red[w][2 * e + 1];
+        }
+        a.part[((size_t)blockIdx.y * a.Au + u) * a.ncols + c0 + j] = make_float2(vr, vi);
+    }
+}
+
+template <int AU, int CB>
+cudaError_t launch(const ProjArgs& a, cudaStream_t st)
+{
+    dim3 grid((a.ncols + CB - 1) / CB, a.nsplit);
+    proj_small_kernel<AU, CB><<<grid, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int au_class(int Au) { return Au <= 1 ? 1 : Au <= 2 ? 2 : Au <= 4 ? 4 : Au <= 8 ? 8 : 16; }
+int cb_of(int Au) { return 64 / au_class(Au) > 32 ? 32 : 64 / au_class(Au); }
+
+}  // namespace
+
+bool small_supported(int Au) { return Au >= 1 && Au <= 16; }
+
+ProjPlan small_plan(int Au, int ncols, int64_t nc, int num_sms)
+{
+    const int cbs = (ncols + cb_of(Au) - 1) / cb_of(Au);
+    int want = (2 * num_sms + cbs - 1) / cbs;       // about two blocks per SM
+    int64_t len = (nc + want - 1) / want;
+    if (len < 4 * NT) len = 4 * NT;
+    ProjPlan p;
+    p.split_len = len;
+    p.nsplit = (int)((nc + len - 1) / len);
+    if (p.nsplit < 1) p.nsplit = 1;
+    return p;
+}
+
+size_t small_max_partials(int Au, int ncols, int num_sms)
+{
+    const int cbs = (ncols + cb_of(Au) - 1) / cb_of(Au);
+    size_t want = (size_t)((2 * num_sms + cbs - 1) / cbs);
+    return want * (size_t)Au * (size_t)ncols;
+}
+
+cudaError_t small_launch(const ProjArgs& a, cudaStream_t st)
+{
+    switch (au_class(a.Au)) {
+    case 1: return launch<1, 32>(a, st);
+    case 2: return launch<2, 32>(a, st);
+    case 4: return launch<4, 16>(a, st);
+    case 8: return launch<8, 8>(a, st);
+    default: return launch<16, 4>(a, st);
+    }
+}
+
+}  // namespace cyc

@@ -253,3 +253,16 @@ def test_tensor_core_lag_limit(cyc, precision):
     with pytest.raises(cyc.CycError) as e:
         cyc.Stream([0, 2561], [0.1], cyc.CYC_BOTH, precision=precision)
     assert e.value.code == cyc.CYC_ENOTSUP
+
+
+@pytest.mark.parametrize("na", [1, 2, 5, 8, 16, 17])
+def test_fp32_small_and_general_paths(cyc, na):
+    """FP32 with at most 16 distinct cycle frequencies takes the register/warp-shuffle path,
+    17 and more the GEMM-tiled one; both match the oracle on ragged column counts."""
+    x = synth.white(12007, seed=111).astype(np.complex64)
+    lags = np.array([0, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89])
+    alphas = np.linspace(-0.45, 0.45, na) if na > 1 else np.array([0.2])
+    R, neff = run_gpu(cyc, x, lags, alphas, chunks=[3001, 9006])
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert neff == no
+    assert rel_err(R, Ro, x, 89) < 1e-5
