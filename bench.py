@@ -42,7 +42,9 @@ TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per projection launch from one ncu capture,
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu file).
-TRAFFIC = {}
+TRAFFIC = {
+    "proj_tc@3ea3124d93ef": 643584 + 94208,     # profiles/proj_tc_bf16x3_cfg1_ncu.md
+}
 
 
 def workload_config(precision):
