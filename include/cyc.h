@@ -231,6 +231,58 @@ CYC_API int cyc_server_close(cyc_server* srv, int sid);
 CYC_API int cyc_server_stats(cyc_server* srv, int64_t* batches, int64_t* items, double* busy_ms,
                              uint64_t* bytes_held);
 
+/* ======================================================================================
+ * Learned cycle-frequency proposer.
+ *
+ * The paper's future work is the estimation of cycle frequencies themselves (Sec. 6);
+ * here a small net proposes, from cheap spectra, which cycle frequencies of the 512-bin
+ * grid a = -1/2 + k/512 carry lines, so that the estimator (Sec. 4) runs at those few
+ * instead of the full grid -- and falls back to the full grid when it is unsure.
+ *
+ * Features (cyc_features): for each signal, Welch-averaged periodograms (16 segments of
+ * 4096 samples, Hann window) of x, x^2 and |x|^2 -- the lag-0 products whose spectral
+ * lines are the conventional and conjugate cycle frequencies (Sec. 2) -- as log10, bin j
+ * at frequency -1/2 + j/4096, each channel standardised; FP16 [nsig][3][4096].
+ * Net: circular 1-D convolutions, kernel 9, 3 -> 64 -> 64 -> 64 -> 2 channels, ReLU after
+ * the first three, mean over groups of 8 bins: logits [B][form][512] (CONV, CONJ).  FP16
+ * weights and activations, FP32 sums; parameters as one flat FP32 vector
+ * (W1 b1 W2 b2 W3 b3 W4 b4, W[out][in][9]) of cyc_net_nparams() values.
+ * Training minimises the mean binary cross-entropy with logits (positives weighted by
+ * pos_weight) against labels [B][form][512] in {0, 1}, with Adam (0.9, 0.999, 1e-8).
+ * ====================================================================================== */
+typedef struct cyc_net cyc_net;
+
+/* params: cyc_net_nparams() FP32 values, or NULL for seeded He-normal weights, zero biases. */
+CYC_API int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out);
+CYC_API int cyc_net_destroy(cyc_net* n);
+CYC_API int cyc_net_nparams(void);
+CYC_API int cyc_net_get_params(cyc_net* n, float* out);           /* host, nparams floats */
+CYC_API int cyc_net_set_params(cyc_net* n, const float* params);  /* host; resets Adam state */
+
+/* Features of nsig signals stored back to back in device memory (signal s at x + s*T
+ * complex64 samples, T >= 65536; the first 65536 are used) into device FP16 `feats`. */
+CYC_API int cyc_features(const void* x, int64_t T, int nsig, void* feats);
+
+/* Logits of B feature sets (device pointers): logits [B][2][512] FP32. */
+CYC_API int cyc_net_forward(cyc_net* n, const void* feats, int B, float* logits);
+
+/* Loss and parameter gradients for a batch (device feats and labels); grads (host,
+ * nparams floats) and loss (host) may be NULL.  No update. */
+CYC_API int cyc_net_gradients(cyc_net* n, const void* feats, const float* labels, int B, float pos_weight,
+                              float* grads, float* loss);
+
+/* One Adam step on a batch; *loss (host, optional) receives the batch loss before the step. */
+CYC_API int cyc_net_train_step(cyc_net* n, const void* feats, const float* labels, int B, float lr,
+                               float pos_weight, float* loss);
+
+/* Proposals for one signal (host or device, >= 65536 samples): the k most likely grid
+ * cycle frequencies of each form into alphas_conv[k] and alphas_conj[k] (host), the
+ * confidence (share of the predicted probability mass inside the chosen bins, the lower
+ * of the two forms), and *used_fallback = 1 when the confidence is below tau or more
+ * than k bins of a form are predicted on: the caller should then run the full grid. */
+CYC_API int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, float tau,
+                        double* alphas_conv, double* alphas_conj, float* conf, int* used_fallback);
+
 /*
  * cyc_estimate_static: a one-shot estimate over x[0..T) that allocates no memory at all.
  * The paper has no counterpart; it exists for callers that cannot call cudaMalloc when

@@ -11,4 +11,7 @@ from ._cyc import (CycError, Stream, load, declared_functions, LIB_PATH, HEADER,
 from ._cyc import (Server, cyc_server_create, cyc_server_destroy, cyc_server_open,  # noqa: F401
                    cyc_server_submit, cyc_server_poll, cyc_server_drain, cyc_server_read, cyc_server_close,
                    cyc_server_stats)
+from ._cyc import (cyc_net_create, cyc_net_destroy, cyc_net_nparams, cyc_net_get_params,  # noqa: F401
+                   cyc_net_set_params, cyc_features, cyc_net_forward, cyc_net_gradients, cyc_net_train_step,
+                   cyc_propose)
 from .build import build  # noqa: F401

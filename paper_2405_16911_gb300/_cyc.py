@@ -97,6 +97,16 @@ def load(path: str = LIB_PATH):
         "cyc_server_read": ([P, I, P, P], I),
         "cyc_server_close": ([P, I], I),
         "cyc_server_stats": ([P, P, P, P, P], I),
+        "cyc_net_create": ([P, ctypes.c_uint64, I, P], I),
+        "cyc_net_destroy": ([P], I),
+        "cyc_net_nparams": ([], I),
+        "cyc_net_get_params": ([P, P], I),
+        "cyc_net_set_params": ([P, P], I),
+        "cyc_features": ([P, I64, I, P], I),
+        "cyc_net_forward": ([P, P, I, P], I),
+        "cyc_net_gradients": ([P, P, P, I, ctypes.c_float, P, P], I),
+        "cyc_net_train_step": ([P, P, P, I, ctypes.c_float, ctypes.c_float, P], I),
+        "cyc_propose": ([P, P, I64, I, I, ctypes.c_float, P, P, P, P], I),
         "cyc_strerror": ([I], ctypes.c_char_p),
         "cyc_last_error": ([], ctypes.c_char_p),
     }
@@ -388,6 +398,88 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- proposer
+
+def cyc_net_nparams() -> int:
+    return int(load().cyc_net_nparams())
+
+
+def cyc_net_create(params=None, seed: int = 0, device: int = 0) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    if params is not None:
+        params = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if params.size != cyc_net_nparams():
+            raise ValueError("expected %d parameters" % cyc_net_nparams())
+    _check(lib.cyc_net_create(params.ctypes.data if params is not None else None, int(seed), device, ctypes.byref(h)))
+    return h.value
+
+
+def cyc_net_destroy(n: int) -> None:
+    if n:
+        _check(load().cyc_net_destroy(n))
+
+
+def cyc_net_get_params(n: int) -> np.ndarray:
+    out = np.empty(cyc_net_nparams(), dtype=np.float32)
+    _check(load().cyc_net_get_params(n, out.ctypes.data))
+    return out
+
+
+def cyc_net_set_params(n: int, params) -> None:
+    params = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if params.size != cyc_net_nparams():
+        raise ValueError("expected %d parameters" % cyc_net_nparams())
+    _check(load().cyc_net_set_params(n, params.ctypes.data))
+
+
+def cyc_features(x, T: int, nsig: int, feats) -> None:
+    """x: device complex64 signals back to back (T samples each); feats: device FP16 [nsig][3][4096]."""
+    xa, _, _, _k1 = _ptr_info(x)
+    fa, _, _, _k2 = _ptr_info(feats)
+    _check(load().cyc_features(xa, int(T), int(nsig), fa))
+
+
+def cyc_net_forward(n: int, feats, B: int, logits) -> None:
+    fa, _, _, _k1 = _ptr_info(feats)
+    la, _, _, _k2 = _ptr_info(logits)
+    _check(load().cyc_net_forward(n, fa, int(B), la))
+
+
+def cyc_net_gradients(n: int, feats, labels, B: int, pos_weight: float = 1.0):
+    """(gradients as a host float32 vector, loss)."""
+    fa, _, _, _k1 = _ptr_info(feats)
+    la, _, _, _k2 = _ptr_info(labels)
+    g = np.empty(cyc_net_nparams(), dtype=np.float32)
+    loss = ctypes.c_float(0)
+    _check(load().cyc_net_gradients(n, fa, la, int(B), float(pos_weight), g.ctypes.data, ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def cyc_net_train_step(n: int, feats, labels, B: int, lr: float, pos_weight: float = 1.0) -> float:
+    fa, _, _, _k1 = _ptr_info(feats)
+    la, _, _, _k2 = _ptr_info(labels)
+    loss = ctypes.c_float(0)
+    _check(load().cyc_net_train_step(n, fa, la, int(B), float(lr), float(pos_weight), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def cyc_propose(n: int, x, T: int | None = None, k: int = 32, tau: float = 0.9, on_device: int | None = None):
+    """(alphas_conv[k], alphas_conj[k], confidence, used_fallback)."""
+    xa, nb, dev, _k = _ptr_info(x)
+    if T is None:
+        T = nb // 8
+    if on_device is None:
+        on_device = dev
+    ac = np.empty(k, dtype=np.float64)
+    aj = np.empty(k, dtype=np.float64)
+    conf = ctypes.c_float(0)
+    fb = ctypes.c_int(0)
+    _check(load().cyc_propose(n, xa, int(T), int(on_device), int(k), float(tau), ac.ctypes.data, aj.ctypes.data,
+                              ctypes.byref(conf), ctypes.byref(fb)))
+    return ac, aj, float(conf.value), bool(fb.value)
 
 
 # shapes are tracked on the Python side for cyc_read's default output

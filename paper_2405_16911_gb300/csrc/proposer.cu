@@ -1,0 +1,686 @@
+// proposer.cu -- learned cycle-frequency proposer: spectral features, a small 1-D conv net
+// with hand-written forward, backward and Adam kernels, and top-K proposals with a
+// full-grid fallback (declared in include/cyc.h).
+//
+// Features of a signal (Welch, 16 segments of 4096 samples, Hann window): the averaged
+// periodograms of x, x^2 and |x|^2, as log10, shifted so that bin j is frequency
+// -1/2 + j/4096, each channel standardised.  Cycle frequencies show up there as lines:
+// the cyclic statistics are Fourier coefficients of the lag products (Sec. 2), and the
+// lag-0 products are |x|^2 (conventional) and x^2 (conjugate); the spectrum of x carries
+// the symbol rate that places the conventional lines at other lags (Sec. 3: k/T).
+//
+// Net: four circular convolutions (kernel 9, padding 4), 3 -> 64 -> 64 -> 64 -> 2 channels,
+// ReLU after the first three, then the mean over groups of 8 bins: 2 x 512 logits, one per
+// grid bin a = -1/2 + k/512 and form (CONV, CONJ).  Activations are stored in FP16, weights
+// kept in FP32 (master copy for Adam) and FP16 (used by the kernels), all sums in FP32.
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cyc_impl.h"
+
+using namespace cyc;
+
+namespace {
+
+constexpr int NFFT = 4096, NSEG = 16, NBIN = 512, POOL = 8, KW = 9, NL = 4;
+constexpr int CHS[NL + 1] = {3, 64, 64, 64, 2};
+
+int pfail(int code, const char* fmt, ...)
+{
+    char buf[400];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    record_error(buf);
+    return code;
+}
+
+#define PCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return pfail(e_ == cudaErrorMemoryAllocation ? CYC_ENOMEM : CYC_ECUDA,          \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+    } while (0)
+
+// parameter offsets in the flat FP32 vector: W1 b1 W2 b2 W3 b3 W4 b4
+struct Layout {
+    int w[NL], b[NL], total;
+    Layout()
+    {
+        int o = 0;
+        for (int l = 0; l < NL; ++l) {
+            w[l] = o;
+            o += CHS[l + 1] * CHS[l] * KW;
+            b[l] = o;
+            o += CHS[l + 1];
+        }
+        total = o;
+    }
+};
+const Layout LAY;
+
+// ------------------------------------------------------------------------ features (FFT)
+// One CTA per (signal, channel): 16 radix-2 FFTs of 4096 points in shared memory,
+// periodograms accumulated, then log10, shift and standardisation.
+__global__ void __launch_bounds__(512) features_kernel(const float2* __restrict__ x, int64_t T, __half* __restrict__ out)
+{
+    extern __shared__ float fsm[];
+    float2* d = reinterpret_cast<float2*>(fsm);          // 4096 complex
+    float2* tw = d + NFFT;                                // 2048 twiddles
+    float* acc = reinterpret_cast<float*>(tw + NFFT / 2); // 4096
+    __shared__ float red[2][16];
+    const int sig = blockIdx.x / 3, ch = blockIdx.x % 3, tid = threadIdx.x;
+    const float2* xs = x + (size_t)sig * T;
+    for (int k = tid; k < NFFT / 2; k += blockDim.x) {
+        float s, c;
+        sincospif(-2.0f * k / NFFT, &s, &c);              // exp(-j 2 pi k / N)
+        tw[k] = make_float2(c, s);
+    }
+    for (int k = tid; k < NFFT; k += blockDim.x) acc[k] = 0.f;
+    for (int seg = 0; seg < NSEG; ++seg) {
+        __syncthreads();
+        for (int k = tid; k < NFFT; k += blockDim.x) {
+            float2 v = xs[(size_t)seg * NFFT + k];
+            float2 y;
+            if (ch == 0) y = v;
+            else if (ch == 1) y = make_float2(v.x * v.x - v.y * v.y, 2.f * v.x * v.y);
+            else y = make_float2(v.x * v.x + v.y * v.y, 0.f);
+            float s, c;
+            sincospif(2.0f * k / NFFT, &s, &c);
+            float w = 0.5f - 0.5f * c;                    // Hann
+            d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
+        }
+        for (int half = 1; half < NFFT; half <<= 1) {
+            __syncthreads();
+            const int tstep = NFFT / (2 * half);
+            for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
+                const int grp = bf / half, pos = bf % half;
+                const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+                const float2 w = tw[pos * tstep];
+                const float2 a = d[i0], b = d[i1];
+                const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+                d[i0] = make_float2(a.x + bw.x, a.y + bw.y);
+                d[i1] = make_float2(a.x - bw.x, a.y - bw.y);
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < NFFT; k += blockDim.x) acc[k] += d[k].x * d[k].x + d[k].y * d[k].y;
+    }
+    __syncthreads();
+    // log10 and the shift: output bin j <- FFT bin (j + N/2) mod N
+    float s1 = 0.f, s2 = 0.f;
+    for (int j = tid; j < NFFT; j += blockDim.x) {
+        float v = log10f(acc[(j + NFFT / 2) & (NFFT - 1)] / NSEG + 1e-12f);
+        d[j].x = v;
+        s1 += v;
+        s2 += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = s1;
+        red[1][tid >> 5] = s2;
+    }
+    __syncthreads();
+    float t1 = 0.f, t2 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        t1 += red[0][w];
+        t2 += red[1][w];
+    }
+    const float mu = t1 / NFFT;
+    const float sd = fmaxf(sqrtf(fmaxf(t2 / NFFT - mu * mu, 0.f)), 1e-6f);
+    __half* o = out + ((size_t)sig * 3 + ch) * NFFT;
+    for (int j = tid; j < NFFT; j += blockDim.x) o[j] = __float2half_rn((d[j].x - mu) / sd);
+}
+
+// ------------------------------------------------------------------------ convolution
+// y[b][o][i] = bias[o] + sum_c sum_k W[o][c][k] x[b][c][(i + k - 4) mod N]  (+ ReLU, mask)
+// Block: 32 outputs channels x 128 positions of one sample; 256 threads, 4 x 4 each.
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, int cin, int cout,
+                                                   const __half* __restrict__ w, const float* __restrict__ bias,
+                                                   int relu, const __half* __restrict__ mask, TOut* __restrict__ y)
+{
+    constexpr int TI = 128, TCO = 32;
+    extern __shared__ float csm[];
+    float* xs = csm;                          // [cin][TI + 8]
+    float* ws = csm + cin * (TI + 8);         // [TCO][cin][9]
+    const int b = blockIdx.z, i0 = blockIdx.x * TI, o0 = blockIdx.y * TCO, tid = threadIdx.x;
+    const TIn* xb = x + (size_t)b * cin * NFFT;
+    for (int e = tid; e < cin * (TI + 8); e += 256) {
+        const int c = e / (TI + 8), j = e % (TI + 8);
+        const int src = (i0 + j - 4 + NFFT) & (NFFT - 1);
+        xs[e] = (float)xb[(size_t)c * NFFT + src];
+    }
+    for (int e = tid; e < TCO * cin * KW; e += 256) {
+        const int o = e / (cin * KW);
+        ws[e] = o0 + o < cout ? __half2float(w[(size_t)(o0 + o) * cin * KW + e % (cin * KW)]) : 0.f;
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[a][m] = 0.f;
+    for (int c = 0; c < cin; ++c) {
+        const float* xr = xs + c * (TI + 8);
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            float wv[4], xv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) wv[a] = ws[((warp + 8 * a) * cin + c) * KW + k];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xv[m] = xr[lane + 32 * m + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) acc[a][m] = fmaf(wv[a], xv[m], acc[a][m]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int o = o0 + warp + 8 * a;
+        if (o >= cout) continue;
+        const float bv = bias ? bias[o] : 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int i = i0 + lane + 32 * m;
+            float v = acc[a][m] + bv;
+            if (relu) v = fmaxf(v, 0.f);
+            const size_t idx = ((size_t)b * cout + o) * NFFT + i;
+            if (mask && !(__half2float(mask[idx]) > 0.f)) v = 0.f;
+            y[idx] = (TOut)v;
+        }
+    }
+}
+
+// dW[o][c][k] += sum_b sum_i dz[b][o][i] h[b][c][(i + k - 4) mod N];  db[o] += sum dz[b][o][i]
+// Block: 16 x 16 (o, c) pairs, a range of positions of one sample; atomics across blocks.
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(const __half* __restrict__ h, const float* __restrict__ dz,
+                                                         int cin, int cout, float* __restrict__ dW,
+                                                         float* __restrict__ db, int ichunk)
+{
+    constexpr int T = 16;
+    __shared__ float hs[T][256 + 9];          // odd row length: conflict-free column walks
+    __shared__ float ds[T][256];
+    const int tid = threadIdx.x, oc = tid / T, cc = tid % T;
+    const int o0 = blockIdx.x * T, c0 = blockIdx.y * T;
+    const int b = blockIdx.z / ichunk, part = blockIdx.z % ichunk;
+    const int span = NFFT / ichunk;
+    float acc[KW] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float bacc = 0.f;
+    for (int i0 = part * span; i0 < (part + 1) * span; i0 += 256) {
+        __syncthreads();
+        for (int e = tid; e < T * (256 + 8); e += 256) {
+            const int c = e / (256 + 8), j = e % (256 + 8);   // 264 positions per row are used
+            const int src = (i0 + j - 4 + NFFT) & (NFFT - 1);
+            hs[c][j] = c0 + c < cin ? __half2float(h[((size_t)b * cin + c0 + c) * NFFT + src]) : 0.f;
+        }
+        for (int e = tid; e < T * 256; e += 256) {
+            const int o = e / 256, j = e % 256;
+            ds[o][j] = o0 + o < cout ? dz[((size_t)b * cout + o0 + o) * NFFT + i0 + j] : 0.f;
+        }
+        __syncthreads();
+        float win[KW];
+#pragma unroll
+        for (int k = 0; k < KW - 1; ++k) win[k] = hs[cc][k];
+        for (int j = 0; j < 256; ++j) {
+            win[KW - 1] = hs[cc][j + KW - 1];
+            const float dv = ds[oc][j];
+#pragma unroll
+            for (int k = 0; k < KW; ++k) acc[k] = fmaf(dv, win[k], acc[k]);
+            bacc += dv;
+#pragma unroll
+            for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
+        }
+    }
+    if (o0 + oc < cout && c0 + cc < cin) {
+#pragma unroll
+        for (int k = 0; k < KW; ++k) atomicAdd(&dW[((size_t)(o0 + oc) * cin + c0 + cc) * KW + k], acc[k]);
+        if (c0 == 0 && cc == 0) atomicAdd(&db[o0 + oc], bacc);
+    }
+}
+
+// W'[c][o][k] = W[o][c][8 - k]: the backward-data convolution as a forward one.
+__global__ void flip_weights_kernel(const __half* __restrict__ w, int cin, int cout, __half* __restrict__ wt)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cin * cout * KW) return;
+    const int k = e % KW, o = (e / KW) % cout, c = e / (KW * cout);
+    wt[e] = w[((size_t)o * cin + c) * KW + (KW - 1 - k)];
+}
+
+// logits[b][f][j] = mean over 8 bins of z[b][f][8j..8j+7]; BCE with logits, and
+// dz[b][f][i] = dL/dlogit / 8 (mean over all B x 1024 entries).
+__global__ void pool_loss_kernel(const float* __restrict__ z, const float* __restrict__ labels, int B, float pw,
+                                 float* __restrict__ logits, float* __restrict__ dz, float* __restrict__ loss)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = B * 2 * NBIN;
+    float lv = 0.f;
+    if (e < n) {
+        const float* zz = z + (size_t)e * POOL;
+        float s = 0.f;
+#pragma unroll
+        for (int r = 0; r < POOL; ++r) s += zz[r];
+        const float zl = s / POOL;
+        if (logits) logits[e] = zl;
+        if (labels) {
+            const float y = labels[e];
+            const float lsp = fmaxf(-zl, 0.f) + log1pf(expf(-fabsf(zl)));   // -log sigmoid(z)
+            const float lsn = fmaxf(zl, 0.f) + log1pf(expf(-fabsf(zl)));    // -log(1 - sigmoid(z))
+            lv = (pw * y * lsp + (1.f - y) * lsn) / n;
+            const float sg = 1.f / (1.f + expf(-zl));
+            const float g = (pw * y * (sg - 1.f) + (1.f - y) * sg) / n;
+            if (dz)
+                for (int r = 0; r < POOL; ++r) dz[(size_t)e * POOL + r] = g / POOL;
+        }
+    }
+    if (loss) {
+        for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        if ((threadIdx.x & 31) == 0 && lv != 0.f) atomicAdd(loss, lv);
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            int n, float lr, float b1, float b2, float c1, float c2, float eps)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_half_kernel(const float* __restrict__ p, int n, __half* __restrict__ h)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) h[e] = __float2half_rn(p[e]);
+}
+
+// Top-K per form by logit (iterated block argmax), confidence = share of the sigmoid mass
+// in the K chosen bins, and the count of bins with sigmoid > 1/2.
+__global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
+                                                   float* __restrict__ conf, int* __restrict__ nhot)
+{
+    __shared__ float val[NBIN];
+    __shared__ float bv[16];
+    __shared__ int bi[16];
+    __shared__ float tot, chosen;
+    const int f = blockIdx.x, tid = threadIdx.x;
+    const float z = logits[f * NBIN + tid];
+    const float sg = 1.f / (1.f + expf(-z));
+    val[tid] = z;
+    float s = sg;
+    int hot = sg > 0.5f ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        hot += __shfl_xor_sync(0xffffffffu, hot, o);
+    }
+    if ((tid & 31) == 0) {
+        bv[tid >> 5] = s;
+        bi[tid >> 5] = hot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.f;
+        int h = 0;
+        for (int w = 0; w < 16; ++w) { t += bv[w]; h += bi[w]; }
+        tot = t;
+        chosen = 0.f;
+        nhot[f] = h;
+    }
+    for (int r = 0; r < k; ++r) {
+        __syncthreads();
+        float v = val[tid];
+        int id = tid;
+        for (int o = 16; o > 0; o >>= 1) {
+            float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            int i2 = __shfl_xor_sync(0xffffffffu, id, o);
+            if (v2 > v || (v2 == v && i2 < id)) { v = v2; id = i2; }
+        }
+        if ((tid & 31) == 0) { bv[tid >> 5] = v; bi[tid >> 5] = id; }
+        __syncthreads();
+        if (tid == 0) {
+            float bb = bv[0];
+            int ii = bi[0];
+            for (int w = 1; w < 16; ++w)
+                if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
+            idx[f * k + r] = ii;
+            chosen += 1.f / (1.f + expf(-bb));
+            val[ii] = -INFINITY;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) conf[f] = tot > 0.f ? chosen / tot : 1.f;
+}
+
+}  // namespace
+
+struct cyc_net {
+    int device = 0;
+    float* p = nullptr;       // FP32 master parameters
+    __half* ph = nullptr;     // FP16 copy used by the kernels
+    float* g = nullptr;       // gradients
+    float* m = nullptr;
+    float* v = nullptr;
+    __half* wt = nullptr;     // flipped weights of one layer (backward data)
+    int step = 0;
+    int cap = 0;              // batch capacity of the buffers below
+    __half* h[NL] = {nullptr, nullptr, nullptr, nullptr};   // h[0] unused (features), h[1..3]
+    float* z4 = nullptr;      // last conv output [B][2][4096]
+    float* dz = nullptr;      // [B][64][4096]
+    float* dh = nullptr;      // [B][64][4096]
+    float* logits = nullptr;  // [B][2][512]
+    float* loss = nullptr;
+    float* labels = nullptr;
+    __half* feats = nullptr;  // [1][3][4096] for cyc_propose
+    float2* xbuf = nullptr;   // staging for a host signal
+    int64_t xcap = 0;
+    int* topi = nullptr;
+    float* conf = nullptr;
+    int* nhot = nullptr;
+
+    void free_acts()
+    {
+        for (int l = 1; l < NL; ++l)
+            if (h[l]) { cudaFree(h[l]); h[l] = nullptr; }
+        void* ps[] = {z4, dz, dh, logits};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+        z4 = nullptr; dz = nullptr; dh = nullptr; logits = nullptr;
+        cap = 0;
+    }
+};
+
+namespace {
+
+int ensure_batch(cyc_net* n, int B)
+{
+    if (B <= n->cap) return CYC_OK;
+    n->free_acts();
+    for (int l = 1; l < NL; ++l) PCK(cudaMalloc(&n->h[l], (size_t)B * 64 * NFFT * sizeof(__half)));
+    PCK(cudaMalloc(&n->z4, (size_t)B * 2 * NFFT * sizeof(float)));
+    PCK(cudaMalloc(&n->dz, (size_t)B * 64 * NFFT * sizeof(float)));
+    PCK(cudaMalloc(&n->dh, (size_t)B * 64 * NFFT * sizeof(float)));
+    PCK(cudaMalloc(&n->logits, (size_t)B * 2 * NBIN * sizeof(float)));
+    n->cap = B;
+    return CYC_OK;
+}
+
+size_t conv_smem(int cin) { return (size_t)cin * (128 + 8) * 4 + (size_t)32 * cin * KW * 4; }
+
+template <typename TI, typename TO>
+cudaError_t conv(const TI* x, int cin, int cout, const __half* w, const float* bias, int relu, const __half* mask,
+                 TO* y, int B, cudaStream_t st)
+{
+    static bool set = false;
+    if (!set) {
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)conv_smem(64));
+        if (e != cudaSuccess) return e;
+        set = true;
+    }
+    dim3 grid(NFFT / 128, (cout + 31) / 32, B);
+    conv_kernel<TI, TO><<<grid, 256, conv_smem(cin), st>>>(x, cin, cout, w, bias, relu, mask, y);
+    return cudaGetLastError();
+}
+
+// forward of B feature sets; leaves h[1..3], z4 and (pooled) logits in the net's buffers
+int net_forward(cyc_net* n, const __half* feats, int B, cudaStream_t st)
+{
+    int rc = ensure_batch(n, B);
+    if (rc) return rc;
+    const __half* in = feats;
+    for (int l = 0; l < NL - 1; ++l) {
+        PCK((conv<__half, __half>(in, CHS[l], CHS[l + 1], n->ph + LAY.w[l], n->p + LAY.b[l], 1, nullptr, n->h[l + 1], B, st)));
+        in = n->h[l + 1];
+    }
+    PCK((conv<__half, float>(in, CHS[NL - 1], CHS[NL], n->ph + LAY.w[NL - 1], n->p + LAY.b[NL - 1], 0, nullptr, n->z4, B, st)));
+    return CYC_OK;
+}
+
+// gradients into n->g (zeroed first) and the loss into n->loss
+int net_backward(cyc_net* n, const __half* feats, const float* labels, int B, float pw, cudaStream_t st)
+{
+    PCK(cudaMemsetAsync(n->g, 0, LAY.total * sizeof(float), st));
+    PCK(cudaMemsetAsync(n->loss, 0, sizeof(float), st));
+    const int ne = B * 2 * NBIN;
+    pool_loss_kernel<<<(ne + 255) / 256, 256, 0, st>>>(n->z4, labels, B, pw, n->logits, n->dz, n->loss);
+    PCK(cudaGetLastError());
+    for (int l = NL - 1; l >= 0; --l) {
+        const int cin = CHS[l], cout = CHS[l + 1];
+        const __half* hin = l == 0 ? feats : n->h[l];
+        const int ich = 8;
+        dim3 gw((cout + 15) / 16, (cin + 15) / 16, B * ich);
+        conv_wgrad_kernel<<<gw, 256, 0, st>>>(hin, n->dz, cin, cout, n->g + LAY.w[l], n->g + LAY.b[l], ich);
+        PCK(cudaGetLastError());
+        if (l == 0) break;
+        // dL/dh_l = conv of dz with the flipped, transposed weights; times the ReLU mask of h_l
+        const int nw = cin * cout * KW;
+        flip_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(n->ph + LAY.w[l], cin, cout, n->wt);
+        PCK(cudaGetLastError());
+        PCK((conv<float, float>(n->dz, cout, cin, n->wt, nullptr, 0, n->h[l], n->dh, B, st)));
+        float* t = n->dz;
+        n->dz = n->dh;
+        n->dh = t;
+    }
+    return CYC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out)
+{
+    if (!out) return pfail(CYC_EINVAL, "cyc_net_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return pfail(CYC_ECUDA, "cyc_net_create: device %d is not available", device);
+    }
+    cudaSetDevice(device);
+    cyc_net* n = new cyc_net();
+    n->device = device;
+    std::vector<float> host(LAY.total, 0.f);
+    if (params) {
+        memcpy(host.data(), params, LAY.total * sizeof(float));
+    } else {
+        // He-normal weights from splitmix64 + Box-Muller, zero biases
+        uint64_t st = seed;
+        auto next = [&st]() {
+            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        for (int l = 0; l < NL; ++l) {
+            const int nw = CHS[l + 1] * CHS[l] * KW;
+            const double sdev = sqrt(2.0 / (CHS[l] * KW));
+            for (int i = 0; i < nw; ++i) {
+                double u1 = ((next() >> 11) + 1) * (1.0 / 9007199254740992.0);
+                double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+                host[LAY.w[l] + i] = (float)(sdev * sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2));
+            }
+        }
+    }
+    int rc = CYC_OK;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == CYC_OK) rc = pfail(CYC_ECUDA, "cyc_net_create: %s", cudaGetErrorString(e));
+    };
+    chk(cudaMalloc(&n->p, LAY.total * sizeof(float)));
+    chk(cudaMalloc(&n->ph, LAY.total * sizeof(__half)));
+    chk(cudaMalloc(&n->g, LAY.total * sizeof(float)));
+    chk(cudaMalloc(&n->m, LAY.total * sizeof(float)));
+    chk(cudaMalloc(&n->v, LAY.total * sizeof(float)));
+    chk(cudaMalloc(&n->wt, 64 * 64 * KW * sizeof(__half)));
+    chk(cudaMalloc(&n->loss, sizeof(float)));
+    chk(cudaMalloc(&n->feats, 3 * NFFT * sizeof(__half)));
+    chk(cudaMalloc(&n->topi, 2 * NBIN * sizeof(int)));
+    chk(cudaMalloc(&n->conf, 2 * sizeof(float)));
+    chk(cudaMalloc(&n->nhot, 2 * sizeof(int)));
+    if (rc == CYC_OK) {
+        chk(cudaMemcpy(n->p, host.data(), LAY.total * sizeof(float), cudaMemcpyHostToDevice));
+        chk(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
+        chk(cudaMemset(n->v, 0, LAY.total * sizeof(float)));
+        to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+        chk(cudaDeviceSynchronize());
+    }
+    if (rc != CYC_OK) {
+        cyc_net_destroy(n);
+        return rc;
+    }
+    *out = n;
+    return CYC_OK;
+}
+
+int cyc_net_destroy(cyc_net* n)
+{
+    if (!n) return CYC_OK;
+    cudaSetDevice(n->device);
+    n->free_acts();
+    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->conf, n->nhot};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    delete n;
+    return CYC_OK;
+}
+
+int cyc_net_nparams(void) { return LAY.total; }
+
+int cyc_net_get_params(cyc_net* n, float* out)
+{
+    if (!n || !out) return pfail(CYC_EINVAL, "cyc_net_get_params: NULL argument");
+    cudaSetDevice(n->device);
+    PCK(cudaMemcpy(out, n->p, LAY.total * sizeof(float), cudaMemcpyDeviceToHost));
+    return CYC_OK;
+}
+
+int cyc_net_set_params(cyc_net* n, const float* params)
+{
+    if (!n || !params) return pfail(CYC_EINVAL, "cyc_net_set_params: NULL argument");
+    cudaSetDevice(n->device);
+    PCK(cudaMemcpy(n->p, params, LAY.total * sizeof(float), cudaMemcpyHostToDevice));
+    to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+    PCK(cudaDeviceSynchronize());
+    n->step = 0;
+    PCK(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
+    PCK(cudaMemset(n->v, 0, LAY.total * sizeof(float)));
+    return CYC_OK;
+}
+
+int cyc_features(const void* x, int64_t T, int nsig, void* feats)
+{
+    if (!x || !feats || nsig <= 0) return pfail(CYC_EINVAL, "cyc_features: bad argument");
+    if (T < (int64_t)NSEG * NFFT) return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT);
+    static bool set = false;
+    const int smem = NFFT * 8 + NFFT / 2 * 8 + NFFT * 4;
+    if (!set) {
+        PCK(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        set = true;
+    }
+    features_kernel<<<nsig * 3, 512, smem>>>((const float2*)x, T, (__half*)feats);
+    PCK(cudaGetLastError());
+    PCK(cudaDeviceSynchronize());
+    return CYC_OK;
+}
+
+int cyc_net_forward(cyc_net* n, const void* feats, int B, float* logits)
+{
+    if (!n || !feats || !logits || B <= 0) return pfail(CYC_EINVAL, "cyc_net_forward: bad argument");
+    cudaSetDevice(n->device);
+    int rc = net_forward(n, (const __half*)feats, B, 0);
+    if (rc) return rc;
+    const int ne = B * 2 * NBIN;
+    pool_loss_kernel<<<(ne + 255) / 256, 256>>>(n->z4, nullptr, B, 1.f, logits, nullptr, nullptr);
+    PCK(cudaGetLastError());
+    PCK(cudaDeviceSynchronize());
+    return CYC_OK;
+}
+
+int cyc_net_gradients(cyc_net* n, const void* feats, const float* labels, int B, float pos_weight, float* grads,
+                      float* loss)
+{
+    if (!n || !feats || !labels || B <= 0) return pfail(CYC_EINVAL, "cyc_net_gradients: bad argument");
+    cudaSetDevice(n->device);
+    int rc = net_forward(n, (const __half*)feats, B, 0);
+    if (rc) return rc;
+    rc = net_backward(n, (const __half*)feats, labels, B, pos_weight, 0);
+    if (rc) return rc;
+    PCK(cudaDeviceSynchronize());
+    if (grads) PCK(cudaMemcpy(grads, n->g, LAY.total * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss) PCK(cudaMemcpy(loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return CYC_OK;
+}
+
+int cyc_net_train_step(cyc_net* n, const void* feats, const float* labels, int B, float lr, float pos_weight,
+                       float* loss)
+{
+    int rc = cyc_net_gradients(n, feats, labels, B, pos_weight, nullptr, loss);
+    if (rc) return rc;
+    n->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+    adam_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, n->g, n->m, n->v, LAY.total, lr, b1, b2, c1, c2, 1e-8f);
+    to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+    PCK(cudaGetLastError());
+    return CYC_OK;
+}
+
+int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, float tau, double* alphas_conv,
+                double* alphas_conj, float* conf, int* used_fallback)
+{
+    if (!n || !x || k <= 0 || k > NBIN || !alphas_conv || !alphas_conj || !used_fallback)
+        return pfail(CYC_EINVAL, "cyc_propose: bad argument");
+    if (T < (int64_t)NSEG * NFFT) return pfail(CYC_EINVAL, "cyc_propose: needs at least %d samples", NSEG * NFFT);
+    cudaSetDevice(n->device);
+    const float2* xd = (const float2*)x;
+    const int64_t use = (int64_t)NSEG * NFFT;
+    if (!on_device) {
+        if (n->xcap < use) {
+            if (n->xbuf) cudaFree(n->xbuf);
+            PCK(cudaMalloc(&n->xbuf, use * sizeof(float2)));
+            n->xcap = use;
+        }
+        PCK(cudaMemcpy(n->xbuf, x, use * sizeof(float2), cudaMemcpyHostToDevice));
+        xd = n->xbuf;
+    }
+    int rc = cyc_features(xd, use, 1, n->feats);
+    if (rc) return rc;
+    rc = net_forward(n, n->feats, 1, 0);
+    if (rc) return rc;
+    pool_loss_kernel<<<(2 * NBIN + 255) / 256, 256>>>(n->z4, nullptr, 1, 1.f, n->logits, nullptr, nullptr);
+    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf, n->nhot);
+    PCK(cudaGetLastError());
+    std::vector<int> idx(2 * k);
+    float cf[2];
+    int hot[2];
+    PCK(cudaMemcpy(idx.data(), n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost));
+    PCK(cudaMemcpy(cf, n->conf, sizeof cf, cudaMemcpyDeviceToHost));
+    PCK(cudaMemcpy(hot, n->nhot, sizeof hot, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < k; ++r) {
+        alphas_conv[r] = -0.5 + idx[r] / (double)NBIN;
+        alphas_conj[r] = -0.5 + idx[k + r] / (double)NBIN;
+    }
+    const float c = fminf(cf[0], cf[1]);
+    if (conf) *conf = c;
+    *used_fallback = (c < tau || hot[0] > k || hot[1] > k) ? 1 : 0;
+    return CYC_OK;
+}
+
+}  // extern "C"

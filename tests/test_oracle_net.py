@@ -1,0 +1,88 @@
+"""Pins of the FP64 proposer oracle (CPU): explicit-loop convolution, finite-difference
+gradients, closed-form BCE values, and the line positions of a tone's features."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import net as on
+
+
+def test_conv_matches_explicit_loops():
+    rng = np.random.default_rng(0)
+    ci, co, n = 3, 4, 20
+    x = rng.normal(size=(ci, n))
+    W = rng.normal(size=(co, ci, on.K))
+    b = rng.normal(size=co)
+    y = on.conv(x, W, b)
+    for o in range(co):
+        for i in range(n):
+            ref = b[o] + sum(W[o, c, k] * x[c, (i + k - 4) % n] for c in range(ci) for k in range(on.K))
+            assert abs(y[o, i] - ref) < 1e-12
+
+
+def test_conv_backward_finite_differences():
+    rng = np.random.default_rng(1)
+    ci, co, n = 3, 5, 24
+    x = rng.normal(size=(ci, n))
+    W = rng.normal(size=(co, ci, on.K))
+    b = rng.normal(size=co)
+    gy = rng.normal(size=(co, n))
+    L = lambda x_, W_, b_: float(np.sum(gy * on.conv(x_, W_, b_)))
+    dx, dW, db = on.conv_backward(x, W, gy)
+    eps = 1e-6
+    for (c, j) in [(0, 0), (2, 23), (1, 7)]:
+        xp, xm = x.copy(), x.copy()
+        xp[c, j] += eps
+        xm[c, j] -= eps
+        assert abs((L(xp, W, b) - L(xm, W, b)) / (2 * eps) - dx[c, j]) < 1e-6
+    for (o, c, k) in [(0, 0, 0), (4, 2, 8), (2, 1, 4)]:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[o, c, k] += eps
+        Wm[o, c, k] -= eps
+        assert abs((L(x, Wp, b) - L(x, Wm, b)) / (2 * eps) - dW[o, c, k]) < 1e-6
+    assert np.allclose(db, gy.sum(axis=1))
+
+
+def test_bce_closed_forms():
+    z = np.array([[0.0, 2.0], [-3.0, 0.5]])
+    y = np.array([[1.0, 0.0], [1.0, 1.0]])
+    loss, g = on.bce(z, y, pos_weight=2.0)
+    s = 1 / (1 + np.exp(-z))
+    ref = np.mean(2.0 * y * -np.log(s) + (1 - y) * -np.log(1 - s))
+    assert abs(loss - ref) < 1e-12
+    assert abs(on.bce(np.zeros(4), np.zeros(4))[0] - math.log(2.0)) < 1e-15
+    assert np.allclose(g, (2.0 * y * (s - 1) + (1 - y) * s) / z.size)
+
+
+@pytest.mark.slow
+def test_full_net_gradient_finite_differences():
+    params = on.init_params(3)
+    rng = np.random.default_rng(2)
+    feat = rng.normal(size=(3, on.NFFT))
+    lab = (rng.uniform(size=(2, on.NBIN)) < 0.05).astype(float)
+    loss, grads = on.batch_loss_and_grads(params, [feat], [lab], pos_weight=3.0)
+    eps = 1e-5
+    for (li, idx) in [(0, (5, 1, 3)), (2, (10, 20, 4)), (3, (1, 63, 8))]:
+        W, b = params[li]
+        Wp = [(w.copy(), bb.copy()) for w, bb in params]
+        Wm = [(w.copy(), bb.copy()) for w, bb in params]
+        Wp[li][0][idx] += eps
+        Wm[li][0][idx] -= eps
+        lp, _ = on.batch_loss_and_grads(Wp, [feat], [lab], pos_weight=3.0)
+        lm, _ = on.batch_loss_and_grads(Wm, [feat], [lab], pos_weight=3.0)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - grads[li][0][idx]) < 1e-6 * max(1.0, abs(fd)) + 1e-9, (li, idx)
+
+
+def test_tone_feature_lines():
+    """x = exp(j 2 pi f0 n): the x channel peaks at f0, x^2 at 2 f0, |x|^2 is flat but for DC."""
+    f0 = 0.1171875                                   # on the 4096-bin grid: 480/4096
+    n = np.arange(on.NSEG * on.NFFT)
+    x = np.exp(2j * np.pi * f0 * n)
+    F = on.features(x)
+    j = lambda f: int(round((f + 0.5) * on.NFFT)) % on.NFFT
+    assert int(np.argmax(F[0])) == j(f0)
+    assert int(np.argmax(F[1])) == j(2 * f0)
+    assert int(np.argmax(F[2])) == j(0.0)
+    assert np.allclose(F.mean(axis=1), 0.0, atol=1e-9) and np.allclose(F.std(axis=1), 1.0, atol=1e-9)
