@@ -240,10 +240,11 @@ CYC_API int cyc_server_stats(cyc_server* srv, int64_t* batches, int64_t* items, 
  * instead of the full grid -- and falls back to the full grid when it is unsure.
  *
  * Features (cyc_features): for each signal, Welch-averaged periodograms (16 segments of
- * 4096 samples, Hann window) of x, x^2 and |x|^2 -- the lag-0 products whose spectral
- * lines are the conventional and conjugate cycle frequencies (Sec. 2) -- as log10, bin j
- * at frequency -1/2 + j/4096, each channel standardised; FP16 [nsig][3][4096].
- * Net: circular 1-D convolutions, kernel 9, 3 -> 64 -> 64 -> 64 -> 2 channels, ReLU after
+ * 4096 samples, Hann window) of x, x^2 and the lag products x[n+d] conj(x[n]) for
+ * d = 0, 1, 2, 3, 4, 6, 8, 12, 16 -- spectra whose lines are the conjugate and the
+ * conventional cycle frequencies (Sec. 2) -- as log10, bin j at frequency -1/2 + j/4096,
+ * each channel standardised; FP16 [nsig][11][4096].
+ * Net: circular 1-D convolutions, kernel 9, 11 -> 64 -> 64 -> 64 -> 2 channels, ReLU after
  * the first three, mean over groups of 8 bins: logits [B][form][512] (CONV, CONJ).  FP16
  * weights and activations, FP32 sums; parameters as one flat FP32 vector
  * (W1 b1 W2 b2 W3 b3 W4 b4, W[out][in][9]) of cyc_net_nparams() values.
@@ -260,7 +261,7 @@ CYC_API int cyc_net_get_params(cyc_net* n, float* out);           /* host, npara
 CYC_API int cyc_net_set_params(cyc_net* n, const float* params);  /* host; resets Adam state */
 
 /* Features of nsig signals stored back to back in device memory (signal s at x + s*T
- * complex64 samples, T >= 65536; the first 65536 are used) into device FP16 `feats`. */
+ * complex64 samples, T >= 65552; the first 65552 are used) into device FP16 `feats`. */
 CYC_API int cyc_features(const void* x, int64_t T, int nsig, void* feats);
 
 /* Logits of B feature sets (device pointers): logits [B][2][512] FP32. */
@@ -275,11 +276,11 @@ CYC_API int cyc_net_gradients(cyc_net* n, const void* feats, const float* labels
 CYC_API int cyc_net_train_step(cyc_net* n, const void* feats, const float* labels, int B, float lr,
                                float pos_weight, float* loss);
 
-/* Proposals for one signal (host or device, >= 65536 samples): the k most likely grid
+/* Proposals for one signal (host or device, >= 65552 samples): the k most likely grid
  * cycle frequencies of each form into alphas_conv[k] and alphas_conj[k] (host), the
- * confidence (share of the predicted probability mass inside the chosen bins, the lower
- * of the two forms), and *used_fallback = 1 when the confidence is below tau or more
- * than k bins of a form are predicted on: the caller should then run the full grid. */
+ * confidence (1 - the predicted probability of the most likely bin left out, the lower of
+ * the two forms), and *used_fallback = 1 when the confidence is below tau: the caller
+ * should then run the full grid. */
 CYC_API int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, float tau,
                         double* alphas_conv, double* alphas_conj, float* conf, int* used_fallback);
 

@@ -5,12 +5,14 @@ proposer computes, so that the CUDA features, forward pass, gradients and loss c
 checked value by value:
 
 * features(x): Welch-averaged periodograms (16 segments of 4096 samples, Hann window) of
-  x, x**2 and |x|**2 -- the spectra in which conventional and conjugate cycle frequencies
-  show up as lines (Sec. 2: the cyclic statistics are Fourier coefficients of the lag
-  products; at lag 0 these are |x|^2 and x^2) -- as log10, frequency axis shifted to
-  [-1/2, 1/2), each channel standardised to zero mean and unit variance.
+  x, x**2 and of the lag products x[n+d] conj(x[n]) for d in LAG_CHANNELS (d = 0 is
+  |x|^2) -- the spectra in which conjugate (x^2) and conventional (lag products) cycle
+  frequencies show up as lines (Sec. 2: the cyclic statistics are Fourier coefficients of
+  the lag products; a constant-envelope signal such as GMSK has its conventional lines at
+  non-zero lags only) -- as log10, frequency axis shifted to [-1/2, 1/2), each channel
+  standardised to zero mean and unit variance.  Needs 65536 + 16 samples.
 * forward/backward of the net: four circular 1-D convolutions (kernel 9, padding 4),
-  3 -> 64 -> 64 -> 64 -> 2 channels, ReLU after the first three, then the mean over
+  11 -> 64 -> 64 -> 64 -> 2 channels, ReLU after the first three, then the mean over
   groups of 8 bins: 2 x 512 logits, one per cycle-frequency grid bin a = -1/2 + k/512
   and form (CONV, CONJ).
 * the loss: mean binary cross-entropy with logits, positives weighted by `pos_weight`.
@@ -22,7 +24,10 @@ from __future__ import annotations
 import numpy as np
 
 NFFT, NSEG, NBIN, POOL, K = 4096, 16, 512, 8, 9
-CH = (3, 64, 64, 64, 2)
+LAG_CHANNELS = (0, 1, 2, 3, 4, 6, 8, 12, 16)
+NIN = 2 + len(LAG_CHANNELS)
+CH = (NIN, 64, 64, 64, 2)
+NEED = NSEG * NFFT + max(LAG_CHANNELS)
 
 
 def hann(n: int = NFFT) -> np.ndarray:
@@ -30,14 +35,16 @@ def hann(n: int = NFFT) -> np.ndarray:
 
 
 def features(x, nseg: int = NSEG, nfft: int = NFFT, eps: float = 1e-12) -> np.ndarray:
-    """[3][nfft] float64 standardised log spectra of x, x^2, |x|^2 (see module doc)."""
+    """[NIN][nfft] float64 standardised log spectra (see module doc)."""
     x = np.asarray(x, dtype=np.complex128)
-    assert x.size >= nseg * nfft
+    assert x.size >= nseg * nfft + max(LAG_CHANNELS)
     w = hann(nfft)
-    out = np.zeros((3, nfft))
+    out = np.zeros((NIN, nfft))
     for s in range(nseg):
-        seg = x[s * nfft:(s + 1) * nfft]
-        for c, y in enumerate((seg, seg * seg, (np.abs(seg) ** 2).astype(np.complex128))):
+        n = np.arange(s * nfft, (s + 1) * nfft)
+        seg = x[n]
+        ys = [seg, seg * seg] + [x[n + d] * np.conj(seg) for d in LAG_CHANNELS]
+        for c, y in enumerate(ys):
             Y = np.fft.fft(y * w)
             out[c] += np.abs(Y) ** 2
     out = np.log10(out / nseg + eps)

@@ -19,6 +19,9 @@
 // copies (a ring of two slots), so that the lag-product warps read shared memory only.
 // BF16x3: v = hi + lo, hi = bf16(v), lo = bf16(v - hi); products hi.hi, hi.lo, lo.hi.
 //
+// Items with at most 128 columns ("narrow", e.g. 64 lags x 2 forms) issue N = 128 MMAs: each
+// P thread forms one column (B row = tile column) and the epilogue reads 128 D columns.
+//
 // Warp roles (576 threads).  Two producer sets; set k produces the groups G = k mod 2 of
 // the CTA's running group counter G, so one set's latencies hide behind the other's work:
 //   set k, warps 8k+0..3  P warps: thread t forms tile columns 2t, 2t+1 (with lag-major
@@ -217,13 +220,15 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         const int XB = (XSLOT - mpad - 2) & ~(GS - 1);          // samples per staged block
         const int nblocks = (ngroups * GS + XB - 1) / XB;
         const int xoff = (int)(n_beg & 1);    // bulk copies start at an even sample (16-byte aligned)
+        const bool narrow = it.ncols - it.c0 <= BN / 2;     // N = 128 MMAs, one column per P thread
 
         if (warp < MMA_WARP && role < P_WARPS) {
             // -------------------------------------------------------- P warps (lag products)
             const int t = (warp - pset * SET_WARPS) * 32 + lane;     // 0..127
             const int c0 = it.c0, ncols = it.ncols;
-            const int jA = 2 * t, jB = 2 * t + 1;
-            const bool okA = c0 + jA < ncols, okB = c0 + jB < ncols;
+            // wide items: columns 2t, 2t+1 -> B rows t, t+128; narrow items: column t -> row t
+            const int jA = narrow ? t : 2 * t, jB = 2 * t + 1;
+            const bool okA = c0 + jA < ncols, okB = !narrow && c0 + jB < ncols;
             const int mA = okA ? it.col_lag[c0 + jA] : 0, mB = okB ? it.col_lag[c0 + jB] : 0;
             const bool cjA = okA && it.col_conj[c0 + jA], cjB = okB && it.col_conj[c0 + jB];
             const bool same_lag = okB && mA == mB;
@@ -272,12 +277,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     pack8<C::BF>(piA, h, l);
                     st16(st + offA + P_LBO, h);
                     if (C::BF) st16(sl + offA + P_LBO, l);
-                    pack8<C::BF>(prB, h, l);
-                    st16(st + offB, h);
-                    if (C::BF) st16(sl + offB, l);
-                    pack8<C::BF>(piB, h, l);
-                    st16(st + offB + P_LBO, h);
-                    if (C::BF) st16(sl + offB + P_LBO, l);
+                    if (!narrow) {
+                        pack8<C::BF>(prB, h, l);
+                        st16(st + offB, h);
+                        if (C::BF) st16(sl + offB, l);
+                        pack8<C::BF>(piB, h, l);
+                        st16(st + offB + P_LBO, h);
+                        if (C::BF) st16(sl + offB + P_LBO, l);
+                    }
                     tc::fence_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&bars->full[s]);
@@ -369,7 +376,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             }
         } else if (warp == MMA_WARP && lane == 0) {
             // -------------------------------------------------------- MMA issuer
-            constexpr uint32_t idesc = tc::idesc_f16(BM, BN, C::BF);
+            const uint32_t idesc = tc::idesc_f16(BM, narrow ? BN / 2 : BN, C::BF);
             const uint32_t pbase = tc::smem_u32(smem);
             for (int g = 0; g < ngroups; ++g) {
                 const uint32_t Gg = G + g;
@@ -412,10 +419,29 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 uint32_t dr0[16], di0[16], dr1[16], di1[16];
                 tc::tmem_ld16(lane_addr + TM_DR + cb * 16, dr0);
                 tc::tmem_ld16(lane_addr + TM_DI + cb * 16, di0);
-                tc::tmem_ld16(lane_addr + TM_DR + 128 + cb * 16, dr1);
-                tc::tmem_ld16(lane_addr + TM_DI + 128 + cb * 16, di1);
+                if (!narrow) {
+                    tc::tmem_ld16(lane_addr + TM_DR + 128 + cb * 16, dr1);
+                    tc::tmem_ld16(lane_addr + TM_DI + 128 + cb * 16, di1);
+                }
                 tc::tmem_ld_wait();
                 if (it.u0 + row >= it.Au) continue;
+                if (narrow) {
+                    // D column r <-> tile column r
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const int c = cb * 16 + j;
+                        float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
+                                                      __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (vec && it.c0 + c + 1 < it.ncols) {
+                            *reinterpret_cast<float4*>(&out[c]) = v;
+                        } else {
+                            if (it.c0 + c < it.ncols) out[c] = make_float2(v.x, v.y);
+                            if (it.c0 + c + 1 < it.ncols) out[c + 1] = make_float2(v.z, v.w);
+                        }
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int r = cb * 16 + j;               // B rows r, r + 128 <-> tile columns 2r, 2r+1

@@ -3,13 +3,14 @@
 // full-grid fallback (declared in include/cyc.h).
 //
 // Features of a signal (Welch, 16 segments of 4096 samples, Hann window): the averaged
-// periodograms of x, x^2 and |x|^2, as log10, shifted so that bin j is frequency
-// -1/2 + j/4096, each channel standardised.  Cycle frequencies show up there as lines:
-// the cyclic statistics are Fourier coefficients of the lag products (Sec. 2), and the
-// lag-0 products are |x|^2 (conventional) and x^2 (conjugate); the spectrum of x carries
-// the symbol rate that places the conventional lines at other lags (Sec. 3: k/T).
+// periodograms of x, x^2 and of the lag products x[n+d] conj(x[n]), d in {0, 1, 2, 3, 4, 6,
+// 8, 12, 16} (d = 0: |x|^2), as log10, shifted so that bin j is frequency -1/2 + j/4096,
+// each channel standardised.  Cycle frequencies show up there as lines: the cyclic
+// statistics are Fourier coefficients of the lag products (Sec. 2); x^2 carries the
+// conjugate lines, the lag products the conventional ones -- at non-zero lags only for a
+// constant-envelope signal such as GMSK (Sec. 3).
 //
-// Net: four circular convolutions (kernel 9, padding 4), 3 -> 64 -> 64 -> 64 -> 2 channels,
+// Net: four circular convolutions (kernel 9, padding 4), 11 -> 64 -> 64 -> 64 -> 2 channels,
 // ReLU after the first three, then the mean over groups of 8 bins: 2 x 512 logits, one per
 // grid bin a = -1/2 + k/512 and form (CONV, CONJ).  Activations are stored in FP16, weights
 // kept in FP32 (master copy for Adam) and FP16 (used by the kernels), all sums in FP32.
@@ -28,7 +29,9 @@ using namespace cyc;
 namespace {
 
 constexpr int NFFT = 4096, NSEG = 16, NBIN = 512, POOL = 8, KW = 9, NL = 4;
-constexpr int CHS[NL + 1] = {3, 64, 64, 64, 2};
+constexpr int NLAGC = 9, NIN = 2 + NLAGC, MAXD = 16;
+__constant__ int c_lagch[NLAGC] = {0, 1, 2, 3, 4, 6, 8, 12, 16};
+constexpr int CHS[NL + 1] = {NIN, 64, 64, 64, 2};
 
 int pfail(int code, const char* fmt, ...)
 {
@@ -76,7 +79,8 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
     float2* tw = d + NFFT;                                // 2048 twiddles
     float* acc = reinterpret_cast<float*>(tw + NFFT / 2); // 4096
     __shared__ float red[2][16];
-    const int sig = blockIdx.x / 3, ch = blockIdx.x % 3, tid = threadIdx.x;
+    const int sig = blockIdx.x / NIN, ch = blockIdx.x % NIN, tid = threadIdx.x;
+    const int lag = ch >= 2 ? c_lagch[ch - 2] : 0;
     const float2* xs = x + (size_t)sig * T;
     for (int k = tid; k < NFFT / 2; k += blockDim.x) {
         float s, c;
@@ -89,9 +93,14 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
         for (int k = tid; k < NFFT; k += blockDim.x) {
             float2 v = xs[(size_t)seg * NFFT + k];
             float2 y;
-            if (ch == 0) y = v;
-            else if (ch == 1) y = make_float2(v.x * v.x - v.y * v.y, 2.f * v.x * v.y);
-            else y = make_float2(v.x * v.x + v.y * v.y, 0.f);
+            if (ch == 0) {
+                y = v;
+            } else if (ch == 1) {
+                y = make_float2(v.x * v.x - v.y * v.y, 2.f * v.x * v.y);
+            } else {
+                const float2 u = xs[(size_t)seg * NFFT + k + lag];      // x[n+d] conj(x[n])
+                y = make_float2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);
+            }
             float s, c;
             sincospif(2.0f * k / NFFT, &s, &c);
             float w = 0.5f - 0.5f * c;                    // Hann
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
     }
     const float mu = t1 / NFFT;
     const float sd = fmaxf(sqrtf(fmaxf(t2 / NFFT - mu * mu, 0.f)), 1e-6f);
-    __half* o = out + ((size_t)sig * 3 + ch) * NFFT;
+    __half* o = out + ((size_t)sig * NIN + ch) * NFFT;
     for (int j = tid; j < NFFT; j += blockDim.x) o[j] = __float2half_rn((d[j].x - mu) / sd);
 }
 
@@ -311,39 +320,17 @@ __global__ void to_half_kernel(const float* __restrict__ p, int n, __half* __res
     if (e < n) h[e] = __float2half_rn(p[e]);
 }
 
-// Top-K per form by logit (iterated block argmax), confidence = share of the sigmoid mass
-// in the K chosen bins, and the count of bins with sigmoid > 1/2.
+// Top-K per form by logit (iterated block argmax).  Confidence of a form: 1 - sigmoid of
+// the best bin left out, i.e. how sure the net is that no line was left behind.
 __global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
-                                                   float* __restrict__ conf, int* __restrict__ nhot)
+                                                   float* __restrict__ conf)
 {
     __shared__ float val[NBIN];
     __shared__ float bv[16];
     __shared__ int bi[16];
-    __shared__ float tot, chosen;
     const int f = blockIdx.x, tid = threadIdx.x;
-    const float z = logits[f * NBIN + tid];
-    const float sg = 1.f / (1.f + expf(-z));
-    val[tid] = z;
-    float s = sg;
-    int hot = sg > 0.5f ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        hot += __shfl_xor_sync(0xffffffffu, hot, o);
-    }
-    if ((tid & 31) == 0) {
-        bv[tid >> 5] = s;
-        bi[tid >> 5] = hot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float t = 0.f;
-        int h = 0;
-        for (int w = 0; w < 16; ++w) { t += bv[w]; h += bi[w]; }
-        tot = t;
-        chosen = 0.f;
-        nhot[f] = h;
-    }
-    for (int r = 0; r < k; ++r) {
+    val[tid] = logits[f * NBIN + tid];
+    for (int r = 0; r <= k; ++r) {
         __syncthreads();
         float v = val[tid];
         int id = tid;
@@ -359,13 +346,14 @@ __global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ log
             int ii = bi[0];
             for (int w = 1; w < 16; ++w)
                 if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
-            idx[f * k + r] = ii;
-            chosen += 1.f / (1.f + expf(-bb));
-            val[ii] = -INFINITY;
+            if (r < k) {
+                idx[f * k + r] = ii;
+                val[ii] = -INFINITY;
+            } else {
+                conf[f] = k < NBIN ? 1.f - 1.f / (1.f + expf(-bb)) : 1.f;
+            }
         }
     }
-    __syncthreads();
-    if (tid == 0) conf[f] = tot > 0.f ? chosen / tot : 1.f;
 }
 
 }  // namespace
@@ -387,12 +375,11 @@ struct cyc_net {
     float* logits = nullptr;  // [B][2][512]
     float* loss = nullptr;
     float* labels = nullptr;
-    __half* feats = nullptr;  // [1][3][4096] for cyc_propose
+    __half* feats = nullptr;  // [1][NIN][4096] for cyc_propose
     float2* xbuf = nullptr;   // staging for a host signal
     int64_t xcap = 0;
     int* topi = nullptr;
     float* conf = nullptr;
-    int* nhot = nullptr;
 
     void free_acts()
     {
@@ -530,10 +517,9 @@ int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out
     chk(cudaMalloc(&n->v, LAY.total * sizeof(float)));
     chk(cudaMalloc(&n->wt, 64 * 64 * KW * sizeof(__half)));
     chk(cudaMalloc(&n->loss, sizeof(float)));
-    chk(cudaMalloc(&n->feats, 3 * NFFT * sizeof(__half)));
+    chk(cudaMalloc(&n->feats, NIN * NFFT * sizeof(__half)));
     chk(cudaMalloc(&n->topi, 2 * NBIN * sizeof(int)));
     chk(cudaMalloc(&n->conf, 2 * sizeof(float)));
-    chk(cudaMalloc(&n->nhot, 2 * sizeof(int)));
     if (rc == CYC_OK) {
         chk(cudaMemcpy(n->p, host.data(), LAY.total * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
@@ -554,7 +540,7 @@ int cyc_net_destroy(cyc_net* n)
     if (!n) return CYC_OK;
     cudaSetDevice(n->device);
     n->free_acts();
-    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->conf, n->nhot};
+    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->conf};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete n;
@@ -587,14 +573,15 @@ int cyc_net_set_params(cyc_net* n, const float* params)
 int cyc_features(const void* x, int64_t T, int nsig, void* feats)
 {
     if (!x || !feats || nsig <= 0) return pfail(CYC_EINVAL, "cyc_features: bad argument");
-    if (T < (int64_t)NSEG * NFFT) return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT);
+    if (T < (int64_t)NSEG * NFFT + MAXD)
+        return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT + MAXD);
     static bool set = false;
     const int smem = NFFT * 8 + NFFT / 2 * 8 + NFFT * 4;
     if (!set) {
         PCK(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         set = true;
     }
-    features_kernel<<<nsig * 3, 512, smem>>>((const float2*)x, T, (__half*)feats);
+    features_kernel<<<nsig * NIN, 512, smem>>>((const float2*)x, T, (__half*)feats);
     PCK(cudaGetLastError());
     PCK(cudaDeviceSynchronize());
     return CYC_OK;
@@ -647,10 +634,11 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
 {
     if (!n || !x || k <= 0 || k > NBIN || !alphas_conv || !alphas_conj || !used_fallback)
         return pfail(CYC_EINVAL, "cyc_propose: bad argument");
-    if (T < (int64_t)NSEG * NFFT) return pfail(CYC_EINVAL, "cyc_propose: needs at least %d samples", NSEG * NFFT);
+    if (T < (int64_t)NSEG * NFFT + MAXD)
+        return pfail(CYC_EINVAL, "cyc_propose: needs at least %d samples", NSEG * NFFT + MAXD);
     cudaSetDevice(n->device);
     const float2* xd = (const float2*)x;
-    const int64_t use = (int64_t)NSEG * NFFT;
+    const int64_t use = (int64_t)NSEG * NFFT + MAXD;
     if (!on_device) {
         if (n->xcap < use) {
             if (n->xbuf) cudaFree(n->xbuf);
@@ -665,21 +653,19 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
     rc = net_forward(n, n->feats, 1, 0);
     if (rc) return rc;
     pool_loss_kernel<<<(2 * NBIN + 255) / 256, 256>>>(n->z4, nullptr, 1, 1.f, n->logits, nullptr, nullptr);
-    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf, n->nhot);
+    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf);
     PCK(cudaGetLastError());
     std::vector<int> idx(2 * k);
     float cf[2];
-    int hot[2];
     PCK(cudaMemcpy(idx.data(), n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost));
     PCK(cudaMemcpy(cf, n->conf, sizeof cf, cudaMemcpyDeviceToHost));
-    PCK(cudaMemcpy(hot, n->nhot, sizeof hot, cudaMemcpyDeviceToHost));
     for (int r = 0; r < k; ++r) {
         alphas_conv[r] = -0.5 + idx[r] / (double)NBIN;
         alphas_conj[r] = -0.5 + idx[k + r] / (double)NBIN;
     }
     const float c = fminf(cf[0], cf[1]);
     if (conf) *conf = c;
-    *used_fallback = (c < tau || hot[0] > k || hot[1] > k) ? 1 : 0;
+    *used_fallback = c < tau ? 1 : 0;
     return CYC_OK;
 }
 

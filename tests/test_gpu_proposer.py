@@ -10,7 +10,7 @@ from synth import workloads
 
 pytestmark = pytest.mark.gpu
 
-NS = 1 << 16
+NS = (1 << 16) + 16          # 16 x 4096 feature samples plus the largest feature lag
 
 
 def oracle_params(flat):
@@ -34,7 +34,7 @@ def gpu_features(cyc, xs):
     import torch
     n = xs.shape[0]
     xd = torch.from_numpy(xs.view(np.float32)).cuda()
-    f = torch.empty((n, 3, 4096), dtype=torch.float16, device="cuda")
+    f = torch.empty((n, 11, 4096), dtype=torch.float16, device="cuda")
     cyc.cyc_features(xd, NS, n, f)
     return f
 

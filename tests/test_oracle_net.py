@@ -59,7 +59,7 @@ def test_bce_closed_forms():
 def test_full_net_gradient_finite_differences():
     params = on.init_params(3)
     rng = np.random.default_rng(2)
-    feat = rng.normal(size=(3, on.NFFT))
+    feat = rng.normal(size=(on.NIN, on.NFFT))
     lab = (rng.uniform(size=(2, on.NBIN)) < 0.05).astype(float)
     loss, grads = on.batch_loss_and_grads(params, [feat], [lab], pos_weight=3.0)
     eps = 1e-5
@@ -76,13 +76,30 @@ def test_full_net_gradient_finite_differences():
 
 
 def test_tone_feature_lines():
-    """x = exp(j 2 pi f0 n): the x channel peaks at f0, x^2 at 2 f0, |x|^2 is flat but for DC."""
+    """x = exp(j 2 pi f0 n): the x channel peaks at f0, x^2 at 2 f0, and every lag product
+    x[n+d] x*[n] = exp(j 2 pi f0 d) is constant: its line is at 0."""
     f0 = 0.1171875                                   # on the 4096-bin grid: 480/4096
-    n = np.arange(on.NSEG * on.NFFT)
+    n = np.arange(on.NEED)
     x = np.exp(2j * np.pi * f0 * n)
     F = on.features(x)
     j = lambda f: int(round((f + 0.5) * on.NFFT)) % on.NFFT
+    assert F.shape == (on.NIN, on.NFFT)
     assert int(np.argmax(F[0])) == j(f0)
     assert int(np.argmax(F[1])) == j(2 * f0)
-    assert int(np.argmax(F[2])) == j(0.0)
+    for c in range(2, on.NIN):
+        assert int(np.argmax(F[c])) == j(0.0)
+
+
+def test_lag_product_channel_shows_a_conventional_line():
+    """Rectangular BPSK at 8 samples/symbol: the lag-4 product has a line at 1/8 (its cyclic
+    autocorrelation at lag 4 is nonzero at the baud rate), the |x|^2 channel has none."""
+    import synth
+    x = synth.rect_bpsk(on.NEED, sps=8, seed=5)
+    F = on.features(x)
+    j = lambda f: int(round((f + 0.5) * on.NFFT)) % on.NFFT
+    c4 = 2 + on.LAG_CHANNELS.index(4)
+    k = j(0.125)
+    assert F[c4, k] > 3.0 and F[c4, k] > np.median(F[c4]) + 3.0
+    assert F[c4, k] > F[c4, k - 5] + 2.0 and F[c4, k] > F[c4, k + 5] + 2.0
+    assert abs(F[2, k] - np.median(F[2])) < 1e-6     # |x|^2 = 1: no line at 1/8
     assert np.allclose(F.mean(axis=1), 0.0, atol=1e-9) and np.allclose(F.std(axis=1), 1.0, atol=1e-9)
