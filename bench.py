@@ -160,15 +160,17 @@ def oracle_sample_rate(x, lags, alphas, target_s=10.0, max_T=1 << 16):
     return cmac / dt / 1e9, n, dt
 
 
-def sampled_error(R, x, lags, alphas, nent=8, seed=3):
-    import oracle
-    rng = np.random.default_rng(seed)
-    f = rng.integers(0, 2, nent)
-    ia = rng.integers(0, len(alphas), nent)
-    im = rng.integers(0, len(lags), nent)
-    M = int(np.max(lags))
-    Ro, _ = oracle.entries(x, M, f + 1, np.asarray(alphas)[ia], np.asarray(lags)[im])
-    return float(np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, M))
+def stored_error(R, key, T):
+    """max |R - R_oracle| / R^0(0) over the sampled entries that tests/golden/bench_entries.json
+    holds for workload `key` (FP64 oracle values written by make_bench_entries.py beside it);
+    None when the run's stream length differs from the stored one."""
+    with open(os.path.join(ROOT, "tests", "golden", "bench_entries.json")) as fh:
+        g = json.load(fh)[key]
+    if g["T"] != T:
+        return None
+    ref = np.array(g["re"]) + 1j * np.array(g["im"])
+    got = R[g["form"], g["alpha_index"], g["lag_index"]]
+    return float(np.max(np.abs(got - ref)) / g["r00"])
 
 
 # --------------------------------------------------------------------------- serving leg
@@ -267,6 +269,77 @@ def serving_leg(pkg, seconds=3.0, loads=(0.5, 0.9), nbase=16, blen=3 << 19):
             res.append(r)
         out["loads"] = res
     return out
+
+
+def latency_leg(pkg, calls=1000, warm=20):
+    """Config 0: one 65536-sample GMSK chunk (BT 0.3, 8 sps, offset 0.05, 10 dB), lags 0..31,
+    64 cycle frequencies per form (k/8 CONV and 0.1 + k/8 CONJ, 8 distinct mod 1 each), FP32.
+    One call = reset + push of the resident chunk + read into host memory, on one stream
+    per form; per-call wall time percentiles over `calls` calls."""
+    import torch
+    from synth import workloads
+    w = workloads.config0()
+    x_dev = torch.from_numpy(w["x"].view(np.float32)).cuda()
+    T = w["x"].size
+    lags = w["lags"]
+    outs = [np.empty((1, 64, 32), dtype=np.complex128) for _ in range(2)]
+    with pkg.Stream(lags, w["alphas_conv"], pkg.CYC_CONV, precision="fp32", max_chunk=T) as sc, \
+            pkg.Stream(lags, w["alphas_conj"], pkg.CYC_CONJ, precision="fp32", max_chunk=T) as sj:
+        def call():
+            for s, o in ((sc, outs[0]), (sj, outs[1])):
+                s.reset()
+                s.push(x_dev)
+                s.read(o)
+        for _ in range(warm):
+            call()
+        ts = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
+            call()
+            ts.append(time.perf_counter() - t0)
+    ts = np.array(ts) * 1e6
+    cmac = (T - 31) * 32 * 8 * 2
+    return {"workload": "cfg0 GMSK 65536 samples, lags 0..31, 64 a per form (8 distinct mod 1), CONV+CONJ, fp32",
+            "calls": calls, "p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99)),
+            "mean_us": float(ts.mean()), "gmac_s_at_p50": cmac / (np.percentile(ts, 50) * 1e-6) / 1e9,
+            "call": "reset + push (device chunk) + read (host) for each form"}
+
+
+def precision_leg(pkg, reps=3):
+    """Config 2: one 2^20-sample GMSK block (BT 0.5, 4 sps, 0 dB), lags 0..255, 4096 cycle
+    frequencies, both forms, in each precision: device time per block (CUDA events, median
+    of `reps` after one warm-up) and the error on sampled entries relative to R^0(0)."""
+    import torch
+    from synth import workloads
+    w = workloads.config2()
+    x, lags, alphas = w["x"], w["lags"], w["alphas"]
+    x_dev = torch.from_numpy(x.view(np.float32)).cuda()
+    T = x.size
+    cmac = (T - 255) * 256 * 4096 * 2
+    out = torch.empty((2, 4096, 256, 2), dtype=torch.float64, device="cuda")
+    res = {"workload": "cfg2 GMSK block 2^20 samples, lags 0..255, 4096 a -0.5+k/4096, CONV+CONJ"}
+    for prec in ("fp16", "bf16x3", "fp32"):
+        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=prec, max_chunk=T) as s:
+            def blk():
+                s.reset()
+                s.push(x_dev)
+                s.read(out)
+            blk()
+            ms = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                blk()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            R = out.cpu().numpy()
+        R = R[..., 0] + 1j * R[..., 1]
+        m = statistics.median(ms)
+        res[prec] = {"ms": m, "gmac_s": cmac / (m * 1e-3) / 1e9, "tol": TOL[prec],
+                     "err_rel_r00": stored_error(R, "cfg2", T)}
+    return res
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -428,7 +501,7 @@ def run_ours(args):
         "gpu_launches": kernels, "roofline": roof, "clocks": clocks,
     }
     if rank == 0:
-        line["err_rel_r00"] = sampled_error(R, x, lags, alphas)
+        line["err_rel_r00"] = stored_error(R, "cfg1", ARGS_SAMPLES[0])
         line["err_tol"] = TOL[precision]
 
     if rank == 0 and not args.no_e2e:
@@ -442,11 +515,15 @@ def run_ours(args):
         k = max(1, min(args.steps, 2))
         ms32, R32, pms, pl, _ = time_device_steps(pkg, x_dev, lags, alphas, "fp32", k, 1, 1, True)
         line["plain_fp32"] = {"value": cmac_per_step() / (ms32 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms32,
-                              "steps": k, "err_rel_r00": sampled_error(R32, x, lags, alphas)}
+                              "steps": k, "err_rel_r00": stored_error(R32, "cfg1", ARGS_SAMPLES[0])}
         line["speedup_vs_plain_fp32"] = value / world / line["plain_fp32"]["value"]
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_leg(pkg, seconds=args.serving_seconds)
         line["p99_ms"] = line["serving"]["loads"][-1]["p99_ms"]
+    if rank == 0 and not args.no_latency:
+        line["cfg0_latency"] = latency_leg(pkg)
+    if rank == 0 and not args.no_precisions:
+        line["cfg2_precisions"] = precision_leg(pkg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
@@ -474,6 +551,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
+    ap.add_argument("--no-latency", action="store_true", help="skip the config-0 per-call latency leg")
+    ap.add_argument("--no-precisions", action="store_true", help="skip the config-2 precision leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")

@@ -100,8 +100,8 @@ def test_trained_proposer_recall_and_gain(cyc):
     import torch
     if not os.path.exists(pt.WEIGHTS):
         pytest.skip("no trained weights committed")
-    n = 128
-    xs = np.stack([workloads.mix_stream(i, NS, seed_base=pt.SEED_TEST) for i in range(n)]).astype(np.complex64)
+    n = 512
+    xs = pt.make_signals(n, pt.SEED_TEST)
     xd = torch.from_numpy(xs.view(np.float32)).cuda().view(n, NS * 2)
     labels = pt.label(cyc, xd, n)
     net = cyc.cyc_net_create(np.load(pt.WEIGHTS), 0)
@@ -109,5 +109,6 @@ def test_trained_proposer_recall_and_gain(cyc):
         r = pt.recall_and_gain(cyc, net, xd, labels)
     finally:
         cyc.cyc_net_destroy(net)
+    assert r["detections"] >= 100, r
     assert r["recall"] >= 0.99, r
     assert r["work_ratio"] > 4.0, r
