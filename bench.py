@@ -342,6 +342,58 @@ def precision_leg(pkg, reps=3):
     return res
 
 
+def proposer_leg(pkg, nsig=64, k=32, pushes=64):
+    """Config 4: what the learned proposer buys.  One-off cost of a proposal (features, net,
+    top-k, confidence) per held-out 65552-sample signal of the serving mix, and the cost of
+    estimating 2^16 further samples of a stream (lags 0..63, both forms, BF16x3) on the full
+    512-point grid against the proposed cycle frequencies (the 2k proposals of both forms in
+    one stream); with the recall of those proposals against the full-grid detections."""
+    import torch
+    from paper_2405_16911_gb300 import proposer_train as pt
+    xs = pt.make_signals(nsig, pt.SEED_TEST)
+    xd = torch.from_numpy(xs.view(np.float32)).cuda().view(nsig, pt.NS * 2)
+    labels = pt.label(pkg, xd, nsig)
+    net = pkg.cyc_net_create(np.load(pt.WEIGHTS), 0)
+    try:
+        props = [pkg.cyc_propose(net, xd[i], pt.NS, k=k) for i in range(2)]     # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        props = [pkg.cyc_propose(net, xd[i], pt.NS, k=k) for i in range(nsig)]
+        t_prop = (time.perf_counter() - t0) / nsig
+        rec = pt.recall_and_gain(pkg, net, xd, labels, k=k)
+    finally:
+        pkg.cyc_net_destroy(net)
+    C = 1 << 16
+    y = torch.from_numpy(np.concatenate([xs[i % nsig] for i in range(2 * pushes * C // pt.NS + 2)])[:pushes * C]
+                         .view(np.float32)).cuda()
+
+    def per_push(alphas):
+        with pkg.Stream(pt.LAGS, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C) as s:
+            def run():
+                s.reset()
+                for c in range(pushes):
+                    s.push(y[2 * c * C:2 * (c + 1) * C])
+                s.sync()
+            run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) * 1e-3 / pushes
+
+    t_full = per_push(pt.GRID)
+    t_top = per_push(np.concatenate([props[0][0], props[0][1]]))
+    return {"workload": "cfg4 held-out serving-mix signals (65552 samples), lags 0..63, 512-point grid, "
+                        "top-%d per form" % k,
+            "signals": nsig, "recall": rec["recall"], "detections": rec["detections"],
+            "fallback_rate": rec["fallback_rate"], "projection_work_ratio": rec["work_ratio"],
+            "propose_ms_per_signal": t_prop * 1e3,
+            "full_grid_us_per_2^16_samples": t_full * 1e6, "proposed_us_per_2^16_samples": t_top * 1e6,
+            "breakeven_samples": (t_prop / max(t_full - t_top, 1e-12)) * C if t_full > t_top else None}
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -524,6 +576,8 @@ def run_ours(args):
         line["cfg0_latency"] = latency_leg(pkg)
     if rank == 0 and not args.no_precisions:
         line["cfg2_precisions"] = precision_leg(pkg)
+    if rank == 0 and not args.no_proposer:
+        line["cfg4_proposer"] = proposer_leg(pkg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
@@ -553,6 +607,7 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=3.0)
     ap.add_argument("--no-latency", action="store_true", help="skip the config-0 per-call latency leg")
     ap.add_argument("--no-precisions", action="store_true", help="skip the config-2 precision leg")
+    ap.add_argument("--no-proposer", action="store_true", help="skip the config-4 proposer leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")

@@ -62,6 +62,10 @@ extern "C" {
 #define CYC_P_FP32   0       /* FP32 CUDA-core complex GEMM, FP32 accumulate */
 #define CYC_P_FP16   1       /* tensor cores, FP16 operands, one pass, FP32 accumulate */
 #define CYC_P_BF16X3 2       /* tensor cores, BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+/* The tensor-core passes of cyc_push run on pairs of SMs (two-CTA clusters issuing
+ * cta_group::2 MMAs) when the device can hold such clusters; the environment variable
+ * CYC_TC_PAIR=0, read when a stream is created, selects the one-CTA kernel instead.  Both
+ * compute the same products in the same order of terms per tile. */
 
 typedef struct cyc_stream cyc_stream;   /* opaque, owned by the library */
 
@@ -118,7 +122,8 @@ CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);
 /* cyc_sync: wait until all work queued by this stream has finished. */
 CYC_API int cyc_sync(cyc_stream* s);
 
-/* cyc_reset: drop all samples and sums (parameters kept). */
+/* cyc_reset: drop all samples and sums (parameters kept).  The zeroing of the sums is
+ * queued on the stream's CUDA stream; the call does not wait for it. */
 CYC_API int cyc_reset(cyc_stream* s);
 
 /* cyc_destroy: free the handle and its device memory (NULL is a no-op). */

@@ -1,6 +1,7 @@
 // cyc_api.cu -- host side of libcyc: stream state, ingest with the carried tail, the
 // projection passes, FP64 running sums, read-out, save/load.  Declared in include/cyc.h.
 #include <math.h>
+#include <stdlib.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -103,6 +104,7 @@ struct cyc_stream {
     int device = 0;
     cudaStream_t st = nullptr;
     int num_sms = 1;
+    int pair_ctas = 0;              // > 0: tensor-core passes run as two-CTA pairs
     int precision = CYC_P_FP32;
     int conj_flag = 0;
     int F = 0;
@@ -130,6 +132,7 @@ struct cyc_stream {
     size_t part_elems = 0;
     double2* d_out = nullptr;
     int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
+    int* h_err = nullptr;       // page-locked copy, read after a stream synchronisation
     // profiling
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -150,9 +153,10 @@ struct cyc_stream {
         void* ps[] = {stage[0], stage[1], sums, d_phi, d_amap, d_col_lag, d_col_conj, part, d_out, d_err};
         for (void* p : ps)
             if (p) cudaFree(p);
+        if (h_err) cudaFreeHost(h_err);
         stage[0] = stage[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
-        d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr;
+        d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
     }
 };
 
@@ -214,6 +218,8 @@ int alloc_state(cyc_stream* s)
     CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
     CK(cudaMalloc(&s->d_err, sizeof(int)));
     CK(cudaMemset(s->d_err, 0, sizeof(int)));
+    CK(cudaMallocHost(&s->h_err, sizeof(int)));
+    *s->h_err = 0;
     return CYC_OK;
 }
 
@@ -235,7 +241,7 @@ int project(cyc_stream* s, int64_t nc)
     a.x_avail = (s->M + s->max_chunk + kStagePad) & ~(int64_t)1;
     // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
     const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
-    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms)
+    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)
                   : small                    ? small_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : fp32_plan(s->Au, s->ncols, nc, s->num_sms);
     a.nsplit = pl.nsplit;
@@ -253,7 +259,7 @@ int project(cyc_stream* s, int64_t nc)
         }
         CK(cudaEventRecord(ev.first, s->st));
     }
-    CK(s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->st)
+    CK(s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->pair_ctas > 0, s->st)
        : small                    ? small_launch(a, s->st)
                                   : fp32_launch(a, s->st));
     if (s->prof) {
@@ -267,12 +273,16 @@ int project(cyc_stream* s, int64_t nc)
 }
 
 // After a stream synchronisation: did a kernel's bounded wait give up?
-int check_device_status(cyc_stream* s)
+// Queues the copy of the kernels' status word, synchronises the stream and reports it.
+int sync_and_check(cyc_stream* s)
 {
-    int flag = 0;
-    CK(cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const int flag = *s->h_err;
     if (flag) {
-        CK(cudaMemset(s->d_err, 0, sizeof(int)));
+        *s->h_err = 0;
+        CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st));
+        CK(cudaStreamSynchronize(s->st));
         return fail(CYC_ETIMEDOUT, "a projection kernel gave up waiting (code %d); the sums are unreliable", flag);
     }
     return CYC_OK;
@@ -371,6 +381,10 @@ int cyc_create_ex(const cyc_params* p, cyc_stream** out)
         delete s;
         return fail(CYC_ECUDA, "cannot query the SM count");
     }
+    if (s->precision != CYC_P_FP32) {
+        const char* ev = getenv("CYC_TC_PAIR");
+        s->pair_ctas = (ev && ev[0] == '0') ? 0 : tc_pair_ctas(s->precision);
+    }
     rc = alloc_state(s);
     if (rc) {
         s->free_all();
@@ -428,8 +442,7 @@ int cyc_sync(cyc_stream* s)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_sync: handle is NULL");
     DeviceGuard g(s->device);
-    CK(cudaStreamSynchronize(s->st));
-    return check_device_status(s);
+    return sync_and_check(s);
 }
 
 int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
@@ -447,8 +460,7 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     s->kernel_launches++;
     if (!dev)
         CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
-    return check_device_status(s);
+    return sync_and_check(s);
 }
 
 int cyc_reset(cyc_stream* s)
@@ -456,7 +468,6 @@ int cyc_reset(cyc_stream* s)
     if (!s) return fail(CYC_EINVAL, "cyc_reset: handle is NULL");
     DeviceGuard g(s->device);
     CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
-    CK(cudaStreamSynchronize(s->st));
     s->T = s->n_eff = s->held = 0;
     return CYC_OK;
 }

@@ -70,8 +70,11 @@ size_t      small_max_partials(int Au, int ncols, int num_sms);
 
 // Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu).
 bool        tc_supported(int ncols, int M);
-ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms);
-cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
+// pair_ctas: CTAs that can run as resident two-CTA clusters (tc_pair_ctas), 0 for the
+// one-CTA kernel; tc_launch(pair = true) then runs cta_group::2 pairs.
+int         tc_pair_ctas(int precision);
+ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas);
+cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t st);
 size_t      tc_max_partials(int Au, int ncols, int num_sms);
 int         tc_tile_rows();     // cycle frequencies per work item
 int         tc_tile_cols();     // columns per work item

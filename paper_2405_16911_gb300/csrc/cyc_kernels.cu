@@ -8,7 +8,7 @@ namespace {
 // dozen terms, each already a sum over thousands of samples) and the total once in FP64:
 // FP64 arithmetic is scarce on this GPU, so it is kept to one add per value and push.
 // Each thread folds two neighbouring elements with one 16-byte load per split and keeps
-// four loads in flight.
+// eight loads in flight.
 __global__ void reduce_partials_kernel(const float2* __restrict__ part, int nsplit, int n_uc,
                                        double2* __restrict__ sums)
 {
@@ -19,15 +19,17 @@ __global__ void reduce_partials_kernel(const float2* __restrict__ part, int nspl
         const size_t stride = (size_t)n_uc / 2;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         int s = 0;
-        for (; s + 4 <= nsplit; s += 4) {
-            float4 v0 = __ldg(p + (size_t)(s + 0) * stride);
-            float4 v1 = __ldg(p + (size_t)(s + 1) * stride);
-            float4 v2 = __ldg(p + (size_t)(s + 2) * stride);
-            float4 v3 = __ldg(p + (size_t)(s + 3) * stride);
-            acc.x += (v0.x + v1.x) + (v2.x + v3.x);
-            acc.y += (v0.y + v1.y) + (v2.y + v3.y);
-            acc.z += (v0.z + v1.z) + (v2.z + v3.z);
-            acc.w += (v0.w + v1.w) + (v2.w + v3.w);
+        for (; s + 8 <= nsplit; s += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(p + (size_t)(s + k) * stride);
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                acc.x += v[k].x + v[k + 1].x;
+                acc.y += v[k].y + v[k + 1].y;
+                acc.z += v[k].z + v[k + 1].z;
+                acc.w += v[k].w + v[k + 1].w;
+            }
         }
         for (; s < nsplit; ++s) {
             float4 v = __ldg(p + (size_t)s * stride);

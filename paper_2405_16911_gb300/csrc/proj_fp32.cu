@@ -10,7 +10,10 @@
 // reduced exactly as a u64 product phi * n mod 2^64, so n may run far past 2^30.
 //
 // Tile: 128 cycle frequencies x 128 columns per CTA, 16 samples per K-tile, 256 threads,
-// 8 x 8 complex accumulators per thread, double-buffered operand tiles.
+// 8 x 8 complex accumulators per thread, double-buffered operand tiles.  The register sums
+// are added into the CTA's own partial every FLUSH samples and restarted, so no FP32 chain
+// is longer than FLUSH terms (a sequential FP32 sum of 2^20 positive terms drifts by about
+// 1e-4 of its value; one of 4096 terms by a few 1e-6).
 #include "cyc_impl.h"
 #include "cyc_device.cuh"
 
@@ -21,6 +24,7 @@ constexpr int TA = 128;    // cycle frequencies per CTA
 constexpr int TC = 128;    // columns per CTA
 constexpr int TK = 16;     // samples per K-tile
 constexpr int NT = 256;    // threads
+constexpr int FLUSH = 4096; // samples per register-sum chain
 
 struct Smem {
     float2 w[2][TK][TA];
@@ -55,6 +59,32 @@ __device__ __forceinline__ void gen_tile(const ProjArgs& a, Smem& sm, int buf, i
     }
 }
 
+// Adds (or, for the first chain, writes) the thread's 8 x 8 sums into the partial tile.
+__device__ __forceinline__ void flush_sums(float2* out, const ProjArgs& a, int u0, int c0, int tx, int ty,
+                                          float (&acc_r)[8][8], float (&acc_i)[8][8], bool add)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int u = u0 + 2 * ty + (i & 1) + 32 * (i >> 1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            int c = c0 + 2 * tx + (j & 1) + 32 * (j >> 1);
+            if (u < a.Au && c < a.ncols) {
+                float2* o = &out[(size_t)u * a.ncols + c];
+                float2 v = make_float2(acc_r[i][j], acc_i[i][j]);
+                if (add) {
+                    const float2 q = *o;
+                    v.x += q.x;
+                    v.y += q.y;
+                }
+                *o = v;
+            }
+            acc_r[i][j] = 0.f;
+            acc_i[i][j] = 0.f;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(NT, 1) proj_fp32_kernel(ProjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -83,10 +113,16 @@ __global__ void __launch_bounds__(NT, 1) proj_fp32_kernel(ProjArgs a)
 #pragma unroll
         for (int j = 0; j < 8; ++j) { acc_r[i][j] = 0.f; acc_i[i][j] = 0.f; }
 
+    float2* out = a.part + (size_t)split * a.Au * a.ncols;
+    bool flushed = false;
     int buf = 0;
     if (n_beg < n_end) gen_tile(a, sm, 0, n_beg, n_end, phi_g, a_ok, gen_a, lag_g, conj_g, c_ok, gen_c, k0);
     __syncthreads();
     for (int64_t nt = n_beg; nt < n_end; nt += TK) {
+        if (nt > n_beg && (nt - n_beg) % FLUSH == 0) {
+            flush_sums(out, a, u0, c0, tx, ty, acc_r, acc_i, flushed);
+            flushed = true;
+        }
         if (nt + TK < n_end)
             gen_tile(a, sm, buf ^ 1, nt + TK, n_end, phi_g, a_ok, gen_a, lag_g, conj_g, c_ok, gen_c, k0);
 #pragma unroll 4
@@ -118,17 +154,7 @@ __global__ void __launch_bounds__(NT, 1) proj_fp32_kernel(ProjArgs a)
     }
 
     // partials: thread's rows are 2ty + {0,1} + 32 j, columns 2tx + {0,1} + 32 j
-    float2* out = a.part + (size_t)split * a.Au * a.ncols;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int u = u0 + 2 * ty + (i & 1) + 32 * (i >> 1);
-        if (u >= a.Au) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            int c = c0 + 2 * tx + (j & 1) + 32 * (j >> 1);
-            if (c < a.ncols) out[(size_t)u * a.ncols + c] = make_float2(acc_r[i][j], acc_i[i][j]);
-        }
-    }
+    flush_sums(out, a, u0, c0, tx, ty, acc_r, acc_i, flushed);
 }
 
 int tiles_of(int Au, int ncols) { return ((Au + TA - 1) / TA) * ((ncols + TC - 1) / TC); }

@@ -8,8 +8,11 @@
 // K = 16 step:
 //     D_r += [Wr | -Wi] . [Pr ; Pi]        D_i += [Wi | Wr] . [Pr ; Pi]
 // D_r and D_i live in TMEM columns [0, 256) and [256, 512).  The weights carry the absolute
-// sample index, so the whole n-range of an item accumulates in TMEM without any per-tile
-// rotation; the epilogue writes one FP32 partial tile per item.
+// sample index, so an item accumulates in TMEM without any per-tile rotation.  The tensor
+// core's FP32 accumulation drifts with the length of the chain (on the mean-power entry,
+// about 1e-3 of its value over 2^19 samples), so an item longer than SUBG groups (4096
+// samples) runs as consecutive sub-items, each a fresh TMEM chain: the first writes the
+// item's FP32 partial tile, the later ones add to it.
 // Operands go through a ring of shared-memory stages (one 8-sample group each), K-major,
 // no swizzle, 8-row x 16-byte core matrices:
 //   P block: row r (column), chunk k (0: Pr, 1: Pi) at (r/8)*256 + k*128 + (r%8)*16
@@ -38,6 +41,14 @@
 //
 // Two launch modes share the code: one item per CTA derived from the grid (cyc_push), and a
 // persistent list of items taken with an atomic counter (the multi-stream server).
+//
+// CTA pairs (grid mode): a cluster of two CTAs on two SMs takes two neighbouring 128-row
+// cycle-frequency tiles over the same columns and samples and issues cta_group::2 MMAs with
+// M = 256.  Each CTA forms the weights of its own 128 rows (A) and half of the B rows: the
+// even CTA B rows [0, N/2), the odd one [N/2, N) -- so each SM forms half the lag products
+// and its tensor core reads half of B from its own shared memory.  Producers of both CTAs
+// arrive on the even CTA's full[s]; the even CTA's MMA thread signals empty[s] and done in
+// both CTAs through a multicast commit.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -62,6 +73,23 @@ constexpr int XSLOT = 3072;              // samples per staging slot (block + ha
 constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
 constexpr uint32_t TM_DR = 0, TM_DI = 256;
 constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
+constexpr int SUBG = 512;                // groups per TMEM accumulation chain (4096 samples)
+constexpr int SUBN = SUBG * 8;           // samples per sub-item
+
+// Waits and arrivals on the stage barriers: cluster scope when the pair shares them.
+template <bool PAIR>
+__device__ __forceinline__ bool bwait(void* bar, uint32_t parity)
+{
+    if constexpr (PAIR) return tc::mbar_wait_cluster(bar, parity, WAIT_BUDGET);
+    else return tc::mbar_wait(bar, parity, WAIT_BUDGET);
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void full_arrive(void* bar)
+{
+    if constexpr (PAIR) tc::mbar_arrive_remote(bar, 0);     // the even CTA's barrier
+    else tc::mbar_arrive(bar);
+}
 
 template <int PREC>
 struct Cfg;
@@ -123,8 +151,76 @@ struct Bars {
     uint32_t tmem;
     int item;
     int abort;
+    int add;                                    // this sub-item adds to the partial tile
+    int64_t sub_end;                            // n_end of the whole item
     TcItem it;
 };
+
+// Columns c, c + 1 of one partial-tile row (only those below cmax exist), written or added.
+__device__ __forceinline__ void put2(float2* out, int c, float4 v, bool vec, int cmax, bool add)
+{
+    if (vec && c + 1 < cmax) {
+        float4* o = reinterpret_cast<float4*>(&out[c]);
+        if (add) {
+            const float4 q = *o;
+            v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+        }
+        *o = v;
+        return;
+    }
+    if (c < cmax) {
+        float2 w = make_float2(v.x, v.y);
+        if (add) { w.x += out[c].x; w.y += out[c].y; }
+        out[c] = w;
+    }
+    if (c + 1 < cmax) {
+        float2 w = make_float2(v.z, v.w);
+        if (add) { w.x += out[c + 1].x; w.y += out[c + 1].y; }
+        out[c + 1] = w;
+    }
+}
+
+// Epilogue warp (TMEM lane quadrant q): its 32 rows of the item's D tile into the FP32
+// partial tile.  Wide items: D columns r, r + 128 <-> tile columns 2r, 2r + 1; narrow items:
+// D column r <-> tile column r.  live = false writes zeros.
+__device__ __forceinline__ void drain_tile(uint32_t tmem, int q, int lane, const TcItem& it, bool narrow,
+                                           bool live, bool add)
+{
+    const int row = q * 32 + lane;
+    const bool vec = (it.out_stride & 1) == 0;
+    const int cmax = it.ncols - it.c0;
+    float2* out = it.out + (size_t)row * it.out_stride;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    const bool mine = it.u0 + row < it.Au;
+    for (int cb = 0; cb < 16; ++cb) {
+        uint32_t dr0[8], di0[8], dr1[8], di1[8];
+        tc::tmem_ld8(lane_addr + TM_DR + cb * 8, dr0);
+        tc::tmem_ld8(lane_addr + TM_DI + cb * 8, di0);
+        if (!narrow) {
+            tc::tmem_ld8(lane_addr + TM_DR + 128 + cb * 8, dr1);
+            tc::tmem_ld8(lane_addr + TM_DI + 128 + cb * 8, di1);
+        }
+        tc::tmem_ld_wait();
+        if (!mine) continue;
+        if (narrow) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                const float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
+                                                    __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                put2(out, cb * 8 + j, v, vec, cmax, add);
+            }
+            continue;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
+                                                __uint_as_float(dr1[j]), __uint_as_float(di1[j]))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            put2(out, 2 * (cb * 8 + j), v, vec, cmax, add);
+        }
+    }
+}
 
 __device__ __forceinline__ void give_up(int* err, Bars* b, int code)
 {
@@ -155,20 +251,22 @@ __device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, i
     return it;
 }
 
-template <int PREC, bool LIST>
+template <int PREC, bool LIST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
 proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restrict__ nitems, int* counter, int* err)
 {
+    static_assert(!(LIST && PAIR), "CTA pairs run grid items only");
     using C = Cfg<PREC>;
     extern __shared__ __align__(1024) unsigned char smem[];
     Bars* bars = reinterpret_cast<Bars*>(smem + xslots_off<PREC>() + 2 * XSLOT * 8);
     float2* xs = reinterpret_cast<float2*>(smem + xslots_off<PREC>());
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (!LIST) err = pa.err;
+    const uint32_t crank = PAIR ? tc::cluster_rank() : 0u;
 
     if (tid == 0) {
         for (int s = 0; s < C::NSTAGE; ++s) {
-            tc::mbar_init(&bars->full[s], SET_WARPS);
+            tc::mbar_init(&bars->full[s], PAIR ? 2 * SET_WARPS : SET_WARPS);
             tc::mbar_init(&bars->empty[s], 1);
         }
         for (int k = 0; k < 2; ++k) {
@@ -177,11 +275,16 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         }
         tc::mbar_init(&bars->done, 1);
         bars->abort = 0;
+        bars->add = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == MMA_WARP) tc::tmem_alloc<512>(&bars->tmem);
+    if (warp == MMA_WARP) {
+        if constexpr (PAIR) tc::tmem_alloc_pair<512>(&bars->tmem);
+        else tc::tmem_alloc<512>(&bars->tmem);
+    }
     tc::tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) tc::cluster_sync();        // the other CTA's barriers exist before any arrival
     tc::tc_fence_after();
     const uint32_t tmem = bars->tmem;
 
@@ -193,17 +296,30 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
     int lastb = -1;                                 // loader: last block issued (running count)
 
     for (;;) {
-        // ---- next item (thread 0 fetches; everybody reads it after the barrier) ----
+        // ---- next (sub-)item (thread 0 fetches; everybody reads it after the barrier) ----
         if (tid == 0) {
             int idx = -1;
             if (!bars->abort) {
-                if (LIST) {
-                    idx = atomicAdd(counter, 1);
-                    if (idx >= *nitems) idx = -1;
-                    else bars->it = items[idx];
-                } else if (nit == 0) {
-                    idx = 0;
-                    bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
+                if (nit > 0 && bars->it.n_end < bars->sub_end) {
+                    // the next sub-item of the current item: a fresh TMEM chain that adds
+                    idx = bars->item;
+                    bars->it.n_beg = bars->it.n_end;
+                    bars->add = 1;
+                } else {
+                    bars->add = 0;
+                    if (LIST) {
+                        idx = atomicAdd(counter, 1);
+                        if (idx >= *nitems) idx = -1;
+                        else bars->it = items[idx];
+                    } else if (nit == 0) {
+                        idx = 0;
+                        bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
+                    }
+                    if (idx >= 0) bars->sub_end = bars->it.n_end;
+                }
+                if (idx >= 0) {
+                    const int64_t e = bars->it.n_beg + SUBN;
+                    bars->it.n_end = e < bars->sub_end ? e : bars->sub_end;
                 }
             }
             bars->item = idx;
@@ -226,9 +342,13 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             // -------------------------------------------------------- P warps (lag products)
             const int t = (warp - pset * SET_WARPS) * 32 + lane;     // 0..127
             const int c0 = it.c0, ncols = it.ncols;
-            // wide items: columns 2t, 2t+1 -> B rows t, t+128; narrow items: column t -> row t
-            const int jA = narrow ? t : 2 * t, jB = 2 * t + 1;
-            const bool okA = c0 + jA < ncols, okB = !narrow && c0 + jB < ncols;
+            // wide items: columns 2t, 2t+1 -> B rows t, t+128; narrow items: column t -> row t.
+            // CTA pairs hold B rows [N/2 rank, N/2 (rank + 1)): wide, thread t forms column
+            // 2t + rank (its B row t); narrow, threads t < 64 form column 64 rank + t.
+            const int jA = PAIR ? (narrow ? (t < 64 ? 64 * (int)crank + t : ncols) : 2 * t + (int)crank)
+                                : (narrow ? t : 2 * t);
+            const int jB = 2 * t + 1;
+            const bool okA = c0 + jA < ncols, okB = !PAIR && !narrow && c0 + jB < ncols;
             const int mA = okA ? it.col_lag[c0 + jA] : 0, mB = okB ? it.col_lag[c0 + jB] : 0;
             const bool cjA = okA && it.col_conj[c0 + jA], cjB = okB && it.col_conj[c0 + jB];
             const bool same_lag = okB && mA == mB;
@@ -247,8 +367,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     const uint32_t Gg = G + g;
                     if ((int)(Gg % NSET) != pset) continue;
                     const int s = Gg % C::NSTAGE;
-                    if (Gg >= (uint32_t)C::NSTAGE &&
-                        !tc::mbar_wait(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
+                    if (Gg >= (uint32_t)C::NSTAGE && !bwait<PAIR>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1)) {
                         give_up(err, bars, 1);
                         run = false;
                         break;
@@ -277,7 +396,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     pack8<C::BF>(piA, h, l);
                     st16(st + offA + P_LBO, h);
                     if (C::BF) st16(sl + offA + P_LBO, l);
-                    if (!narrow) {
+                    if (!PAIR && !narrow) {
                         pack8<C::BF>(prB, h, l);
                         st16(st + offB, h);
                         if (C::BF) st16(sl + offB, l);
@@ -287,7 +406,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     }
                     tc::fence_async_smem();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars->full[s]);
+                    if (lane == 0) full_arrive<PAIR>(&bars->full[s]);
                 }
                 __syncwarp();
                 if (run && lane == 0) tc::mbar_arrive(&bars->xempty[bg & 1]);
@@ -312,8 +431,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 const uint32_t Gg = G + g;
                 if ((int)(Gg % NSET) != pset) continue;
                 const int s = Gg % C::NSTAGE;
-                if (Gg >= (uint32_t)C::NSTAGE &&
-                    !tc::mbar_wait(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, WAIT_BUDGET)) {
+                if (Gg >= (uint32_t)C::NSTAGE && !bwait<PAIR>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1)) {
                     give_up(err, bars, 1);
                     break;
                 }
@@ -349,7 +467,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 }
                 tc::fence_async_smem();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&bars->full[s]);
+                if (lane == 0) full_arrive<PAIR>(&bars->full[s]);
             }
         } else if (warp == LOAD_WARP && lane == 0) {
             // -------------------------------------------------------- sample loader (TMA)
@@ -374,14 +492,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 }
                 lastb = (int)bg;
             }
-        } else if (warp == MMA_WARP && lane == 0) {
+        } else if (warp == MMA_WARP && lane == 0 && crank == 0) {
             // -------------------------------------------------------- MMA issuer
-            const uint32_t idesc = tc::idesc_f16(BM, narrow ? BN / 2 : BN, C::BF);
+            const uint32_t idesc = tc::idesc_f16(PAIR ? 2 * BM : BM, narrow ? BN / 2 : BN, C::BF);
             const uint32_t pbase = tc::smem_u32(smem);
             for (int g = 0; g < ngroups; ++g) {
                 const uint32_t Gg = G + g;
                 const int s = Gg % C::NSTAGE;
-                if (!tc::mbar_wait(&bars->full[s], (Gg / C::NSTAGE) & 1, WAIT_BUDGET)) {
+                if (!bwait<PAIR>(&bars->full[s], (Gg / C::NSTAGE) & 1)) {
                     give_up(err, bars, 2);
                     break;
                 }
@@ -396,67 +514,28 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     const uint64_t ar = tc::smem_desc(wb + 1 * W_LBO, W_LBO, W_SBO);
                     const uint64_t ai = tc::smem_desc(wb + 0 * W_LBO, W_LBO, W_SBO);
                     const uint32_t acc = (g > 0 || p > 0) ? 1u : 0u;
-                    tc::mma_f16(tmem + TM_DR, ar, bdesc, idesc, acc);
-                    tc::mma_f16(tmem + TM_DI, ai, bdesc, idesc, acc);
+                    if constexpr (PAIR) {
+                        tc::mma_f16_pair(tmem + TM_DR, ar, bdesc, idesc, acc);
+                        tc::mma_f16_pair(tmem + TM_DI, ai, bdesc, idesc, acc);
+                    } else {
+                        tc::mma_f16(tmem + TM_DR, ar, bdesc, idesc, acc);
+                        tc::mma_f16(tmem + TM_DI, ai, bdesc, idesc, acc);
+                    }
                 }
-                tc::mma_commit(&bars->empty[s]);
+                if constexpr (PAIR) tc::mma_commit_pair(&bars->empty[s], 3);
+                else tc::mma_commit(&bars->empty[s]);
             }
-            tc::mma_commit(&bars->done);
+            if constexpr (PAIR) tc::mma_commit_pair(&bars->done, 3);
+            else tc::mma_commit(&bars->done);
         }
 
         // ------------------------------------------------------------ epilogue (set 0 W warps)
         if (warp >= P_WARPS && warp < SET_WARPS) {
-            const bool got = tc::mbar_wait(&bars->done, nit & 1, WAIT_BUDGET);
+            const bool got = bwait<PAIR>(&bars->done, nit & 1);
             if (!got) give_up(err, bars, 3);
             tc::tc_fence_after();
-            const int q = warp & 3;
-            const int row = q * 32 + lane;
             const bool live = got && ngroups > 0 && !bars->abort;
-            const bool vec = (it.out_stride & 1) == 0;
-            float2* out = it.out + (size_t)row * it.out_stride;
-            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-            for (int cb = 0; cb < 8; ++cb) {
-                uint32_t dr0[16], di0[16], dr1[16], di1[16];
-                tc::tmem_ld16(lane_addr + TM_DR + cb * 16, dr0);
-                tc::tmem_ld16(lane_addr + TM_DI + cb * 16, di0);
-                if (!narrow) {
-                    tc::tmem_ld16(lane_addr + TM_DR + 128 + cb * 16, dr1);
-                    tc::tmem_ld16(lane_addr + TM_DI + 128 + cb * 16, di1);
-                }
-                tc::tmem_ld_wait();
-                if (it.u0 + row >= it.Au) continue;
-                if (narrow) {
-                    // D column r <-> tile column r
-#pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        const int c = cb * 16 + j;
-                        float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                                      __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (vec && it.c0 + c + 1 < it.ncols) {
-                            *reinterpret_cast<float4*>(&out[c]) = v;
-                        } else {
-                            if (it.c0 + c < it.ncols) out[c] = make_float2(v.x, v.y);
-                            if (it.c0 + c + 1 < it.ncols) out[c + 1] = make_float2(v.z, v.w);
-                        }
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int r = cb * 16 + j;               // B rows r, r + 128 <-> tile columns 2r, 2r+1
-                    const int c = 2 * r;
-                    float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                                  __uint_as_float(dr1[j]), __uint_as_float(di1[j]))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (vec && it.c0 + c + 1 < it.ncols) {
-                        *reinterpret_cast<float4*>(&out[c]) = v;
-                    } else {
-                        if (it.c0 + c < it.ncols) out[c] = make_float2(v.x, v.y);
-                        if (it.c0 + c + 1 < it.ncols) out[c + 1] = make_float2(v.z, v.w);
-                    }
-                }
-            }
+            drain_tile(tmem, warp & 3, lane, it, narrow, live, bars->add != 0);
         }
         G += ngroups;
         Bk += nblocks;
@@ -473,47 +552,94 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET);
     tc::tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) tc::cluster_sync();        // no MMA of the pair still reads this CTA
     if (warp == MMA_WARP) {
         tc::tc_fence_after();
-        tc::tmem_dealloc<512>(tmem);
+        if constexpr (PAIR) tc::tmem_dealloc_pair<512>(tmem);
+        else tc::tmem_dealloc<512>(tmem);
     }
 }
 
 int tiles_of(int Au, int ncols) { return ((Au + BM - 1) / BM) * ((ncols + BN - 1) / BN); }
 
-template <int PREC, bool LIST>
+template <int PREC, bool LIST, bool PAIR>
 cudaError_t set_smem()
 {
     static bool done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes<PREC>());
+    cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC, LIST, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<PREC>());
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
 template <int PREC>
-cudaError_t launch_grid(const ProjArgs& a, cudaStream_t st)
+cudaError_t launch_grid(const ProjArgs& a, bool pair, cudaStream_t st)
 {
-    cudaError_t e = set_smem<PREC, false>();
+    int gx = (a.Au + BM - 1) / BM;
+    const dim3 block(NTHREADS);
+    if (pair) {
+        cudaError_t e = set_smem<PREC, false, true>();
+        if (e != cudaSuccess) return e;
+        gx = (gx + 1) & ~1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(gx, (a.ncols + BN - 1) / BN, a.nsplit);
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem_bytes<PREC>();
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, proj_tc_kernel<PREC, false, true>, a, (const TcItem*)nullptr,
+                                  (const int*)nullptr, (int*)nullptr, (int*)nullptr);
+    }
+    cudaError_t e = set_smem<PREC, false, false>();
     if (e != cudaSuccess) return e;
-    dim3 grid((a.Au + BM - 1) / BM, (a.ncols + BN - 1) / BN, a.nsplit);
-    proj_tc_kernel<PREC, false><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(a, nullptr, nullptr, nullptr, nullptr);
+    dim3 grid(gx, (a.ncols + BN - 1) / BN, a.nsplit);
+    proj_tc_kernel<PREC, false, false><<<grid, block, smem_bytes<PREC>(), st>>>(a, nullptr, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 template <int PREC>
 cudaError_t launch_list(const TcItem* items, const int* nitems, int* counter, int grid, int* err, cudaStream_t st)
 {
-    cudaError_t e = set_smem<PREC, true>();
+    cudaError_t e = set_smem<PREC, true, false>();
     if (e != cudaSuccess) return e;
     ProjArgs none;
     none.x = nullptr; none.nc = 0; none.nbase = 0; none.phi = nullptr; none.Au = 0; none.col_lag = nullptr;
     none.col_conj = nullptr; none.ncols = 0; none.nsplit = 0; none.split_len = 0; none.part = nullptr;
-    proj_tc_kernel<PREC, true><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(none, items, nitems, counter, err);
+    proj_tc_kernel<PREC, true, false><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(none, items, nitems, counter, err);
     return cudaGetLastError();
+}
+
+// CTA pairs that can be resident at once (0: cluster launches unavailable).
+template <int PREC>
+int pair_slots()
+{
+    if (set_smem<PREC, false, true>() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem_bytes<PREC>();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, proj_tc_kernel<PREC, false, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace
@@ -523,10 +649,23 @@ bool tc_supported(int ncols, int M) { return ncols > 0 && M >= 0 && M <= MAX_LAG
 int tc_tile_rows() { return BM; }
 int tc_tile_cols() { return BN; }
 
-ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms)
+int tc_pair_ctas(int precision)
+{
+    const int n = precision == CYC_P_FP16 ? pair_slots<CYC_P_FP16>()
+                : precision == CYC_P_BF16X3 ? pair_slots<CYC_P_BF16X3>() : 0;
+    return 2 * n;
+}
+
+ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
 {
     int tiles = tiles_of(Au, ncols);
-    int want = num_sms >= tiles ? num_sms / tiles : 1;
+    int slots = num_sms;
+    if (pair_ctas > 0) {            // x tiles rounded up to whole pairs, one wave of pairs
+        const int tx = (Au + BM - 1) / BM;
+        tiles = ((tx + 1) & ~1) * ((ncols + BN - 1) / BN);
+        slots = pair_ctas < num_sms ? pair_ctas : num_sms;
+    }
+    int want = slots >= tiles ? slots / tiles : 1;
     int64_t len = (nc + want - 1) / want;
     if (len < 256) len = 256;
     len = (len + GS - 1) / GS * GS;
@@ -544,10 +683,10 @@ size_t tc_max_partials(int Au, int ncols, int num_sms)
     return want * (size_t)Au * (size_t)ncols;
 }
 
-cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st)
+cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t st)
 {
-    if (precision == CYC_P_FP16) return launch_grid<CYC_P_FP16>(a, st);
-    if (precision == CYC_P_BF16X3) return launch_grid<CYC_P_BF16X3>(a, st);
+    if (precision == CYC_P_FP16) return launch_grid<CYC_P_FP16>(a, pair, st);
+    if (precision == CYC_P_BF16X3) return launch_grid<CYC_P_BF16X3>(a, pair, st);
     return cudaErrorInvalidValue;
 }
 

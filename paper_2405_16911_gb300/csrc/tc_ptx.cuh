@@ -95,6 +95,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
                  : "r"(taddr));
 }
 
+// 32 lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- mbarriers ----------------------------------------------------------------------------
@@ -147,6 +156,80 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // Make this thread's generic-proxy shared-memory writes visible to the async proxy
 // (the tensor core reads operands through it).
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---- CTA pairs: a cluster of two CTAs on two SMs issuing cta_group::2 MMAs -----------------
+// The even-ranked CTA issues every MMA for the pair: M = 256 rows, 128 from each CTA's
+// shared memory (A) and each CTA's TMEM (D); the B operand is split by N, the first N/2
+// rows in the even CTA's shared memory, the rest in the odd CTA's, at the same offsets.
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of both CTAs; release/acquire orders the shared-memory state around it.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot)   // one warp in each CTA of the pair
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(slot)), "n"(NCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr) // one warp in each CTA of the pair
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" :: "r"(taddr), "n"(NCOLS) : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
+}
+
+// Arrive once on the mbarrier at this offset in every CTA of `mask` when the pair's
+// previously issued MMAs finish.
+__device__ __forceinline__ void mma_commit_pair(void* bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 :: "r"(smem_u32(bar)), "h"(mask) : "memory");
+}
+
+// Arrive (release, cluster scope) on the mbarrier at this offset in CTA `rank` of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote(void* bar, uint32_t rank)
+{
+    asm volatile("{\n.reg .b32 ra;\nmapa.shared::cluster.u32 ra, %0, %1;\n"
+                 "mbarrier.arrive.release.cluster.shared::cluster.b64 _, [ra];\n}\n"
+                 :: "r"(smem_u32(bar)), "r"(rank) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(void* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// As mbar_wait, with cluster-scope acquire (arrivals that come from the other CTA).
+__device__ __forceinline__ bool mbar_wait_cluster(void* bar, uint32_t parity, long long budget)
+{
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait_cluster(bar, parity))
+        if (clock64() - t0 > budget) return false;
+    return true;
+}
 
 }  // namespace tc
 }  // namespace cyc

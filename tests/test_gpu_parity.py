@@ -234,6 +234,7 @@ def test_config2_full_size_sampled(cyc, precision):
     k = int(round(((2 * w["f0"] + 0.125 + 0.5) % 1.0) * 4096)) % 4096
     f[0], ia[0], im[0] = 1, k, 0
     f[1], ia[1], im[1] = 1, 4095, 255
+    f[2], ia[2], im[2] = 0, 2048, 0                 # a = 0, m = 0: the mean power itself
     Ro, _ = oracle.entries(x, 255, f + 1, alphas[ia], lags[im])
     err = np.max(np.abs(R[f, ia, im] - Ro)) / oracle.r00(x, 255)
     assert err < TOL[precision], err
@@ -266,3 +267,40 @@ def test_fp32_small_and_general_paths(cyc, na):
     Ro, no = oracle.estimate(x, lags, alphas)
     assert neff == no
     assert rel_err(R, Ro, x, 89) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16"])
+def test_pair_and_single_tensor_core_kernels(cyc, precision, monkeypatch):
+    """cyc_push runs the tensor-core projection as two-CTA pairs by default and as single
+    CTAs with CYC_TC_PAIR=0: both against the oracle on wide items with an odd number of
+    cycle-frequency tiles, narrow items, and two column tiles."""
+    cases = [(9001, np.arange(128), 300), (7003, np.arange(41), 130), (6007, np.arange(200), 129)]
+    for i, (T, lags, na) in enumerate(cases):
+        x = synth.white(T, seed=120 + i).astype(np.complex64)
+        alphas = np.random.default_rng(20 + i).uniform(-0.5, 0.5, na)
+        Ro, no = oracle.estimate(x, lags, alphas)
+        out = {}
+        for pair in ("1", "0"):
+            monkeypatch.setenv("CYC_TC_PAIR", pair)
+            R, neff = run_gpu(cyc, x, lags, alphas, precision=precision, chunks=[T // 3, T - T // 3])
+            assert neff == no
+            assert rel_err(R, Ro, x, int(lags.max())) < TOL[precision], (i, pair)
+            out[pair] = R
+        assert rel_err(out["1"], out["0"], x, int(lags.max())) < TOL[precision] / 10
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_long_single_push_accumulation(cyc, precision):
+    """One push of 2^20 + 100 samples: every FP32 accumulation chain (tensor-memory or
+    register sums) is bounded, so even the all-positive mean-power entry a = 0, m = 0 keeps
+    its tolerance; 20 cycle frequencies so that FP32 takes the GEMM path."""
+    T = (1 << 20) + 100
+    x = (synth.white(T, seed=130) * 1.3 + 0.4).astype(np.complex64)
+    lags = np.array([0, 1, 7, 100])
+    alphas = np.concatenate([[0.0], np.random.default_rng(30).uniform(-0.5, 0.5, 19)])
+    R, neff = run_gpu(cyc, x, lags, alphas, precision=precision)
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert neff == no
+    r00 = oracle.r00(x, 100)
+    assert abs(R[0, 0, 0] - r00) / r00 < TOL[precision] / 4
+    assert rel_err(R, Ro, x, 100) < TOL[precision]
