@@ -6,7 +6,8 @@ shares no code with it; the two meet only through the seeded generators in ``syn
 
 ``estimate`` follows paper Sec. 4 Eq. (impl-corr) with x = y, m >= 0, absolute sample
 index n (origin at the first pushed sample) and normalisation by the number of terms
-N_eff = T - max(lags), as written out in ``cyc_oracle.c``.  Its pins (closed forms,
+N_eff = T - max(lags), as written out in ``cyc_oracle.c``; ``estimate_xy`` is the same
+equation in full (two inputs, signed lags, N_eff = T - M^- - M^+).  Its pins (closed forms,
 DFT special cases, brute force, invariants, statistics) live in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -51,6 +52,11 @@ def _load():
             lib.cyco_entries.restype = ctypes.c_int
             lib.cyco_r00.argtypes = [dp, i64, i32]
             lib.cyco_r00.restype = ctypes.c_double
+            lib.cyco_estimate_xy.argtypes = [dp, dp, i64, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                             i64, ctypes.c_int, dp, ctypes.POINTER(i64)]
+            lib.cyco_estimate_xy.restype = ctypes.c_int
+            lib.cyco_r00_xy.argtypes = [dp, dp, i64, i32, i32]
+            lib.cyco_r00_xy.restype = ctypes.c_double
             lib.cyco_max_threads.argtypes = []
             lib.cyco_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -116,3 +122,35 @@ def r00(x, M: int) -> float:
     """R^0(0) over the first T - M samples: the normaliser of every parity error."""
     xf = _as_x(x)
     return float(_load().cyco_r00(xf.ctypes.data, xf.size // 2, int(M)))
+
+
+def estimate_xy(x, y, lags, alphas, forms: int = CONV | CONJ, n0: int = 0, threads: int = 0):
+    """Eq. (impl-corr) with two inputs (y None: y = x) and signed lags: R complex128
+    [F][len(alphas)][len(lags)] and N_eff = T - M^- - M^+ (see cyc_oracle.c)."""
+    lib = _load()
+    xf = _as_x(x)
+    yf = None if y is None else _as_x(y)
+    if yf is not None and yf.size != xf.size:
+        raise ValueError("oracle: x and y differ in length")
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    F = len(_forms_list(forms))
+    out = np.zeros((F, alphas.size, lags.size, 2), dtype=np.float64)
+    neff = ctypes.c_int64(0)
+    rc = lib.cyco_estimate_xy(xf.ctypes.data, None if yf is None else yf.ctypes.data, xf.size // 2,
+                              lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, forms, int(n0),
+                              threads or max_threads(), out.ctypes.data, ctypes.byref(neff))
+    if rc == -2:
+        return None, 0
+    if rc != 0:
+        raise ValueError("oracle: bad arguments")
+    return out[..., 0] + 1j * out[..., 1], int(neff.value)
+
+
+def r00_xy(x, y, Mneg: int, Mpos: int) -> float:
+    """sqrt(mean|x|^2 mean|y|^2) over the committed range [M^-, T - M^+): the normaliser of
+    cross parity errors (R^0(0) there when y is None)."""
+    xf = _as_x(x)
+    yf = None if y is None else _as_x(y)
+    return float(_load().cyco_r00_xy(xf.ctypes.data, None if yf is None else yf.ctypes.data, xf.size // 2,
+                                     int(Mneg), int(Mpos)))

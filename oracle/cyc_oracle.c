@@ -144,6 +144,88 @@ double cyco_r00(const double* x, int64_t T, int32_t M)
     return s / (double)n_eff;
 }
 
+/*
+ * The estimator of Eq. (impl-corr) in full: two inputs x, y and signed lags.
+ *
+ *   R_f[a][m] = (1/N_eff) * sum_{n=Mneg}^{T-Mpos-1} x[n+m] * c_f(y[n]) * exp(-j 2 pi frac(a*(n0+n)))
+ *
+ *   Mneg  = max(0, -min(lags))   (M^- of Eq. (impl-corr): the window starts Mneg samples in)
+ *   Mpos  = max(0,  max(lags))
+ *   N_eff = max(0, T - Mneg - Mpos), one common n-range for every lag
+ *
+ * n is the absolute index of the y sample (phase origin at the first pushed sample); the
+ * paper's window-local phase differs by the constant factor exp(+j 2 pi a (n0 + Mneg)).
+ * y == NULL means y = x (the cyclic ACF / CCF); with y = x and all lags >= 0 this is
+ * exactly cyco_estimate.  Same layout, threads and return codes as cyco_estimate.
+ */
+static void entry_xy(const double* x, const double* y, int64_t n_lo, int64_t n_eff, int form, double a,
+                     int32_t m, int64_t n0, double* re, double* im)
+{
+    double sr = 0.0, si = 0.0;
+    for (int64_t n = n_lo; n < n_lo + n_eff; ++n) {
+        double xr = x[2 * (n + m)], xi = x[2 * (n + m) + 1];     /* x[n+m]    */
+        double yr = y[2 * n], yi = y[2 * n + 1];                 /* y[n]      */
+        if (form == CYCO_CONV) yi = -yi;                         /* conj(y[n]) */
+        double pr = xr * yr - xi * yi;
+        double pi = xr * yi + xi * yr;
+        double f = frac_an(a, n0 + n);
+        double c = cos(2.0 * M_PI * f), s = -sin(2.0 * M_PI * f);
+        sr += pr * c - pi * s;
+        si += pr * s + pi * c;
+    }
+    *re = sr / (double)n_eff;
+    *im = si / (double)n_eff;
+}
+
+int cyco_estimate_xy(const double* x, const double* y, int64_t T, const int32_t* lags, int nlags,
+                     const double* alphas, int nalphas, int forms, int64_t n0, int nthreads,
+                     double* out, int64_t* n_eff_out)
+{
+    if (!x || T < 0 || !lags || nlags <= 0 || !alphas || nalphas <= 0 || !out) return -1;
+    if ((forms & 3) == 0 || (forms & ~3)) return -1;
+    if (!y) y = x;
+    int32_t lo = 0, hi = 0;
+    for (int i = 0; i < nlags; ++i) {
+        if (lags[i] < lo) lo = lags[i];
+        if (lags[i] > hi) hi = lags[i];
+    }
+    const int64_t Mneg = -(int64_t)lo, Mpos = hi;
+    int64_t n_eff = T - Mneg - Mpos;
+    if (n_eff < 0) n_eff = 0;
+    if (n_eff_out) *n_eff_out = n_eff;
+    if (n_eff == 0) return -2;
+
+    int flist[2], F = 0;
+    if (forms & CYCO_CONV) flist[F++] = CYCO_CONV;
+    if (forms & CYCO_CONJ) flist[F++] = CYCO_CONJ;
+    int64_t total = (int64_t)F * nalphas * nlags;
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int64_t t = 0; t < total; ++t) {
+        int f = (int)(t / ((int64_t)nalphas * nlags));
+        int ia = (int)((t / nlags) % nalphas);
+        int im = (int)(t % nlags);
+        entry_xy(x, y, Mneg, n_eff, flist[f], alphas[ia], lags[im], n0, &out[2 * t], &out[2 * t + 1]);
+    }
+    return 0;
+}
+
+/* Normaliser of the cross error metric: sqrt(mean |x[n]|^2 * mean |y[n]|^2) over the
+ * committed n-range [Mneg, T - Mpos) (Cauchy-Schwarz bound of every entry's terms);
+ * for y == NULL this is R^0(0) over that range. */
+double cyco_r00_xy(const double* x, const double* y, int64_t T, int32_t Mneg, int32_t Mpos)
+{
+    int64_t n_eff = T - Mneg - Mpos;
+    if (!x || n_eff <= 0 || Mneg < 0 || Mpos < 0) return 0.0;
+    if (!y) y = x;
+    double sx = 0.0, sy = 0.0;
+    for (int64_t n = Mneg; n < Mneg + n_eff; ++n) {
+        sx += x[2 * n] * x[2 * n] + x[2 * n + 1] * x[2 * n + 1];
+        sy += y[2 * n] * y[2 * n] + y[2 * n + 1] * y[2 * n + 1];
+    }
+    return sqrt(sx / (double)n_eff) * sqrt(sy / (double)n_eff);
+}
+
 int cyco_max_threads(void)
 {
 #ifdef _OPENMP
