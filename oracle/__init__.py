@@ -57,6 +57,9 @@ def _load():
             lib.cyco_estimate_xy.restype = ctypes.c_int
             lib.cyco_r00_xy.argtypes = [dp, dp, i64, i32, i32]
             lib.cyco_r00_xy.restype = ctypes.c_double
+            lib.cyco_windows.argtypes = [dp, dp, i64, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, i64, i64,
+                                         i64, ctypes.c_int, dp, ctypes.POINTER(i64)]
+            lib.cyco_windows.restype = ctypes.c_int
             lib.cyco_max_threads.argtypes = []
             lib.cyco_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -154,3 +157,29 @@ def r00_xy(x, y, Mneg: int, Mpos: int) -> float:
     yf = None if y is None else _as_x(y)
     return float(_load().cyco_r00_xy(xf.ctypes.data, None if yf is None else yf.ctypes.data, xf.size // 2,
                                      int(Mneg), int(Mpos)))
+
+
+def windows(x, y, lags, alphas, win_len: int, hop: int, forms: int = CONV | CONJ, max_win: int = 1 << 20,
+            threads: int = 0):
+    """The block's windowed output, Eq. (impl-corr) at window starts n0 = k * hop with the
+    window-local phase: complex128 [nwin][F][len(alphas)][len(lags)] (see cyc_oracle.c)."""
+    lib = _load()
+    xf = _as_x(x)
+    yf = None if y is None else _as_x(y)
+    if yf is not None and yf.size != xf.size:
+        raise ValueError("oracle: x and y differ in length")
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    F = len(_forms_list(forms))
+    T = xf.size // 2
+    span = max(0, -int(lags.min())) + max(0, int(lags.max())) + int(win_len)
+    nmax = max(0, (T - span) // int(hop) + 1) if T >= span else 0
+    nmax = min(nmax, int(max_win))
+    out = np.zeros((max(nmax, 1), F, alphas.size, lags.size, 2), dtype=np.float64)
+    nw = ctypes.c_int64(0)
+    rc = lib.cyco_windows(xf.ctypes.data, None if yf is None else yf.ctypes.data, T, lags.ctypes.data, lags.size,
+                          alphas.ctypes.data, alphas.size, forms, int(win_len), int(hop), nmax,
+                          threads or max_threads(), out.ctypes.data, ctypes.byref(nw))
+    if rc != 0:
+        raise ValueError("oracle: bad arguments")
+    return out[:nmax, ..., 0] + 1j * out[:nmax, ..., 1]

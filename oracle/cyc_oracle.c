@@ -210,6 +210,67 @@ int cyco_estimate_xy(const double* x, const double* y, int64_t T, const int32_t*
     return 0;
 }
 
+/*
+ * The block's windowed output (Sec. 4, Eq. (impl-corr) at window start n0 = k * hop):
+ *
+ *   R_k,f[a][m] = (1/N) sum_{n=0}^{N-1} x[k*hop + Mneg + n + m] * c_f(y[k*hop + Mneg + n])
+ *                 * exp(-j 2 pi frac(a * n))
+ *
+ * with the window-local phase of the equation (n = 0 at the window's first reference
+ * sample), N = win_len, for every k with k*hop + Mneg + Mpos + N <= T.  y == NULL: y = x.
+ * out: [nwin][F][nalphas][nlags][2]; *nwin_out receives the number of windows (the caller
+ * sizes out for max_win windows; more are not written).  Returns 0, -1 on bad arguments.
+ */
+int cyco_windows(const double* x, const double* y, int64_t T, const int32_t* lags, int nlags,
+                 const double* alphas, int nalphas, int forms, int64_t win_len, int64_t hop,
+                 int64_t max_win, int nthreads, double* out, int64_t* nwin_out)
+{
+    if (!x || T < 0 || !lags || nlags <= 0 || !alphas || nalphas <= 0 || !out || win_len <= 0 || hop <= 0)
+        return -1;
+    if ((forms & 3) == 0 || (forms & ~3)) return -1;
+    if (!y) y = x;
+    int32_t lo = 0, hi = 0;
+    for (int i = 0; i < nlags; ++i) {
+        if (lags[i] < lo) lo = lags[i];
+        if (lags[i] > hi) hi = lags[i];
+    }
+    const int64_t Mneg = -(int64_t)lo, Mpos = hi;
+    const int64_t span = Mneg + Mpos + win_len;
+    int64_t nwin = T >= span ? (T - span) / hop + 1 : 0;
+    if (nwin_out) *nwin_out = nwin;
+    if (nwin > max_win) nwin = max_win;
+    int flist[2], F = 0;
+    if (forms & CYCO_CONV) flist[F++] = CYCO_CONV;
+    if (forms & CYCO_CONJ) flist[F++] = CYCO_CONJ;
+    const int64_t per = (int64_t)F * nalphas * nlags;
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int64_t t = 0; t < nwin * per; ++t) {
+        const int64_t k = t / per, r = t % per;
+        const int f = (int)(r / ((int64_t)nalphas * nlags));
+        const int ia = (int)((r / nlags) % nalphas);
+        const int im = (int)(r % nlags);
+        /* entry_xy with the reference run starting at k*hop + Mneg and phase index n - that */
+        const int64_t s0 = k * hop + Mneg;
+        double sr = 0.0, si = 0.0;
+        for (int64_t n = 0; n < win_len; ++n) {
+            const int64_t i = s0 + n;
+            double xr = x[2 * (i + lags[im])], xi = x[2 * (i + lags[im]) + 1];
+            double yr = y[2 * i], yi = y[2 * i + 1];
+            if (flist[f] == CYCO_CONV) yi = -yi;
+            double pr = xr * yr - xi * yi;
+            double pi = xr * yi + xi * yr;
+            double ph = frac_an(alphas[ia], n);
+            double c = cos(2.0 * M_PI * ph), sn = -sin(2.0 * M_PI * ph);
+            sr += pr * c - pi * sn;
+            si += pr * sn + pi * c;
+        }
+        out[2 * t] = sr / (double)win_len;
+        out[2 * t + 1] = si / (double)win_len;
+    }
+    return 0;
+}
+
 /* Normaliser of the cross error metric: sqrt(mean |x[n]|^2 * mean |y[n]|^2) over the
  * committed n-range [Mneg, T - Mpos) (Cauchy-Schwarz bound of every entry's terms);
  * for y == NULL this is R^0(0) over that range. */
