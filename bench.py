@@ -43,7 +43,7 @@ TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
 # dram__bytes_read.sum + dram__bytes_write.sum per projection launch from one ncu capture,
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu file).
 TRAFFIC = {
-    "proj_tc@3ea3124d93ef": 643584 + 94208,     # profiles/proj_tc_bf16x3_cfg1_ncu.md
+    "proj_tc@2418c9bb884b": 624640 + 76032,     # profiles/proj_tc_pair_bf16x3_cfg1_ncu.md
 }
 
 
@@ -394,6 +394,43 @@ def proposer_leg(pkg, nsig=64, k=32, pushes=64):
             "breakeven_samples": (t_prop / max(t_full - t_top, 1e-12)) * C if t_full > t_top else None}
 
 
+def cross_leg(pkg, x_dev, T=1 << 24, reps=2):
+    """Eq. (impl-corr) in full: two inputs and signed lags at the config-1 shape -- lags
+    -64..63 (128, M^- = 64), 1024 cycle frequencies, both forms, BF16x3, 2^16-sample
+    pushes -- with y the config-1 stream delayed by one sample; device time per push next
+    to the one-input stream (lags 0..127) on the same samples."""
+    import torch
+    C = CHUNK
+    alphas = -0.5 + np.arange(NALPHAS) / NALPHAS
+    y_dev = torch.roll(x_dev[:2 * T], 2)
+    res = {"workload": "cfg1 shape, two inputs: lags -64..63, 1024 a, CONV+CONJ, bf16x3, %d samples" % T}
+    for name, lags, cross in (("cross_signed", np.arange(-64, 64), True), ("one_input", np.arange(128), False)):
+        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C, cross=cross) as s:
+            def run():
+                s.reset()
+                for c in range(T // C):
+                    sl = slice(2 * c * C, 2 * (c + 1) * C)
+                    if cross:
+                        s.push(x_dev[sl], y=y_dev[sl])
+                    else:
+                        s.push(x_dev[sl])
+                s.sync()
+            run()
+            ms = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        m = statistics.median(ms)
+        cmac = (T - 127) * 128 * NALPHAS * NFORMS
+        res[name] = {"ms": m, "gmac_s": cmac / (m * 1e-3) / 1e9, "us_per_push": m * 1e3 / (T // C)}
+    return res
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -576,6 +613,8 @@ def run_ours(args):
         line["cfg0_latency"] = latency_leg(pkg)
     if rank == 0 and not args.no_precisions:
         line["cfg2_precisions"] = precision_leg(pkg)
+    if rank == 0 and not args.no_cross:
+        line["f1_cross"] = cross_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
     if rank == 0 and not args.no_proposer:
         line["cfg4_proposer"] = proposer_leg(pkg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -608,6 +647,7 @@ def main():
     ap.add_argument("--no-latency", action="store_true", help="skip the config-0 per-call latency leg")
     ap.add_argument("--no-precisions", action="store_true", help="skip the config-2 precision leg")
     ap.add_argument("--no-proposer", action="store_true", help="skip the config-4 proposer leg")
+    ap.add_argument("--no-cross", action="store_true", help="skip the two-input / signed-lag leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")

@@ -3,12 +3,16 @@
  * one NVIDIA GB300 (sm_103a).
  *
  * What a stream estimates (arXiv 2405.16911, Sec. 2 discrete estimators and Sec. 4
- * Eq. (impl-corr) with x = y and lags m >= 0), over every sample pushed so far:
+ * Eq. (impl-corr); here for one input, x = y, and lags m >= 0), over every sample pushed
+ * so far:
  *
  *   R_CONV[a][m] = (1/N_eff) sum_{n=0}^{N_eff-1} x[n+m] conj(x[n]) exp(-j 2 pi a (n0+n))
  *   R_CONJ[a][m] = (1/N_eff) sum_{n=0}^{N_eff-1} x[n+m]      x[n]  exp(-j 2 pi a (n0+n))
  *
  *   N_eff = max(0, T - M), T = samples pushed, M = max(lags), n0 = start index.
+ *
+ * Signed lags shift the window by M^- = -min(lags) (see cyc_params), and streams made by
+ * cyc_create_xy take a second input y in place of the conjugated factor (cross forms).
  *
  * CONV is the cyclic autocorrelation (Eq. (ACF-def)), CONJ the conjugate cyclic
  * correlation (Eq. (CCF-def)); the paper's block attribute `conj` selects between
@@ -71,7 +75,11 @@ typedef struct cyc_stream cyc_stream;   /* opaque, owned by the library */
 
 /*
  * Creation parameters.  Arrays are copied; the caller keeps ownership.
- *   lags[nlags]       lags m >= 0 (Sec. 4 Set mode lists lags; negative lags -> CYC_EINVAL)
+ *   lags[nlags]       signed lags m (Sec. 4 Set mode spans -max_lag .. max_lag), |m| <= 2^20 and
+ *                     max - min <= 2^20 (CYC_EINVAL otherwise).  With M^- = max(0, -min m) and
+ *                     M^+ = max(0, max m), term n pairs x[n + m] with the reference sample
+ *                     at n, n = M^- .. T - M^+ - 1 (Eq. (impl-corr): the window starts M^-
+ *                     samples in), N_eff = T - M^- - M^+, and the phase is that of n.
  *   alphas[nalphas]   normalised cycle frequencies (finite doubles)
  *   conj_flag         CYC_CONV, CYC_CONJ or CYC_BOTH
  *   precision         CYC_P_*
@@ -103,6 +111,16 @@ CYC_API int cyc_create(const int32_t* lags, int nlags, const double* alphas, int
 CYC_API int cyc_create_ex(const cyc_params* p, cyc_stream** out);
 
 /*
+ * cyc_create_xy: a stream with two inputs x and y, the cross forms of Eq. (impl-corr):
+ *   CONV  R[a][m] = (1/N_eff) sum_n x[n+m] conj(y[n]) exp(-j 2 pi a n)   (cyclic cross-correlation)
+ *   CONJ  R[a][m] = (1/N_eff) sum_n x[n+m] y[n]       exp(-j 2 pi a n)   (conjugate form)
+ * with n over the same range as cyc_params describes.  Samples arrive through
+ * cyc_push_xy only; cyc_read, cyc_reset, cyc_save and cyc_load work as for one input (the
+ * blob then carries both tails).  Server streams have one input.
+ */
+CYC_API int cyc_create_xy(const cyc_params* p, cyc_stream** out);
+
+/*
  * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
  * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
  * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read
@@ -111,6 +129,11 @@ CYC_API int cyc_create_ex(const cyc_params* p, cyc_stream** out);
  * memory is read in stream order like device memory.  nsamples == 0 is a no-op.
  */
 CYC_API int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device);
+
+/* cyc_push_xy: as cyc_push for a stream made by cyc_create_xy: nsamples samples of x and
+ * the same nsamples of y (both interleaved complex64, both on the device or both on the
+ * host).  cyc_push on such a stream, or cyc_push_xy on a one-input stream: CYC_EINVAL. */
+CYC_API int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk, int64_t nsamples, int on_device);
 
 /*
  * cyc_read: wait for the stream's work, then write R = sums / N_eff (layout above) to

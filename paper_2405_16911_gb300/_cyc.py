@@ -76,7 +76,9 @@ def load(path: str = LIB_PATH):
     sig = {
         "cyc_create": ([P, I, P, I, I, P], I),
         "cyc_create_ex": ([P, P], I),
+        "cyc_create_xy": ([P, P], I),
         "cyc_push": ([P, P, I64, I], I),
+        "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
         "cyc_sync": ([P], I),
         "cyc_reset": ([P], I),
@@ -157,7 +159,8 @@ def cyc_create(lags, alphas, conj_flag: int = CYC_BOTH) -> int:
 
 
 def cyc_create_ex(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
-                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0) -> int:
+                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False) -> int:
+    """cross=True: cyc_create_xy, a stream with two inputs (cyc_push_xy)."""
     lib = load()
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
@@ -166,7 +169,7 @@ def cyc_create_ex(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32,
     p = cyc_params(lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, conj_flag, precision,
                    int(n0), int(max_chunk), cuda_stream or None, device)
     h = ctypes.c_void_p()
-    _check(lib.cyc_create_ex(ctypes.byref(p), ctypes.byref(h)))
+    _check((lib.cyc_create_xy if cross else lib.cyc_create_ex)(ctypes.byref(p), ctypes.byref(h)))
     _shapes[h.value] = (_nforms(conj_flag), alphas.size, lags.size)
     return h.value
 
@@ -182,6 +185,28 @@ def cyc_push(h: int, chunk, nsamples: int | None = None, on_device: int | None =
             raise ValueError("on_device is required with a raw address")
         on_device = dev
     _check(load().cyc_push(h, addr, int(nsamples), int(on_device)))
+
+
+def cyc_create_xy(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
+                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0) -> int:
+    """A stream with two inputs x, y (the cross forms); feed it with cyc_push_xy."""
+    return cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross=True)
+
+
+def cyc_push_xy(h: int, x_chunk, y_chunk, nsamples: int | None = None, on_device: int | None = None) -> None:
+    xa, xb, xd, _kx = _ptr_info(x_chunk)
+    ya, yb, yd, _ky = _ptr_info(y_chunk)
+    if nsamples is None:
+        if xb is None or yb is None:
+            raise ValueError("nsamples is required with raw addresses")
+        if xb != yb:
+            raise ValueError("x and y chunks differ in length")
+        nsamples = xb // 8
+    if on_device is None:
+        if xd is None or xd != yd:
+            raise ValueError("on_device is required with raw addresses or mixed host/device chunks")
+        on_device = xd
+    _check(load().cyc_push_xy(h, xa, ya, int(nsamples), int(on_device)))
 
 
 def cyc_read(h: int, out=None):
@@ -494,12 +519,19 @@ class Stream:
     """Owning wrapper: ``with Stream(lags, alphas, ...) as s: s.push(x); R, n = s.read()``."""
 
     def __init__(self, lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
-                 max_chunk: int = 0, cuda_stream: int = 0, device: int = 0):
-        self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device)
+                 max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False):
+        self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross)
         self.shape = _shapes[self.h]
+        self.cross = cross
 
-    def push(self, chunk, nsamples=None, on_device=None):
-        cyc_push(self.h, chunk, nsamples, on_device)
+    def push(self, chunk, nsamples=None, on_device=None, y=None):
+        """One input: push(x); a cross stream: push(x, y=y)."""
+        if self.cross:
+            cyc_push_xy(self.h, chunk, y, nsamples, on_device)
+        else:
+            if y is not None:
+                raise ValueError("this stream has one input")
+            cyc_push(self.h, chunk, nsamples, on_device)
 
     def read(self, out=None):
         return cyc_read(self.h, out)

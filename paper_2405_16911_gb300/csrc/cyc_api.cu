@@ -111,7 +111,9 @@ struct cyc_stream {
     int forms[2] = {0, 0};
     std::vector<int32_t> lags;
     int L = 0;
-    int32_t M = 0;
+    int32_t M = 0;                  // lag span M^- + M^+: samples carried from push to push
+    int32_t Mneg = 0;               // M^- = max(0, -min lag): window offset of Eq. (impl-corr)
+    bool cross = false;             // two inputs (cyc_create_xy / cyc_push_xy)
     std::vector<double> alphas;
     int A = 0;
     std::vector<uint64_t> phi_u;
@@ -122,6 +124,7 @@ struct cyc_stream {
     uint64_t fingerprint = 0;
     // device state
     float2* stage[2] = {nullptr, nullptr};
+    float2* stage_y[2] = {nullptr, nullptr};   // second input, same layout (cross streams)
     int cur = 0;
     double2* sums = nullptr;
     uint64_t* d_phi = nullptr;
@@ -150,11 +153,12 @@ struct cyc_stream {
     void free_all()
     {
         free_events();
-        void* ps[] = {stage[0], stage[1], sums, d_phi, d_amap, d_col_lag, d_col_conj, part, d_out, d_err};
+        void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
+                      part, d_out, d_err};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
-        stage[0] = stage[1] = nullptr;
+        stage[0] = stage[1] = stage_y[0] = stage_y[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
     }
@@ -167,10 +171,14 @@ int check_params(const cyc_params* p)
     if (!p) return fail(CYC_EINVAL, "cyc_create_ex: params is NULL");
     if (!p->lags || p->nlags <= 0) return fail(CYC_EINVAL, "lag list is empty");
     if (!p->alphas || p->nalphas <= 0) return fail(CYC_EINVAL, "cycle-frequency list is empty");
+    int32_t lo = 0, hi = 0;
     for (int i = 0; i < p->nlags; ++i) {
-        if (p->lags[i] < 0) return fail(CYC_EINVAL, "lag %d is negative (%d); lags must be >= 0", i, p->lags[i]);
-        if (p->lags[i] > kMaxLag) return fail(CYC_EINVAL, "lag %d exceeds %d", p->lags[i], kMaxLag);
+        if (p->lags[i] < -kMaxLag || p->lags[i] > kMaxLag)
+            return fail(CYC_EINVAL, "lag %d (%d) is outside [-%d, %d]", i, p->lags[i], kMaxLag, kMaxLag);
+        lo = p->lags[i] < lo ? p->lags[i] : lo;
+        hi = p->lags[i] > hi ? p->lags[i] : hi;
     }
+    if ((int64_t)hi - lo > kMaxLag) return fail(CYC_EINVAL, "the lags span more than %d samples", kMaxLag);
     for (int i = 0; i < p->nalphas; ++i)
         if (!isfinite(p->alphas[i])) return fail(CYC_EINVAL, "cycle frequency %d is not finite", i);
     if (p->conj_flag < 1 || p->conj_flag > 3) return fail(CYC_EINVAL, "conj_flag must be 1, 2 or 3");
@@ -189,6 +197,10 @@ int alloc_state(cyc_stream* s)
     for (int b = 0; b < 2; ++b) {
         CK(cudaMalloc(&s->stage[b], stage_n * sizeof(float2)));
         CK(cudaMemset(s->stage[b], 0, stage_n * sizeof(float2)));
+        if (s->cross) {
+            CK(cudaMalloc(&s->stage_y[b], stage_n * sizeof(float2)));
+            CK(cudaMemset(s->stage_y[b], 0, stage_n * sizeof(float2)));
+        }
     }
     CK(cudaMalloc(&s->sums, (size_t)s->Au * s->ncols * sizeof(double2)));
     CK(cudaMemset(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2)));
@@ -201,7 +213,7 @@ int alloc_state(cyc_stream* s)
     // column c = lag index * F + form index: both forms of a lag are neighbours
     for (int f = 0; f < s->F; ++f)
         for (int l = 0; l < s->L; ++l) {
-            cl[l * s->F + f] = s->lags[l];
+            cl[l * s->F + f] = s->lags[l] + s->Mneg;        // shifted lag m + M^- >= 0
             cc[l * s->F + f] = s->forms[f] == CYC_CONJ ? 1 : 0;
         }
     CK(cudaMalloc(&s->d_col_lag, s->ncols * sizeof(int32_t)));
@@ -229,7 +241,7 @@ int project(cyc_stream* s, int64_t nc)
     ProjArgs a;
     a.x = s->stage[s->cur];
     a.nc = nc;
-    a.nbase = (uint64_t)s->n0 + (uint64_t)s->n_eff;
+    a.nbase = (uint64_t)s->n0 + (uint64_t)s->n_eff + (uint64_t)s->Mneg;   // index of y[M^-]
     a.phi = s->d_phi;
     a.Au = s->Au;
     a.col_lag = s->d_col_lag;
@@ -239,6 +251,8 @@ int project(cyc_stream* s, int64_t nc)
     a.err = s->d_err;
     a.M = s->M;
     a.x_avail = (s->M + s->max_chunk + kStagePad) & ~(int64_t)1;
+    a.y = s->cross ? s->stage_y[s->cur] : nullptr;
+    a.D = s->Mneg;
     // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
     const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
     ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)
@@ -321,7 +335,7 @@ int cyc_create(const int32_t* lags, int nlags, const double* alphas, int nalphas
     return cyc_create_ex(&p, out);
 }
 
-int cyc_create_ex(const cyc_params* p, cyc_stream** out)
+static int create_impl(const cyc_params* p, bool cross, cyc_stream** out)
 {
     if (!out) return fail(CYC_EINVAL, "cyc_create_ex: out is NULL");
     *out = nullptr;
@@ -344,7 +358,14 @@ int cyc_create_ex(const cyc_params* p, cyc_stream** out)
     if (p->conj_flag & CYC_CONJ) s->forms[s->F++] = CYC_CONJ;
     s->lags.assign(p->lags, p->lags + p->nlags);
     s->L = p->nlags;
-    for (int32_t m : s->lags) s->M = m > s->M ? m : s->M;
+    s->cross = cross;
+    int32_t lo = 0, hi = 0;
+    for (int32_t m : s->lags) {
+        lo = m < lo ? m : lo;
+        hi = m > hi ? m : hi;
+    }
+    s->Mneg = -lo;
+    s->M = hi - lo;
     s->alphas.assign(p->alphas, p->alphas + p->nalphas);
     s->A = p->nalphas;
     std::map<uint64_t, int> uniq;
@@ -368,11 +389,13 @@ int cyc_create_ex(const cyc_params* p, cyc_stream** out)
     h = fnv1a(h, s->amap.data(), s->amap.size() * sizeof(int32_t));
     h = fnv1a(h, &s->conj_flag, sizeof s->conj_flag);
     h = fnv1a(h, &s->n0, sizeof s->n0);
+    const int32_t xy = s->cross ? 1 : 0;
+    h = fnv1a(h, &xy, sizeof xy);
     s->fingerprint = h;
 
     if (s->precision != CYC_P_FP32 && !tc_supported(s->ncols, s->M)) {
         delete s;
-        return fail(CYC_ENOTSUP, "the tensor-core projection supports lags up to 2560 (max lag %d); use CYC_P_FP32",
+        return fail(CYC_ENOTSUP, "the tensor-core projection supports lag spans up to 2560 (span %d); use CYC_P_FP32",
                     s->M);
     }
     DeviceGuard g(s->device);
@@ -395,26 +418,35 @@ int cyc_create_ex(const cyc_params* p, cyc_stream** out)
     return CYC_OK;
 }
 
-int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device)
+int cyc_create_ex(const cyc_params* p, cyc_stream** out) { return create_impl(p, false, out); }
+
+int cyc_create_xy(const cyc_params* p, cyc_stream** out) { return create_impl(p, true, out); }
+
+static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int64_t nsamples, int on_device,
+                     const char* who)
 {
-    if (!s) return fail(CYC_EINVAL, "cyc_push: handle is NULL");
-    if (nsamples < 0) return fail(CYC_EINVAL, "cyc_push: nsamples < 0");
+    if (nsamples < 0) return fail(CYC_EINVAL, "%s: nsamples < 0", who);
     if (nsamples == 0) return CYC_OK;
-    if (!chunk) return fail(CYC_EINVAL, "cyc_push: chunk is NULL");
+    if (!xchunk || (s->cross && !ychunk)) return fail(CYC_EINVAL, "%s: chunk is NULL", who);
     DeviceGuard g(s->device);
     if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
     if (on_device) {
         bool wrong = false;
-        if (!is_device_ptr(chunk, s->device, &wrong) || wrong)
-            return fail(CYC_EINVAL, "cyc_push: on_device set but chunk is not memory of device %d", s->device);
+        if (!is_device_ptr(xchunk, s->device, &wrong) || wrong ||
+            (s->cross && (!is_device_ptr(ychunk, s->device, &wrong) || wrong)))
+            return fail(CYC_EINVAL, "%s: on_device set but a chunk is not memory of device %d", who, s->device);
     }
-    const float2* src = (const float2*)chunk;
+    const float2* src = (const float2*)xchunk;
+    const float2* ysrc = (const float2*)ychunk;
     int64_t left = nsamples;
     while (left > 0) {
         int64_t c = left < s->max_chunk ? left : s->max_chunk;
         float2* view = s->stage[s->cur];
-        // a1: the view is [carried tail (held samples) | new samples]
+        // a1: the view is [carried tail (held samples) | new samples], for both inputs
         CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, s->st));
+        if (s->cross)
+            CK(cudaMemcpyAsync(s->stage_y[s->cur] + s->held, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault,
+                               s->st));
         int64_t nview = s->held + c;
         int64_t nc = nview - s->M;
         if (nc > 0) {
@@ -427,15 +459,34 @@ int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device)
         s->T += c;
         int64_t keep = s->T < s->M ? s->T : s->M;
         // the last `keep` samples of the view become the next view's head
-        if (keep > 0)
+        if (keep > 0) {
             CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
                                cudaMemcpyDeviceToDevice, s->st));
+            if (s->cross)
+                CK(cudaMemcpyAsync(s->stage_y[s->cur ^ 1], s->stage_y[s->cur] + nview - keep,
+                                   (size_t)keep * sizeof(float2), cudaMemcpyDeviceToDevice, s->st));
+        }
         s->cur ^= 1;
         s->held = keep;
         src += c;
+        if (ysrc) ysrc += c;
         left -= c;
     }
     return CYC_OK;
+}
+
+int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_push: handle is NULL");
+    if (s->cross) return fail(CYC_EINVAL, "cyc_push: the stream has two inputs; use cyc_push_xy");
+    return push_impl(s, chunk, nullptr, nsamples, on_device, "cyc_push");
+}
+
+int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk, int64_t nsamples, int on_device)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_push_xy: handle is NULL");
+    if (!s->cross) return fail(CYC_EINVAL, "cyc_push_xy: the stream has one input; use cyc_push");
+    return push_impl(s, x_chunk, y_chunk, nsamples, on_device, "cyc_push_xy");
 }
 
 int cyc_sync(cyc_stream* s)
@@ -488,7 +539,8 @@ int cyc_save(cyc_stream* s, void* buf, size_t* len)
 {
     if (!s || !len) return fail(CYC_EINVAL, "cyc_save: NULL argument");
     size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
-    size_t need = sizeof(BlobHeader) + (size_t)s->held * sizeof(float2) + sums_b;
+    const size_t held_b = (size_t)s->held * sizeof(float2) * (s->cross ? 2 : 1);
+    size_t need = sizeof(BlobHeader) + held_b + sums_b;
     if (!buf) { *len = need; return CYC_OK; }
     if (*len < need) { *len = need; return fail(CYC_EINVAL, "cyc_save: buffer too small (%zu < %zu)", *len, need); }
     DeviceGuard g(s->device);
@@ -503,9 +555,13 @@ int cyc_save(cyc_stream* s, void* buf, size_t* len)
     unsigned char* b = (unsigned char*)buf;
     memcpy(b, &h, sizeof h);
     CK(cudaStreamSynchronize(s->st));
-    if (s->held)
+    if (s->held) {
         CK(cudaMemcpy(b + sizeof h, s->stage[s->cur], (size_t)s->held * sizeof(float2), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(b + sizeof h + (size_t)s->held * sizeof(float2), s->sums, sums_b, cudaMemcpyDeviceToHost));
+        if (s->cross)
+            CK(cudaMemcpy(b + sizeof h + (size_t)s->held * sizeof(float2), s->stage_y[s->cur],
+                          (size_t)s->held * sizeof(float2), cudaMemcpyDeviceToHost));
+    }
+    CK(cudaMemcpy(b + sizeof h + held_b, s->sums, sums_b, cudaMemcpyDeviceToHost));
     *len = need;
     return CYC_OK;
 }
@@ -520,18 +576,24 @@ int cyc_load(cyc_stream* s, const void* buf, size_t len)
         return fail(CYC_EINVAL, "cyc_load: not a libcyc state blob of version %u", kBlobVersion);
     if (h.fingerprint != s->fingerprint || h.F != s->F || h.L != s->L || h.A != s->A || h.Au != s->Au ||
         h.conj_flag != s->conj_flag || h.n0 != s->n0)
-        return fail(CYC_EINVAL, "cyc_load: blob was saved by a stream with other lags, cycle frequencies, forms or n0");
+        return fail(CYC_EINVAL, "cyc_load: blob was saved by a stream with other lags, cycle frequencies, forms, "
+                                "inputs or n0");
     if (h.held < 0 || h.held > s->M || h.T < 0 || h.n_eff < 0 || h.held > h.T)
         return fail(CYC_EINVAL, "cyc_load: inconsistent counters in blob");
     size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
-    size_t need = sizeof h + (size_t)h.held * sizeof(float2) + sums_b;
+    const size_t held_b = (size_t)h.held * sizeof(float2) * (s->cross ? 2 : 1);
+    size_t need = sizeof h + held_b + sums_b;
     if (len < need) return fail(CYC_EINVAL, "cyc_load: blob truncated (%zu < %zu)", len, need);
     DeviceGuard g(s->device);
     const unsigned char* b = (const unsigned char*)buf;
     CK(cudaStreamSynchronize(s->st));
-    if (h.held)
+    if (h.held) {
         CK(cudaMemcpy(s->stage[s->cur], b + sizeof h, (size_t)h.held * sizeof(float2), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(s->sums, b + sizeof h + (size_t)h.held * sizeof(float2), sums_b, cudaMemcpyHostToDevice));
+        if (s->cross)
+            CK(cudaMemcpy(s->stage_y[s->cur], b + sizeof h + (size_t)h.held * sizeof(float2),
+                          (size_t)h.held * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(s->sums, b + sizeof h + held_b, sums_b, cudaMemcpyHostToDevice));
     s->T = h.T;
     s->n_eff = h.n_eff;
     s->held = h.held;

@@ -15,10 +15,13 @@ namespace cyc {
 //   part[s][u][c] = sum over n in split s of  W(u, n) * P_c(n)
 // with W(u, n) = exp(-j 2 pi phi_u (nbase + n) / 2^64) and P_c the lag product of column c
 // (c = lag index * F + form index).  The caller folds the splits into the FP64 sums.
+// Term n of a pass is x[n + col_lag] * c(y[n + D]) * exp(-j 2 pi phi (nbase + n) / 2^64):
+// col_lag = m + M^- >= 0 and D = M^- for signed lags m >= -M^- (Eq. (impl-corr)); y = x
+// (y == nullptr) for the cyclic ACF / CCF, a second input for the cross forms.
 struct ProjArgs {
     const float2*   x;          // view x[0 .. nc + M)
     int64_t         nc;         // committed n in this pass (0 <= n < nc)
-    uint64_t        nbase;      // absolute index of x[0], mod 2^64
+    uint64_t        nbase;      // absolute phase index of term n = 0, mod 2^64
     const uint64_t* phi;        // [Au] cycle frequencies as u64 fixed point (cycles * 2^64)
     int             Au;
     const int32_t*  col_lag;    // [ncols] lag of each column
@@ -28,8 +31,10 @@ struct ProjArgs {
     int64_t         split_len;  // samples per split
     float2*         part;       // [nsplit][Au][ncols]
     int*            err = nullptr;  // device status word: a bounded wait that gave up sets it
-    int             M = 0;          // max lag (halo of every staged block of samples)
-    int64_t         x_avail = 0;    // samples readable from x (allocation bound, even)
+    int             M = 0;          // lag span M^- + M^+ (halo of every staged block of samples)
+    int64_t         x_avail = 0;    // samples readable from x (and y) (allocation bound, even)
+    const float2*   y = nullptr;    // second input, same indexing as x; nullptr: y = x
+    int             D = 0;          // offset M^- of the reference sample y[n + D]
 };
 
 // One work item of the tensor-core projection: 128 cycle frequencies x 128 columns x an
@@ -48,6 +53,9 @@ struct TcItem {
     float2*         out;
     int             out_stride;
     int             u0, Au, c0, ncols, M;
+    const float2*   y;          // second input (linear views only) or nullptr: y = x
+    int             D;          // offset of the reference sample y[n + D]
+    int64_t         out_peer;   // pair lists: the odd CTA's rows u0 + 128 .. go to out + out_peer
 };
 
 // Launch geometry chosen by a kernel family for one pass.
@@ -79,8 +87,10 @@ size_t      tc_max_partials(int Au, int ncols, int num_sms);
 int         tc_tile_rows();     // cycle frequencies per work item
 int         tc_tile_cols();     // columns per work item
 // Persistent launch over a device list of work items (taken with an atomic counter that
-// the caller zeroes before the launch); `grid` CTAs, one per SM.
-cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision,
+// the caller zeroes before the launch); `grid` CTAs, one per SM.  pair = true: `grid`
+// (even) CTAs in two-CTA clusters, each item covering rows u0 .. u0 + 255 (the odd CTA's
+// half written at out + out_peer).
+cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, bool pair,
                             int* err, cudaStream_t st);
 
 // Sets the calling thread's message returned by cyc_last_error() (cyc_api.cu).

@@ -13,6 +13,7 @@
 // reports every chunk whose samples are fully used.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 #include <time.h>
@@ -152,6 +153,8 @@ struct Batch {
 struct cyc_server {
     cyc_server_params p;
     int num_sms = 1;
+    int grid = 1;               // CTAs of the persistent launch
+    bool pair = false;          // items run on two-CTA pairs (256 cycle-frequency rows each)
     cudaStream_t cst = nullptr, xst = nullptr;
     std::vector<std::unique_ptr<SrvStream>> streams;
     std::mutex admin;
@@ -223,25 +226,32 @@ int cyc_server::form_and_launch()
         const int64_t n_sched = s.n_sched.load();
         if (upto <= n_sched) continue;
         const int ta = (s.Au + BMr - 1) / BMr, tcn = (s.ncols + BNc - 1) / BNc;
+        // pairs: one item covers tiles 2k and 2k + 1 (the second may not exist)
+        const int tstep = pair ? 2 : 1;
+        const int titems = (ta + tstep - 1) / tstep;
         int64_t span = upto - n_sched;
         int pieces = (int)((span + p.item_samples - 1) / p.item_samples);
         // what still fits into this batch
-        int room_items = (p.max_items - ni) / (ta * tcn);
-        int64_t room_slots = (nslot_cap - ns) / (ta * tcn);
+        int room_items = (p.max_items - ni) / (titems * tcn);
+        int64_t room_slots = (nslot_cap - ns) / (titems * tstep * tcn);
+        int room_folds = (2 * p.max_items - nf) / (ta * tcn);
         int fit = (int)std::min<int64_t>(pieces, std::min<int64_t>(room_items, room_slots));
+        if (room_folds <= 0) fit = 0;
         if (fit <= 0) break;
         if (fit < pieces) span = (int64_t)fit * p.item_samples;
         const int64_t nb = n_sched, ne = n_sched + span;
-        for (int ia = 0; ia < ta; ++ia)
+        for (int ip = 0; ip < titems; ++ip)
             for (int ic = 0; ic < tcn; ++ic) {
-                Fold& f = folds[nf++];
-                f.sums = s.sums;
-                f.u0 = ia * BMr;
-                f.Au = s.Au;
-                f.c0 = ic * BNc;
-                f.ncols = s.ncols;
-                f.slot0 = ns;
-                f.nslots = fit;
+                for (int k = 0; k < tstep && ip * tstep + k < ta; ++k) {
+                    Fold& f = folds[nf++];
+                    f.sums = s.sums;
+                    f.u0 = (ip * tstep + k) * BMr;
+                    f.Au = s.Au;
+                    f.c0 = ic * BNc;
+                    f.ncols = s.ncols;
+                    f.slot0 = ns + (int64_t)k * fit;
+                    f.nslots = fit;
+                }
                 for (int pc = 0; pc < fit; ++pc) {
                     TcItem& it = items[ni++];
                     it.x = s.ring;
@@ -255,13 +265,16 @@ int cyc_server::form_and_launch()
                     it.col_conj = s.d_col_conj;
                     it.out = slots + (ns + pc) * (int64_t)BMr * BNc;
                     it.out_stride = BNc;
-                    it.u0 = f.u0;
+                    it.u0 = ip * tstep * BMr;
                     it.Au = s.Au;
-                    it.c0 = f.c0;
+                    it.c0 = ic * BNc;
                     it.ncols = s.ncols;
                     it.M = s.M;
+                    it.y = nullptr;
+                    it.D = 0;
+                    it.out_peer = (int64_t)fit * BMr * BNc;     // the second tile's slots follow
                 }
-                ns += fit;
+                ns += (int64_t)tstep * fit;
             }
         s.n_sched.store(ne);
         marks.emplace_back(sid, ne);
@@ -370,7 +383,7 @@ int capture_graph(cyc_server* s, int b)
     cudaGraph_t g = nullptr;
     SCK(cudaStreamBeginCapture(s->cst, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->cst);
-    tc_launch_items(s->d_items[b], s->d_counts[b], s->d_counter, s->num_sms, s->p.precision, s->d_err, s->cst);
+    tc_launch_items(s->d_items[b], s->d_counts[b], s->d_counter, s->grid, s->p.precision, s->pair, s->d_err, s->cst);
     fold_kernel<<<s->num_sms * 4, 256, 0, s->cst>>>(s->d_folds[b], s->d_counts[b] + 1, s->slots, tc_tile_rows(),
                                                     tc_tile_cols());
     cudaError_t e = cudaStreamEndCapture(s->cst, &g);
@@ -453,13 +466,19 @@ int cyc_server_create(const cyc_server_params* pp, cyc_server** out)
     chk(cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "compute stream");
     chk(cudaStreamCreateWithFlags(&s->xst, cudaStreamNonBlocking), "copy stream");
     const int64_t tile = (int64_t)tc_tile_rows() * tc_tile_cols();
-    s->nslot_cap = p.max_items;
+    {
+        const char* ev = getenv("CYC_TC_PAIR");
+        const int pc = (ev && ev[0] == '0') ? 0 : tc_pair_ctas(p.precision);
+        s->pair = pc >= 2;
+        s->grid = s->pair ? (pc < s->num_sms ? pc : s->num_sms) & ~1 : s->num_sms;
+    }
+    s->nslot_cap = (s->pair ? 2 : 1) * (int64_t)p.max_items;      // one partial tile per item and tile
     for (int b = 0; b < 2 && rc == CYC_OK; ++b) {
         chk(cudaMallocHost(&s->h_items[b], sizeof(TcItem) * p.max_items), "pinned items");
-        chk(cudaMallocHost(&s->h_folds[b], sizeof(Fold) * p.max_items), "pinned folds");
+        chk(cudaMallocHost(&s->h_folds[b], sizeof(Fold) * 2 * p.max_items), "pinned folds");
         chk(cudaMallocHost(&s->h_counts[b], 2 * sizeof(int)), "pinned counts");
         chk(cudaMalloc(&s->d_items[b], sizeof(TcItem) * p.max_items), "items");
-        chk(cudaMalloc(&s->d_folds[b], sizeof(Fold) * p.max_items), "folds");
+        chk(cudaMalloc(&s->d_folds[b], sizeof(Fold) * 2 * p.max_items), "folds");
         chk(cudaMalloc(&s->d_counts[b], 2 * sizeof(int)), "counts");
         if (rc == CYC_OK) chk(cudaMemset(s->d_counts[b], 0, 2 * sizeof(int)), "counts");
     }
@@ -470,7 +489,8 @@ int cyc_server_create(const cyc_server_params* pp, cyc_server** out)
     if (rc == CYC_OK) {
         // an empty launch fixes the kernel's shared-memory attribute before capture
         chk(cudaMemset(s->d_counter, 0, sizeof(int)), "counter");
-        chk(tc_launch_items(s->d_items[0], s->d_counts[0], s->d_counter, 1, p.precision, s->d_err, s->cst), "warm-up");
+        chk(tc_launch_items(s->d_items[0], s->d_counts[0], s->d_counter, s->pair ? 2 : 1, p.precision, s->pair,
+                            s->d_err, s->cst), "warm-up");
         chk(cudaStreamSynchronize(s->cst), "warm-up");
     }
     for (int b = 0; b < 2 && rc == CYC_OK; ++b) rc = capture_graph(s, b);

@@ -2,8 +2,9 @@
 //
 // For one contiguous view of the stream the kernel forms, per (cycle frequency u, column c):
 //   part[s][u][c] = sum_{n in split s} exp(-j 2 pi phi_u (nbase + n) / 2^64) * P_c(n)
-//   P_c(n) = x[n + m_c] * conj(x[n])   (CONV, Eq. (ACF-def) lag product)
-//   P_c(n) = x[n + m_c] * x[n]         (CONJ, Eq. (CCF-def) lag product)
+//   P_c(n) = x[n + m_c] * conj(y[n + D])   (CONV, Eq. (ACF-def) lag product)
+//   P_c(n) = x[n + m_c] * y[n + D]         (CONJ, Eq. (CCF-def) lag product)
+// with y = x for the auto forms and D = M^- for signed lags (Eq. (impl-corr)).
 // i.e. the per-alpha projection of the lag products in Sec. 4 Set mode, written as a
 // complex GEMM  W[u][n] x P[n][c]  over the samples n.  Both operands are produced in
 // shared memory per K-tile (the lag products are never stored in HBM); the phase is
@@ -52,8 +53,8 @@ __device__ __forceinline__ void gen_tile(const ProjArgs& a, Smem& sm, int buf, i
         float2 p = make_float2(0.f, 0.f);
         if (c_ok && n < n_end) {
             float2 xm = __ldg(&a.x[n + lag_g]);
-            float2 x0 = __ldg(&a.x[n]);
-            p = lag_product(xm, x0, conj_g);
+            float2 y0 = __ldg(&(a.y ? a.y : a.x)[n + a.D]);
+            p = lag_product(xm, y0, conj_g);
         }
         sm.p[buf][k][gen_c] = p;
     }

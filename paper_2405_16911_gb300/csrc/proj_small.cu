@@ -42,12 +42,13 @@ __global__ void __launch_bounds__(NT) proj_small_kernel(ProjArgs a)
 #pragma unroll
         for (int j = 0; j < CB; ++j) { sr[u][j] = 0.f; si[u][j] = 0.f; }
 
+    const float2* yv = a.y ? a.y : a.x;          // reference input (y = x for the auto forms)
     for (int64_t n = n_beg + tid; n < n_end; n += NT) {
-        const float2 x0 = __ldg(&a.x[n]);
+        const float2 y0 = __ldg(&yv[n + a.D]);
         float2 p[CB];
 #pragma unroll
         for (int j = 0; j < CB; ++j)
-            p[j] = okc[j] ? lag_product(__ldg(&a.x[n + lag[j]]), x0, cj[j]) : make_float2(0.f, 0.f);
+            p[j] = okc[j] ? lag_product(__ldg(&a.x[n + lag[j]]), y0, cj[j]) : make_float2(0.f, 0.f);
         const uint64_t nabs = a.nbase + (uint64_t)n;
 #pragma unroll
         for (int u = 0; u < AU; ++u) {

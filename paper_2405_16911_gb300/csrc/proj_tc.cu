@@ -10,9 +10,9 @@
 // D_r and D_i live in TMEM columns [0, 256) and [256, 512).  The weights carry the absolute
 // sample index, so an item accumulates in TMEM without any per-tile rotation.  The tensor
 // core's FP32 accumulation drifts with the length of the chain (on the mean-power entry,
-// about 1e-3 of its value over 2^19 samples), so an item longer than SUBG groups (4096
-// samples) runs as consecutive sub-items, each a fresh TMEM chain: the first writes the
-// item's FP32 partial tile, the later ones add to it.
+// about 2e-3 of its value over 2^19 samples), so an item longer than Cfg::SUBN samples (4096
+// for BF16x3, 65536 for FP16) runs as consecutive sub-items, each a fresh TMEM chain: the
+// first writes the item's FP32 partial tile, the later ones add to it.
 // Operands go through a ring of shared-memory stages (one 8-sample group each), K-major,
 // no swizzle, 8-row x 16-byte core matrices:
 //   P block: row r (column), chunk k (0: Pr, 1: Pi) at (r/8)*256 + k*128 + (r%8)*16
@@ -73,8 +73,6 @@ constexpr int XSLOT = 3072;              // samples per staging slot (block + ha
 constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
 constexpr uint32_t TM_DR = 0, TM_DI = 256;
 constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
-constexpr int SUBG = 512;                // groups per TMEM accumulation chain (4096 samples)
-constexpr int SUBN = SUBG * 8;           // samples per sub-item
 
 // Waits and arrivals on the stage barriers: cluster scope when the pair shares them.
 template <bool PAIR>
@@ -97,11 +95,13 @@ template <>
 struct Cfg<CYC_P_FP16> {
     static constexpr int NLEV = 1, NPASS = 1, NSTAGE = 10;
     static constexpr bool BF = false;
+    static constexpr int SUBN = 1 << 16;     // samples per TMEM chain (drift ~4e-4 against 1e-2)
 };
 template <>
 struct Cfg<CYC_P_BF16X3> {
     static constexpr int NLEV = 2, NPASS = 3, NSTAGE = 6;
     static constexpr bool BF = true;
+    static constexpr int SUBN = 1 << 12;     // samples per TMEM chain (drift ~1.6e-5 against 1e-4)
 };
 
 template <int PREC>
@@ -152,6 +152,7 @@ struct Bars {
     int item;
     int abort;
     int add;                                    // this sub-item adds to the partial tile
+    int cmd;                                    // loop control: -1 stop, -2 next sub-item, >= 0 item
     int64_t sub_end;                            // n_end of the whole item
     TcItem it;
 };
@@ -248,6 +249,9 @@ __device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, i
     it.M = a.M;
     it.out = a.part + ((size_t)bz * a.Au + (size_t)it.u0) * a.ncols + it.c0;
     it.out_stride = a.ncols;
+    it.y = a.y;
+    it.D = a.D;
+    it.out_peer = 0;
     return it;
 }
 
@@ -255,7 +259,6 @@ template <int PREC, bool LIST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
 proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restrict__ nitems, int* counter, int* err)
 {
-    static_assert(!(LIST && PAIR), "CTA pairs run grid items only");
     using C = Cfg<PREC>;
     extern __shared__ __align__(1024) unsigned char smem[];
     Bars* bars = reinterpret_cast<Bars*>(smem + xslots_off<PREC>() + 2 * XSLOT * 8);
@@ -297,30 +300,50 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
 
     for (;;) {
         // ---- next (sub-)item (thread 0 fetches; everybody reads it after the barrier) ----
-        if (tid == 0) {
-            int idx = -1;
+        // cmd: -1 stop, -2 the next sub-item of the current item, >= 0 a new item.  CTA pairs
+        // on an item list follow the even CTA's cmd, handed over through distributed shared
+        // memory, so that both always run the same items and the same number of iterations.
+        if (tid == 0 && (!(PAIR && LIST) || crank == 0)) {
+            int cmd = -1;
             if (!bars->abort) {
                 if (nit > 0 && bars->it.n_end < bars->sub_end) {
-                    // the next sub-item of the current item: a fresh TMEM chain that adds
-                    idx = bars->item;
-                    bars->it.n_beg = bars->it.n_end;
-                    bars->add = 1;
-                } else {
-                    bars->add = 0;
-                    if (LIST) {
-                        idx = atomicAdd(counter, 1);
-                        if (idx >= *nitems) idx = -1;
-                        else bars->it = items[idx];
-                    } else if (nit == 0) {
-                        idx = 0;
-                        bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
+                    cmd = -2;
+                } else if (LIST) {
+                    cmd = atomicAdd(counter, 1);
+                    if (cmd >= *nitems) cmd = -1;
+                } else if (nit == 0) {
+                    cmd = 0;
+                }
+            }
+            if constexpr (PAIR && LIST) tc::st_remote_s32(&bars->cmd, 1, cmd);
+            bars->cmd = cmd;
+        }
+        if constexpr (PAIR && LIST) tc::cluster_sync();
+        if (tid == 0) {
+            const int cmd = bars->cmd;
+            int idx = -1;
+            if (cmd == -2) {
+                // the next sub-item of the current item: a fresh TMEM chain that adds
+                idx = bars->item;
+                bars->it.n_beg = bars->it.n_end;
+                bars->add = 1;
+            } else if (cmd >= 0) {
+                idx = cmd;
+                bars->add = 0;
+                if constexpr (LIST) {
+                    bars->it = items[cmd];
+                    if (PAIR && crank == 1) {                  // the odd CTA's 128 rows
+                        bars->it.u0 += BM;
+                        bars->it.out += bars->it.out_peer;
                     }
-                    if (idx >= 0) bars->sub_end = bars->it.n_end;
+                } else {
+                    bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
                 }
-                if (idx >= 0) {
-                    const int64_t e = bars->it.n_beg + SUBN;
-                    bars->it.n_end = e < bars->sub_end ? e : bars->sub_end;
-                }
+                bars->sub_end = bars->it.n_end;
+            }
+            if (idx >= 0) {
+                const int64_t e = bars->it.n_beg + C::SUBN;
+                bars->it.n_end = e < bars->sub_end ? e : bars->sub_end;
             }
             bars->item = idx;
         }
@@ -333,7 +356,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         const int64_t span = n_end - n_beg;
         const int ngroups = span > 0 ? (int)((span + GS - 1) / GS) : 0;
         const int mpad = (it.M + 1) & ~1;
-        const int XB = (XSLOT - mpad - 2) & ~(GS - 1);          // samples per staged block
+        // a slot holds x[block start - xoff .. + XB + M] and, for a second input, y[block
+        // start + D - yoff .. + XB] from YOFF on (both copies start at an even sample)
+        const bool cross = it.y != nullptr;
+        const int XB = cross ? ((XSLOT - mpad - 4) / 2) & ~(GS - 1)
+                             : (XSLOT - mpad - 2) & ~(GS - 1);  // samples per staged block
+        const int YOFF = XB + mpad + 2;
+        const int D = it.D;
+        const int yoff = (int)((n_beg + D) & 1);
         const int nblocks = (ngroups * GS + XB - 1) / XB;
         const int xoff = (int)(n_beg & 1);    // bulk copies start at an even sample (16-byte aligned)
         const bool narrow = it.ncols - it.c0 <= BN / 2;     // N = 128 MMAs, one column per P thread
@@ -373,13 +403,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                         break;
                     }
                     const float2* xb = xsl + xoff + (g * GS - b * XB);
+                    const float2* yb = cross ? xsl + YOFF + yoff + (g * GS - b * XB) : xb + D;
                     const int64_t n = n_beg + (int64_t)g * GS;
                     float prA[8], piA[8], prB[8], piB[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
                         if (n + i < n_end) {
-                            float2 x0 = xb[i];
+                            float2 x0 = yb[i];                  // reference sample y[n + D]
                             float2 xa = okA ? xb[i + mA] : make_float2(0.f, 0.f);
                             float2 xv = same_lag ? xa : (okB ? xb[i + mB] : make_float2(0.f, 0.f));
                             if (okA) pA = lag_product(xa, x0, cjA);
@@ -481,7 +512,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 const int64_t ns = n_beg + (int64_t)b * XB - xoff;   // even
                 int64_t cnt = ((int64_t)XB + mpad + xoff + 1) & ~(int64_t)1;
                 if (cnt > it.x_avail - ns) cnt = it.x_avail - ns;
-                tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)(cnt * 8));
+                int64_t ys = 0, ycnt = 0;
+                if (cross) {
+                    ys = n_beg + (int64_t)b * XB + D - yoff;          // even
+                    ycnt = ((int64_t)XB + yoff + 1) & ~(int64_t)1;
+                    if (ycnt > it.x_avail - ys) ycnt = it.x_avail - ys;
+                }
+                tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)((cnt + ycnt) * 8));
+                if (cross) tc::bulk_g2s(xs + slot * XSLOT + YOFF, it.y + ys, (uint32_t)(ycnt * 8), &bars->xfull[slot]);
                 const uint64_t pos = (uint64_t)ns & it.xmask;
                 const uint64_t room = it.xmask - pos + 1;       // samples before the ring wraps
                 if (it.xmask == ~0ull || (uint64_t)cnt <= room) {
@@ -607,13 +645,31 @@ cudaError_t launch_grid(const ProjArgs& a, bool pair, cudaStream_t st)
 }
 
 template <int PREC>
-cudaError_t launch_list(const TcItem* items, const int* nitems, int* counter, int grid, int* err, cudaStream_t st)
+cudaError_t launch_list(const TcItem* items, const int* nitems, int* counter, int grid, bool pair, int* err,
+                        cudaStream_t st)
 {
-    cudaError_t e = set_smem<PREC, true, false>();
-    if (e != cudaSuccess) return e;
     ProjArgs none;
     none.x = nullptr; none.nc = 0; none.nbase = 0; none.phi = nullptr; none.Au = 0; none.col_lag = nullptr;
     none.col_conj = nullptr; none.ncols = 0; none.nsplit = 0; none.split_len = 0; none.part = nullptr;
+    if (pair) {
+        cudaError_t e = set_smem<PREC, true, true>();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((grid + 1) & ~1);
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = smem_bytes<PREC>();
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, proj_tc_kernel<PREC, true, true>, none, items, nitems, counter, err);
+    }
+    cudaError_t e = set_smem<PREC, true, false>();
+    if (e != cudaSuccess) return e;
     proj_tc_kernel<PREC, true, false><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(none, items, nitems, counter, err);
     return cudaGetLastError();
 }
@@ -691,10 +747,10 @@ cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t 
 }
 
 cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision,
-                            int* err, cudaStream_t st)
+                            bool pair, int* err, cudaStream_t st)
 {
-    if (precision == CYC_P_FP16) return launch_list<CYC_P_FP16>(items, nitems, counter, grid, err, st);
-    if (precision == CYC_P_BF16X3) return launch_list<CYC_P_BF16X3>(items, nitems, counter, grid, err, st);
+    if (precision == CYC_P_FP16) return launch_list<CYC_P_FP16>(items, nitems, counter, grid, pair, err, st);
+    if (precision == CYC_P_BF16X3) return launch_list<CYC_P_BF16X3>(items, nitems, counter, grid, pair, err, st);
     return cudaErrorInvalidValue;
 }
 

@@ -212,6 +212,14 @@ __device__ __forceinline__ void mbar_arrive_remote(void* bar, uint32_t rank)
                  :: "r"(smem_u32(bar)), "r"(rank) : "memory");
 }
 
+// Store a 32-bit value at this shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ void st_remote_s32(void* p, uint32_t rank, int v)
+{
+    asm volatile("{\n.reg .b32 ra;\nmapa.shared::cluster.u32 ra, %0, %1;\n"
+                 "st.shared::cluster.s32 [ra], %2;\n}\n"
+                 :: "r"(smem_u32(p)), "r"(rank), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait_cluster(void* bar, uint32_t parity)
 {
     uint32_t ok;

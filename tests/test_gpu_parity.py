@@ -179,7 +179,7 @@ def test_reset_and_nodata_and_errors(cyc):
         assert np.array_equal(R1, R2)
         with pytest.raises(cyc.CycError):
             s.push(np.ascontiguousarray(x), nsamples=-1)
-    for bad in (dict(lags=[-1, 2], alphas=[0.1]), dict(lags=[], alphas=[0.1]), dict(lags=[1], alphas=[]),
+    for bad in (dict(lags=[-(1 << 21), 2], alphas=[0.1]), dict(lags=[], alphas=[0.1]), dict(lags=[1], alphas=[]),
                 dict(lags=[1], alphas=[float("nan")]), dict(lags=[1], alphas=[0.1], conj_flag=4)):
         with pytest.raises(cyc.CycError) as e:
             cyc.cyc_create_ex(**bad)

@@ -20,7 +20,7 @@ def alone(cyc, x, lags, alphas, forms, n0, precision):
 
 def stream_case(i):
     rng = np.random.default_rng(1000 + i)
-    L = int(rng.integers(1, 40))
+    L = int(rng.integers(1, 40)) if i != 11 else 100       # stream 11: wide (two-form) columns
     lags = np.sort(rng.choice(np.arange(0, 3 * L + 1), size=L, replace=False))
     A = int(rng.integers(1, 300))
     alphas = rng.uniform(-0.5, 0.5, A)
@@ -33,8 +33,12 @@ def stream_case(i):
     return dict(lags=lags, alphas=alphas, forms=forms, n0=n0, x=x, chunks=chunks)
 
 
+@pytest.mark.parametrize("pair", ["1", "0"])
 @pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("fp16", 1e-2)])
-def test_mix_equals_alone(cyc, precision, tol):
+def test_mix_equals_alone(cyc, precision, tol, pair, monkeypatch):
+    """pair = "1": items run on two-CTA pairs (the default where the GPU holds such clusters);
+    "0": one CTA per item (CYC_TC_PAIR=0)."""
+    monkeypatch.setenv("CYC_TC_PAIR", pair)
     cases = [stream_case(i) for i in range(12)]
     with cyc.Server(max_streams=16, precision=precision, item_samples=4096) as srv:
         sids = [srv.open(c["lags"], c["alphas"], c["forms"], c["n0"]) for c in cases]
