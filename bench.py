@@ -297,9 +297,11 @@ def latency_leg(pkg, calls=1000, warm=20):
             t0 = time.perf_counter()
             call()
             ts.append(time.perf_counter() - t0)
+        au = [sc.info()[1], sj.info()[1]]
     ts = np.array(ts) * 1e6
-    cmac = (T - 31) * 32 * 8 * 2
-    return {"workload": "cfg0 GMSK 65536 samples, lags 0..31, 64 a per form (8 distinct mod 1), CONV+CONJ, fp32",
+    cmac = (T - 31) * 32 * sum(au)
+    return {"workload": "cfg0 GMSK 65536 samples, lags 0..31, 64 a per form (k/8: %d distinct doubles mod 1; "
+                        "0.1 + k/8: %d), CONV+CONJ, fp32" % (au[0], au[1]),
             "calls": calls, "p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99)),
             "mean_us": float(ts.mean()), "gmac_s_at_p50": cmac / (np.percentile(ts, 50) * 1e-6) / 1e9,
             "call": "reset + push (device chunk) + read (host) for each form"}
@@ -429,6 +431,87 @@ def cross_leg(pkg, x_dev, T=1 << 24, reps=2):
         cmac = (T - 127) * 128 * NALPHAS * NFORMS
         res[name] = {"ms": m, "gmac_s": cmac / (m * 1e-3) / 1e9, "us_per_push": m * 1e3 / (T // C)}
     return res
+
+
+def window_leg(pkg, x_dev, T=1 << 24, reps=2):
+    """The block's windowed output (Eq. (impl-corr) at every window start k * hop, window-local
+    phase) at the config-1 shape: windows of N = 65536 reference samples every 4096 samples,
+    lags 0..127, 1024 cycle frequencies, both forms, BF16x3, 2^16-sample pushes, every window
+    read into device memory after each push; device time per push next to the running-sum
+    stream, and windows per second."""
+    import torch
+    C = CHUNK
+    N, H = 1 << 16, 4096
+    cap = 2 * C // H
+    lags = np.arange(NLAGS)
+    alphas = -0.5 + np.arange(NALPHAS) / NALPHAS
+    out = torch.empty((cap, NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
+    res = {"workload": "cfg1 shape, windows N=65536 every 4096 samples, lags 0..127, 1024 a, CONV+CONJ, bf16x3, "
+                       "%d samples" % T}
+    for name, window in (("windowed", (N, H, cap)), ("running_sums", None)):
+        nwin = [0]
+        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C, window=window) as s:
+            def run():
+                s.reset()
+                nwin[0] = 0
+                for c in range(T // C):
+                    s.push(x_dev[2 * c * C:2 * (c + 1) * C])
+                    if window is not None:
+                        W, _ = s.read_windows(cap, out)
+                        nwin[0] += W.shape[0]
+                s.sync()
+            run()
+            ms = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                run()
+                torch.cuda.synchronize()
+                ms.append((time.perf_counter() - t0) * 1e3)
+        m = statistics.median(ms)
+        res[name] = {"ms": m, "us_per_push": m * 1e3 / (T // C)}
+        if window is not None:
+            res[name]["windows"] = nwin[0]
+            res[name]["windows_per_s"] = nwin[0] / (m * 1e-3)
+    return res
+
+
+def full_leg(pkg, x_dev, reps=2):
+    """The paper's Full mode on the config-1 workload: every cycle frequency -1/2 + k/1024 (the
+    config-1 grid itself), lags 0..127, both forms, the whole stream in 2^16-sample pushes, one
+    read at the end.  The lag products (FP32) are folded modulo 1024 in FP64 and one FP64 DFT
+    per column runs at the read: a different algorithm from the projection, bound by the
+    sample reads of the fold rather than by the tensor pipe.  Reported: device time, samples/s,
+    the direct estimator's complex MACs per second for the same output, and the error on the
+    stored oracle entries."""
+    import torch
+    C = CHUNK
+    T = x_dev.numel() // 2
+    out = torch.empty((NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
+    with pkg.Stream(np.arange(NLAGS), None, pkg.CYC_BOTH, max_chunk=C, full=NALPHAS) as s:
+        def run():
+            s.reset()
+            for c in range(T // C):
+                s.push(x_dev[2 * c * C:2 * (c + 1) * C])
+            s.read(out)
+        run()
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        R = out.cpu().numpy()
+    m = statistics.median(ms)
+    R = R[..., 0] + 1j * R[..., 1]
+    return {"workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
+                        "%d samples in 2^16 pushes, fp32 products, fp64 fold + DFT" % T,
+            "ms": m, "msamples_s": T / (m * 1e-3) / 1e6, "us_per_push": m * 1e3 / (T // C),
+            "direct_equivalent_gmac_s": cmac_per_step(T) / (m * 1e-3) / 1e9,
+            "err_rel_r00": stored_error(R, "cfg1", T), "err_tol": TOL["fp32"]}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -615,6 +698,10 @@ def run_ours(args):
         line["cfg2_precisions"] = precision_leg(pkg)
     if rank == 0 and not args.no_cross:
         line["f1_cross"] = cross_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
+    if rank == 0 and not args.no_full:
+        line["f3_full_mode"] = full_leg(pkg, x_dev)
+    if rank == 0 and not args.no_windows:
+        line["f2_windows"] = window_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
     if rank == 0 and not args.no_proposer:
         line["cfg4_proposer"] = proposer_leg(pkg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -648,6 +735,8 @@ def main():
     ap.add_argument("--no-precisions", action="store_true", help="skip the config-2 precision leg")
     ap.add_argument("--no-proposer", action="store_true", help="skip the config-4 proposer leg")
     ap.add_argument("--no-cross", action="store_true", help="skip the two-input / signed-lag leg")
+    ap.add_argument("--no-windows", action="store_true", help="skip the windowed-output leg")
+    ap.add_argument("--no-full", action="store_true", help="skip the Full-mode leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")

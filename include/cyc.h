@@ -121,6 +121,49 @@ CYC_API int cyc_create_ex(const cyc_params* p, cyc_stream** out);
 CYC_API int cyc_create_xy(const cyc_params* p, cyc_stream** out);
 
 /*
+ * cyc_create_window: the block's windowed output (Sec. 4, Eq. (impl-corr) evaluated at
+ * window starts n0 = k * hop, k = 0, 1, ...).  Window k is the estimate over the win_len
+ * reference samples n = k * hop + M^- .. k * hop + M^- + win_len - 1 (sample indices from
+ * the first pushed sample), normalised by win_len, with the window-local phase of the
+ * equation: exp(-j 2 pi a n') with n' = 0 at the window's first reference sample.  The
+ * running sums of cyc_read keep their meaning.  A window is complete once its last x
+ * sample has been pushed; completed windows wait in a device ring of `capacity` windows
+ * for cyc_read_windows.  A push that would complete more windows than the ring has room
+ * for fails with CYC_EAGAIN before doing anything (read windows, then push again).
+ *   win_len   positive multiple of hop, win_len / hop <= 65536
+ *   hop       >= 16 samples between window starts
+ *   capacity  1 .. 2^20 windows of F * nalphas * nlags * 16 bytes each (plus device state of
+ *             (win_len / hop + capacity + 2) * (distinct a) * F * nlags * 16 bytes)
+ *   cross     0: one input (cyc_push); 1: two inputs (cyc_push_xy), as cyc_create_xy
+ * cyc_save / cyc_load return CYC_ENOTSUP for windowed streams.
+ */
+CYC_API int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop, int64_t capacity, int cross,
+                              cyc_stream** out);
+
+/*
+ * cyc_create_full: the paper's Full mode -- every cycle frequency of [-1/2, 1/2) on the
+ * uniform grid a_k = -1/2 + k/A, k = 0 .. A-1 (p->alphas and p->nalphas are ignored; the
+ * output's cycle-frequency index is k).  The result is the same estimator as a stream with
+ * those alphas (same layout for cyc_read, same range of n, absolute phase); on this grid the
+ * phase depends on n only through n mod A, so a push folds its lag products modulo A in FP64
+ * and cyc_read takes one A-point DFT per column: O(samples x columns) work per push instead
+ * of O(samples x columns x A).
+ *   A          power of two in [2, 4096]
+ *   precision  must be CYC_P_FP32 (FP32 lag products, FP64 folding and DFT); else CYC_EINVAL
+ *   cross      0: one input (cyc_push); 1: two inputs (cyc_push_xy)
+ * cyc_save / cyc_load, cyc_reset work as for any stream; windows are not available.
+ */
+CYC_API int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_stream** out);
+
+/*
+ * cyc_read_windows: move up to max_win completed windows, oldest first, out of the ring into
+ * out ([nwin][F][nalphas][nlags] complex FP64, host or device memory of the stream's device,
+ * synchronous).  *nwin receives how many were written (0 when none are complete), *first_k
+ * the index k of the first of them.  CYC_EINVAL on a stream not made by cyc_create_window.
+ */
+CYC_API int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k);
+
+/*
  * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
  * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
  * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read

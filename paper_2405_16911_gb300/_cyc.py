@@ -77,6 +77,9 @@ def load(path: str = LIB_PATH):
         "cyc_create": ([P, I, P, I, I, P], I),
         "cyc_create_ex": ([P, P], I),
         "cyc_create_xy": ([P, P], I),
+        "cyc_create_window": ([P, I64, I64, I64, I, P], I),
+        "cyc_create_full": ([P, I32, I, P], I),
+        "cyc_read_windows": ([P, P, I64, P, P], I),
         "cyc_push": ([P, P, I64, I], I),
         "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
@@ -159,8 +162,10 @@ def cyc_create(lags, alphas, conj_flag: int = CYC_BOTH) -> int:
 
 
 def cyc_create_ex(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
-                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False) -> int:
-    """cross=True: cyc_create_xy, a stream with two inputs (cyc_push_xy)."""
+                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False,
+                  window=None) -> int:
+    """cross=True: cyc_create_xy, a stream with two inputs (cyc_push_xy); window=(win_len, hop,
+    capacity): cyc_create_window (windowed output, cyc_read_windows)."""
     lib = load()
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
@@ -169,7 +174,11 @@ def cyc_create_ex(lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32,
     p = cyc_params(lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size, conj_flag, precision,
                    int(n0), int(max_chunk), cuda_stream or None, device)
     h = ctypes.c_void_p()
-    _check((lib.cyc_create_xy if cross else lib.cyc_create_ex)(ctypes.byref(p), ctypes.byref(h)))
+    if window is not None:
+        wl, hp, cap = window
+        _check(lib.cyc_create_window(ctypes.byref(p), int(wl), int(hp), int(cap), 1 if cross else 0, ctypes.byref(h)))
+    else:
+        _check((lib.cyc_create_xy if cross else lib.cyc_create_ex)(ctypes.byref(p), ctypes.byref(h)))
     _shapes[h.value] = (_nforms(conj_flag), alphas.size, lags.size)
     return h.value
 
@@ -207,6 +216,42 @@ def cyc_push_xy(h: int, x_chunk, y_chunk, nsamples: int | None = None, on_device
             raise ValueError("on_device is required with raw addresses or mixed host/device chunks")
         on_device = xd
     _check(load().cyc_push_xy(h, xa, ya, int(nsamples), int(on_device)))
+
+
+def cyc_create_full(lags, A: int, conj_flag: int = CYC_BOTH, n0: int = 0, max_chunk: int = 0, cuda_stream: int = 0,
+                    device: int = 0, cross: bool = False) -> int:
+    """Full mode: every cycle frequency a_k = -1/2 + k/A (FP32 lag products folded mod A)."""
+    lib = load()
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    p = cyc_params(lags.ctypes.data, lags.size, None, 0, conj_flag, CYC_P_FP32, int(n0), int(max_chunk),
+                   cuda_stream or None, device)
+    h = ctypes.c_void_p()
+    _check(lib.cyc_create_full(ctypes.byref(p), int(A), 1 if cross else 0, ctypes.byref(h)))
+    _shapes[h.value] = (_nforms(conj_flag), int(A), lags.size)
+    return h.value
+
+
+def cyc_create_window(lags, alphas, win_len: int, hop: int, capacity: int, conj_flag: int = CYC_BOTH,
+                      precision=CYC_P_FP32, n0: int = 0, max_chunk: int = 0, cuda_stream: int = 0, device: int = 0,
+                      cross: bool = False) -> int:
+    """A windowed stream: estimates over win_len reference samples every hop samples."""
+    return cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross,
+                         window=(win_len, hop, capacity))
+
+
+def cyc_read_windows(h: int, max_win: int, out=None):
+    """Completed windows, oldest first: (R [nwin][F][A][L] complex128 (a view of `out` or a new
+    array), index k of the first window)."""
+    F, A, L = cyc_shape(h)
+    if out is None:
+        out = np.empty((max_win, F, A, L), dtype=np.complex128)
+    addr, nbytes, _dev, _keep = _ptr_info(out)
+    if nbytes is not None and nbytes < max_win * F * A * L * 16:
+        raise ValueError("output buffer too small")
+    nw = ctypes.c_int64(0)
+    k0 = ctypes.c_int64(0)
+    _check(load().cyc_read_windows(h, addr, int(max_win), ctypes.byref(nw), ctypes.byref(k0)))
+    return out[:nw.value], int(k0.value)
 
 
 def cyc_read(h: int, out=None):
@@ -519,8 +564,16 @@ class Stream:
     """Owning wrapper: ``with Stream(lags, alphas, ...) as s: s.push(x); R, n = s.read()``."""
 
     def __init__(self, lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
-                 max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False):
-        self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross)
+                 max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False, window=None,
+                 full: int = 0):
+        """full=A: the uniform grid -1/2 + k/A by folding (alphas must be None)."""
+        if full:
+            if alphas is not None:
+                raise ValueError("full mode generates its own cycle frequencies; pass alphas=None")
+            self.h = cyc_create_full(lags, full, conj_flag, n0, max_chunk, cuda_stream, device, cross)
+        else:
+            self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross,
+                                   window)
         self.shape = _shapes[self.h]
         self.cross = cross
 
@@ -535,6 +588,9 @@ class Stream:
 
     def read(self, out=None):
         return cyc_read(self.h, out)
+
+    def read_windows(self, max_win: int, out=None):
+        return cyc_read_windows(self.h, max_win, out)
 
     def sync(self):
         cyc_sync(self.h)

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -58,6 +59,7 @@ constexpr int64_t kDefaultChunk = 1 << 20;
 constexpr int64_t kMaxChunk = 1ll << 28;
 constexpr int32_t kMaxLag = 1 << 20;
 constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
+constexpr int kWinSplits = 64;      // hop-aligned partials per pass of a windowed stream
 constexpr uint32_t kBlobVersion = 1;
 
 // a (cycles/sample) -> round(a * 2^64) mod 2^64, exactly.  a = m * 2^e with m the 53-bit
@@ -114,6 +116,18 @@ struct cyc_stream {
     int32_t M = 0;                  // lag span M^- + M^+: samples carried from push to push
     int32_t Mneg = 0;               // M^- = max(0, -min lag): window offset of Eq. (impl-corr)
     bool cross = false;             // two inputs (cyc_create_xy / cyc_push_xy)
+    // uniform grid a_k = -1/2 + k/A (cyc_create_full): sums holds the lag products folded mod A
+    bool full = false;
+    // windowed output (cyc_create_window): window k covers committed n in [k hop, k hop + N)
+    bool win = false;
+    int64_t win_len = 0, hop = 0, win_cap = 0;
+    int win_w = 0;                  // hops per window
+    int64_t hops = 0;               // hops completed
+    int64_t win_made = 0, win_read = 0;
+    double2* w_ring = nullptr;      // [win_w][Au][ncols] the last win_w completed hops
+    double2* w_sum = nullptr;       // [Au][ncols] sum of those
+    double2* w_pend = nullptr;      // [Au][ncols] the hop in progress
+    double2* w_out = nullptr;       // [win_cap][Au][ncols] raw sums of completed, unread windows
     std::vector<double> alphas;
     int A = 0;
     std::vector<uint64_t> phi_u;
@@ -154,13 +168,14 @@ struct cyc_stream {
     {
         free_events();
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
-                      part, d_out, d_err};
+                      part, d_out, d_err, w_ring, w_sum, w_pend, w_out};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
         stage[0] = stage[1] = stage_y[0] = stage_y[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
+        w_ring = w_sum = w_pend = w_out = nullptr;
     }
 };
 
@@ -226,7 +241,18 @@ int alloc_state(cyc_stream* s)
         s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
     else
         s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
+    if (s->win && s->part_elems < (size_t)kWinSplits * s->Au * s->ncols)
+        s->part_elems = (size_t)kWinSplits * s->Au * s->ncols;
     CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
+    if (s->win) {
+        const size_t nuc = (size_t)s->Au * s->ncols;
+        CK(cudaMalloc(&s->w_ring, (size_t)s->win_w * nuc * sizeof(double2)));
+        CK(cudaMalloc(&s->w_sum, nuc * sizeof(double2)));
+        CK(cudaMalloc(&s->w_pend, nuc * sizeof(double2)));
+        CK(cudaMalloc(&s->w_out, (size_t)s->win_cap * nuc * sizeof(double2)));
+        CK(cudaMemset(s->w_sum, 0, nuc * sizeof(double2)));
+        CK(cudaMemset(s->w_pend, 0, nuc * sizeof(double2)));
+    }
     CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
     CK(cudaMalloc(&s->d_err, sizeof(int)));
     CK(cudaMemset(s->d_err, 0, sizeof(int)));
@@ -258,6 +284,11 @@ int project(cyc_stream* s, int64_t nc)
     ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)
                   : small                    ? small_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : fp32_plan(s->Au, s->ncols, nc, s->num_sms);
+    if (s->win) {                     // one split per hop (the first and last may be partial)
+        a.split_off = s->n_eff % s->hop;
+        pl.split_len = s->hop;
+        pl.nsplit = (int)((nc + a.split_off + s->hop - 1) / s->hop);
+    }
     a.nsplit = pl.nsplit;
     a.split_len = pl.split_len;
     if ((size_t)pl.nsplit * s->Au * s->ncols > s->part_elems)
@@ -273,7 +304,8 @@ int project(cyc_stream* s, int64_t nc)
         }
         CK(cudaEventRecord(ev.first, s->st));
     }
-    CK(s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->pair_ctas > 0, s->st)
+    CK(s->full                    ? full_fold(a, s->Au, s->sums, s->st)
+       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->pair_ctas > 0, s->st)
        : small                    ? small_launch(a, s->st)
                                   : fp32_launch(a, s->st));
     if (s->prof) {
@@ -281,7 +313,31 @@ int project(cyc_stream* s, int64_t nc)
         s->ev_pending.push_back(ev);
     }
     s->prof_launches++;
-    CK(reduce_partials(s->part, pl.nsplit, s->Au * s->ncols, s->sums, s->st));
+    if (s->full) {
+        // (the fold replaced the projection above)
+    } else if (s->win) {
+        HopArgs h;
+        h.part = s->part;
+        h.nsplit = pl.nsplit;
+        h.n_uc = s->Au * s->ncols;
+        h.off = a.split_off;
+        h.nc = nc;
+        h.hop = s->hop;
+        h.w = s->win_w;
+        h.hops0 = s->hops;
+        h.ring = s->w_ring;
+        h.wsum = s->w_sum;
+        h.pend = s->w_pend;
+        h.sums = s->sums;
+        h.wout = s->w_out;
+        h.cap = s->win_cap;
+        CK(fold_hops(h, s->st));
+        const int64_t done = (s->n_eff + nc) / s->hop;           // hops complete after this pass
+        s->hops = done;
+        s->win_made = done >= s->win_w ? done - s->win_w + 1 : 0;
+    } else {
+        CK(reduce_partials(s->part, pl.nsplit, s->Au * s->ncols, s->sums, s->st));
+    }
     s->kernel_launches += 2;
     return CYC_OK;
 }
@@ -335,7 +391,8 @@ int cyc_create(const int32_t* lags, int nlags, const double* alphas, int nalphas
     return cyc_create_ex(&p, out);
 }
 
-static int create_impl(const cyc_params* p, bool cross, cyc_stream** out)
+static int create_impl(const cyc_params* p, bool cross, int64_t win_len, int64_t hop, int64_t win_cap,
+                       cyc_stream** out, bool full = false)
 {
     if (!out) return fail(CYC_EINVAL, "cyc_create_ex: out is NULL");
     *out = nullptr;
@@ -359,6 +416,14 @@ static int create_impl(const cyc_params* p, bool cross, cyc_stream** out)
     s->lags.assign(p->lags, p->lags + p->nlags);
     s->L = p->nlags;
     s->cross = cross;
+    s->full = full;
+    if (win_len > 0) {
+        s->win = true;
+        s->win_len = win_len;
+        s->hop = hop;
+        s->win_w = (int)(win_len / hop);
+        s->win_cap = win_cap;
+    }
     int32_t lo = 0, hi = 0;
     for (int32_t m : s->lags) {
         lo = m < lo ? m : lo;
@@ -391,6 +456,10 @@ static int create_impl(const cyc_params* p, bool cross, cyc_stream** out)
     h = fnv1a(h, &s->n0, sizeof s->n0);
     const int32_t xy = s->cross ? 1 : 0;
     h = fnv1a(h, &xy, sizeof xy);
+    h = fnv1a(h, &s->win_len, sizeof s->win_len);
+    const int32_t fm = s->full ? 1 : 0;
+    h = fnv1a(h, &fm, sizeof fm);
+    h = fnv1a(h, &s->hop, sizeof s->hop);
     s->fingerprint = h;
 
     if (s->precision != CYC_P_FP32 && !tc_supported(s->ncols, s->M)) {
@@ -418,15 +487,47 @@ static int create_impl(const cyc_params* p, bool cross, cyc_stream** out)
     return CYC_OK;
 }
 
-int cyc_create_ex(const cyc_params* p, cyc_stream** out) { return create_impl(p, false, out); }
+int cyc_create_ex(const cyc_params* p, cyc_stream** out) { return create_impl(p, false, 0, 0, 0, out); }
 
-int cyc_create_xy(const cyc_params* p, cyc_stream** out) { return create_impl(p, true, out); }
+int cyc_create_xy(const cyc_params* p, cyc_stream** out) { return create_impl(p, true, 0, 0, 0, out); }
+
+int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_stream** out)
+{
+    if (out) *out = nullptr;
+    if (!p) return fail(CYC_EINVAL, "cyc_create_full: params is NULL");
+    if (!full_supported(A)) return fail(CYC_EINVAL, "cyc_create_full: A must be a power of two in [2, 4096]");
+    if (p->precision != CYC_P_FP32) return fail(CYC_EINVAL, "cyc_create_full: the folded grid runs in FP32/FP64 only");
+    std::vector<double> grid(A);
+    for (int k = 0; k < A; ++k) grid[k] = -0.5 + (double)k / (double)A;          // exact in binary
+    cyc_params q = *p;
+    q.alphas = grid.data();
+    q.nalphas = A;
+    return create_impl(&q, cross != 0, 0, 0, 0, out, true);
+}
+
+int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop, int64_t capacity, int cross,
+                      cyc_stream** out)
+{
+    if (out) *out = nullptr;
+    if (hop < 16 || win_len < hop || win_len % hop != 0 || win_len / hop > (1 << 16))
+        return fail(CYC_EINVAL, "cyc_create_window: need hop >= 16, win_len a multiple of hop, win_len / hop <= 65536");
+    if (capacity < 1 || capacity > (1 << 20)) return fail(CYC_EINVAL, "cyc_create_window: capacity must be in [1, 2^20]");
+    return create_impl(p, cross != 0, win_len, hop, capacity, out);
+}
 
 static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int64_t nsamples, int on_device,
                      const char* who)
 {
     if (nsamples < 0) return fail(CYC_EINVAL, "%s: nsamples < 0", who);
     if (nsamples == 0) return CYC_OK;
+    if (s->win) {                     // room for every window this push completes?
+        const int64_t T2 = s->T + nsamples;
+        const int64_t hops2 = (T2 > s->M ? T2 - s->M : 0) / s->hop;
+        const int64_t made2 = hops2 >= s->win_w ? hops2 - s->win_w + 1 : 0;
+        if (made2 - s->win_read > s->win_cap)
+            return fail(CYC_EAGAIN, "%s: the push would complete %lld windows with room for %lld; read windows first",
+                        who, (long long)(made2 - s->win_made), (long long)(s->win_cap - (s->win_made - s->win_read)));
+    }
     if (!xchunk || (s->cross && !ychunk)) return fail(CYC_EINVAL, "%s: chunk is NULL", who);
     DeviceGuard g(s->device);
     if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
@@ -439,8 +540,10 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
     const float2* src = (const float2*)xchunk;
     const float2* ysrc = (const float2*)ychunk;
     int64_t left = nsamples;
+    // a windowed pass holds at most kWinSplits hop-aligned partials
+    const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(kWinSplits - 1) * s->hop) : s->max_chunk;
     while (left > 0) {
-        int64_t c = left < s->max_chunk ? left : s->max_chunk;
+        int64_t c = left < pass ? left : pass;
         float2* view = s->stage[s->cur];
         // a1: the view is [carried tail (held samples) | new samples], for both inputs
         CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, s->st));
@@ -507,10 +610,48 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     bool dev = is_device_ptr(out, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_read: out is memory of another device");
     double2* dst = dev ? (double2*)out : s->d_out;
-    CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st));
+    if (s->full)
+        CK(full_read(s->sums, s->Au, s->ncols, s->F, s->L, 1.0 / (double)s->n_eff, dst, s->st));
+    else
+        CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st));
     s->kernel_launches++;
     if (!dev)
         CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+    return sync_and_check(s);
+}
+
+int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_read_windows: handle is NULL");
+    if (!s->win) return fail(CYC_EINVAL, "cyc_read_windows: not a windowed stream (cyc_create_window)");
+    if (nwin) *nwin = 0;
+    if (first_k) *first_k = s->win_read;
+    int64_t n = s->win_made - s->win_read;
+    if (n > max_win) n = max_win;
+    if (n <= 0) return CYC_OK;
+    if (!out) return fail(CYC_EINVAL, "cyc_read_windows: out is NULL");
+    DeviceGuard g(s->device);
+    bool wrong = false;
+    const bool dev = is_device_ptr(out, s->device, &wrong);
+    if (wrong) return fail(CYC_EINVAL, "cyc_read_windows: out is memory of another device");
+    const int64_t per = (int64_t)s->F * s->A * s->L;
+    const uint64_t base = (uint64_t)s->n0 + (uint64_t)s->Mneg;
+    const double inv_n = 1.0 / (double)s->win_len;
+    if (dev) {
+        CK(read_windows(s->w_out, s->win_cap, s->win_read, n, s->d_amap, s->d_phi, s->F, s->A, s->L, s->Au, s->ncols,
+                        base, s->hop, inv_n, (double2*)out, s->st));
+        s->kernel_launches += 1;
+    } else {
+        for (int64_t i = 0; i < n; ++i) {            // one window at a time through the read buffer
+            CK(read_windows(s->w_out, s->win_cap, s->win_read + i, 1, s->d_amap, s->d_phi, s->F, s->A, s->L, s->Au,
+                            s->ncols, base, s->hop, inv_n, s->d_out, s->st));
+            CK(cudaMemcpyAsync((double2*)out + i * per, s->d_out, (size_t)per * sizeof(double2),
+                               cudaMemcpyDeviceToHost, s->st));
+        }
+        s->kernel_launches += n;
+    }
+    s->win_read += n;
+    if (nwin) *nwin = n;
     return sync_and_check(s);
 }
 
@@ -519,6 +660,11 @@ int cyc_reset(cyc_stream* s)
     if (!s) return fail(CYC_EINVAL, "cyc_reset: handle is NULL");
     DeviceGuard g(s->device);
     CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+    if (s->win) {
+        CK(cudaMemsetAsync(s->w_sum, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+        CK(cudaMemsetAsync(s->w_pend, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+        s->hops = s->win_made = s->win_read = 0;
+    }
     s->T = s->n_eff = s->held = 0;
     return CYC_OK;
 }
@@ -538,6 +684,7 @@ int cyc_destroy(cyc_stream* s)
 int cyc_save(cyc_stream* s, void* buf, size_t* len)
 {
     if (!s || !len) return fail(CYC_EINVAL, "cyc_save: NULL argument");
+    if (s->win) return fail(CYC_ENOTSUP, "cyc_save: windowed streams keep no blob");
     size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
     const size_t held_b = (size_t)s->held * sizeof(float2) * (s->cross ? 2 : 1);
     size_t need = sizeof(BlobHeader) + held_b + sums_b;
@@ -569,6 +716,7 @@ int cyc_save(cyc_stream* s, void* buf, size_t* len)
 int cyc_load(cyc_stream* s, const void* buf, size_t len)
 {
     if (!s || !buf) return fail(CYC_EINVAL, "cyc_load: NULL argument");
+    if (s->win) return fail(CYC_ENOTSUP, "cyc_load: windowed streams keep no blob");
     BlobHeader h;
     if (len < sizeof h) return fail(CYC_EINVAL, "cyc_load: blob too short");
     memcpy(&h, buf, sizeof h);

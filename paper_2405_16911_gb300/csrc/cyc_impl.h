@@ -35,6 +35,7 @@ struct ProjArgs {
     int64_t         x_avail = 0;    // samples readable from x (and y) (allocation bound, even)
     const float2*   y = nullptr;    // second input, same indexing as x; nullptr: y = x
     int             D = 0;          // offset M^- of the reference sample y[n + D]
+    int64_t         split_off = 0;  // split s covers [s * split_len - split_off, + split_len) within [0, nc)
 };
 
 // One work item of the tensor-core projection: 128 cycle frequencies x 128 columns x an
@@ -86,6 +87,13 @@ cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t 
 size_t      tc_max_partials(int Au, int ncols, int num_sms);
 int         tc_tile_rows();     // cycle frequencies per work item
 int         tc_tile_cols();     // columns per work item
+// The uniform grid a_k = -1/2 + k/A (full_mode.cu): fold a pass's lag products modulo A into
+// F ([A][ncols], FP64, accumulated), and at read time the A-point DFT of every column into
+// out[f][k][l] / N.  A a power of two in [2, 4096].
+bool        full_supported(int A);
+cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st);
+cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double inv_n, double2* out, cudaStream_t st);
+
 // Persistent launch over a device list of work items (taken with an atomic counter that
 // the caller zeroes before the launch); `grid` CTAs, one per SM.  pair = true: `grid`
 // (even) CTAs in two-CTA clusters, each item covering rows u0 .. u0 + 255 (the odd CTA's
@@ -99,6 +107,31 @@ void record_error(const char* msg);
 // Helpers (cyc_kernels.cu).
 // sums[u][c] += sum_s part[s][u][c]  (FP64)
 cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* sums, cudaStream_t st);
+// Windowed streams (cyc_create_window): fold the hop-aligned partials of one pass into the
+// pending hop, the ring of the last w completed hops, the running window sum and the FP64
+// running sums; every window that completes gets its raw (absolute-phase) sum written to
+// slot k % cap of `wout` ([cap][n_uc]).  Split s ends a hop when s * hop + hop - off <= nc.
+struct HopArgs {
+    const float2* part;
+    int           nsplit;
+    int           n_uc;
+    int64_t       off, nc, hop;
+    int           w;                // hops per window
+    int64_t       hops0;            // hops completed before this pass
+    double2*      ring;             // [w][n_uc]
+    double2*      wsum;             // [n_uc]
+    double2*      pend;             // [n_uc]
+    double2*      sums;             // [n_uc]
+    double2*      wout;             // [cap][n_uc]
+    int64_t       cap;
+};
+cudaError_t fold_hops(const HopArgs& h, cudaStream_t st);
+// Windows k0 .. k0 + n - 1 of a windowed stream into out[i][f][a][l]: wout[k % cap][amap[a]]
+// [l F + f] times exp(+j 2 pi phi_a (base + k hop) / 2^64) / N (the window-local phase of
+// Eq. (impl-corr)).
+cudaError_t read_windows(const double2* wout, int64_t cap, int64_t k0, int64_t n, const int32_t* amap,
+                         const uint64_t* phi, int F, int A, int L, int Au, int ncols, uint64_t base, int64_t hop,
+                         double inv_n, double2* out, cudaStream_t st);
 // out[f][a][l] = sums[amap[a]][l * F + f] / n_eff
 cudaError_t read_sums(const double2* sums, const int32_t* amap, int F, int A, int L, int ncols,
                       double inv_n, double2* out, cudaStream_t st);

@@ -1,0 +1,123 @@
+// full_mode.cu -- the estimator on a uniform cycle-frequency grid a_k = -1/2 + k/A (the
+// paper's Full mode, Sec. 4: every cycle frequency of [-1/2, 1/2) at resolution 1/A).
+//
+// For a_k on that grid the phase term depends on the absolute sample index n only through
+// n mod A (A even):  exp(-j 2 pi a_k n) = (-1)^n exp(-j 2 pi k n / A), and (-1)^n = (-1)^r
+// for r = n mod A.  So
+//     sum_n P_c(n) exp(-j 2 pi a_k n) = sum_{r<A} (-1)^r F_c[r] exp(-j 2 pi k r / A),
+//     F_c[r] = sum_{n = r mod A} P_c(n),
+// an A-point DFT of the lag products folded modulo A.  A push only folds (O(samples x
+// columns) work, bound by memory traffic instead of the O(samples x columns x A) projection);
+// the DFT runs when the estimate is read.  F lives in FP64 in the stream's sums array,
+// [A][ncols], so reset, save and load work unchanged.
+#include "cyc_device.cuh"
+#include "cyc_impl.h"
+
+namespace cyc {
+namespace {
+
+constexpr int FOLD_T = 256;
+
+// Thread (r, c): F_c[r] += sum over pass terms i with (base + i) mod A == r of
+// x[i + col_lag[c]] c(y[i + D]).  Consecutive threads take consecutive residues, so the
+// sample reads of a warp are consecutive.
+__global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__ x, const float2* __restrict__ y,
+                                                      int D, int64_t nc, int A, int base_mod,
+                                                      const int32_t* __restrict__ col_lag,
+                                                      const int8_t* __restrict__ col_conj, int ncols,
+                                                      double2* __restrict__ F)
+{
+    const int r = blockIdx.x * FOLD_T + threadIdx.x;
+    const int c = blockIdx.y;
+    if (r >= A) return;
+    const int m = col_lag[c];
+    const bool cj = col_conj[c] != 0;
+    int64_t i = r - base_mod;
+    if (i < 0) i += A;
+    double tr = 0.0, ti = 0.0;
+    // FP32 runs of at most 64 terms, each added once to the FP64 total
+    while (i < nc) {
+        float sr = 0.f, si = 0.f;
+        for (int q = 0; q < 64 && i < nc; ++q, i += A) {
+            const float2 p = lag_product(__ldg(&x[i + m]), __ldg(&y[i + D]), cj);
+            sr += p.x;
+            si += p.y;
+        }
+        tr += (double)sr;
+        ti += (double)si;
+    }
+    double2* f = F + (size_t)r * ncols + c;
+    const double2 o = *f;
+    *f = make_double2(o.x + tr, o.y + ti);
+}
+
+// Block c: out[f][k][l] = (1/N) sum_r (-1)^r F_c[r] exp(-j 2 pi k r / A) for column
+// c = l F + f, by an in-place radix-2 FFT in shared memory (FP64).
+__global__ void dft_read_kernel(const double2* __restrict__ F, int A, int logA, int ncols, int nF, int L,
+                                double inv_n, double2* __restrict__ out)
+{
+    extern __shared__ double2 v[];
+    double2* tw = v + A;                                               // exp(-j 2 pi j / A), j < A/2
+    const int c = blockIdx.x;
+    for (int j = threadIdx.x; j < A / 2; j += blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)j / (double)A, &sn, &cs);
+        tw[j] = make_double2(cs, sn);
+    }
+    for (int r = threadIdx.x; r < A; r += blockDim.x) {
+        const double2 q = F[(size_t)r * ncols + c];
+        const double s = (r & 1) ? -1.0 : 1.0;
+        const unsigned rev = __brev((unsigned)r) >> (32 - logA);       // bit-reversed position
+        v[rev] = make_double2(s * q.x, s * q.y);
+    }
+    __syncthreads();
+    for (int len = 2; len <= A; len <<= 1) {
+        const int half = len >> 1;
+        for (int t = threadIdx.x; t < A / 2; t += blockDim.x) {
+            const int grp = t / half, j = t % half;
+            const int i0 = grp * len + j, i1 = i0 + half;
+            const double2 z = tw[j * (A / len)];                             // exp(-j 2 pi j / len)
+            const double2 b = v[i1];
+            const double2 w = make_double2(b.x * z.x - b.y * z.y, b.x * z.y + b.y * z.x);
+            const double2 a = v[i0];
+            v[i0] = make_double2(a.x + w.x, a.y + w.y);
+            v[i1] = make_double2(a.x - w.x, a.y - w.y);
+        }
+        __syncthreads();
+    }
+    const int f = c % nF, l = c / nF;
+    for (int k = threadIdx.x; k < A; k += blockDim.x)
+        out[((size_t)f * A + k) * L + l] = make_double2(v[k].x * inv_n, v[k].y * inv_n);
+}
+
+}  // namespace
+
+bool full_supported(int A) { return A >= 2 && A <= 4096 && (A & (A - 1)) == 0; }
+
+cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st)
+{
+    if (a.nc <= 0) return cudaSuccess;
+    const int base_mod = (int)(a.nbase & (uint64_t)(A - 1));
+    dim3 grid((A + FOLD_T - 1) / FOLD_T, a.ncols);
+    fold_kernel<<<grid, FOLD_T, 0, st>>>(a.x, a.y ? a.y : a.x, a.D, a.nc, A, base_mod, a.col_lag, a.col_conj,
+                                         a.ncols, F);
+    return cudaGetLastError();
+}
+
+cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double inv_n, double2* out, cudaStream_t st)
+{
+    int logA = 0;
+    while ((1 << logA) < A) ++logA;
+    const size_t smem = (size_t)A * 3 / 2 * sizeof(double2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(dft_read_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             4096 * 3 / 2 * 16);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dft_read_kernel<<<ncols, 256, smem, st>>>(F, A, logA, ncols, nF, L, inv_n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cyc

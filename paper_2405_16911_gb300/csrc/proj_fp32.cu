@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(NT, 1) proj_fp32_kernel(ProjArgs a)
     const int u0 = blockIdx.x * TA;
     const int c0 = blockIdx.y * TC;
     const int split = blockIdx.z;
-    const int64_t n_beg = (int64_t)split * a.split_len;
+    int64_t n_beg = (int64_t)split * a.split_len - a.split_off;
     int64_t n_end = n_beg + a.split_len;
+    if (n_beg < 0) n_beg = 0;
     if (n_end > a.nc) n_end = a.nc;
 
     // generator roles

@@ -1,6 +1,6 @@
 // proj_small.cu -- FP32 a-projection for a handful of distinct cycle frequencies.
 //
-// When only a few a are distinct (Au <= 16), a 128-row GEMM tile would be almost empty.
+// When only a few a are distinct (Au <= 32), a 128-row GEMM tile would be almost empty.
 // Here every thread keeps the complex sums of all Au cycle frequencies x CB columns in
 // registers while it walks its own strided samples (x[n] and x[n+m] are read once per
 // sample for all of them), and the block then folds its threads' sums with warp shuffles
@@ -21,21 +21,22 @@ __global__ void __launch_bounds__(NT) proj_small_kernel(ProjArgs a)
     __shared__ float red[NT / 32][2 * AU * CB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = blockIdx.x * CB;
-    const int64_t n_beg = (int64_t)blockIdx.y * a.split_len;
+    int64_t n_beg = (int64_t)blockIdx.y * a.split_len - a.split_off;
     int64_t n_end = n_beg + a.split_len;
+    if (n_beg < 0) n_beg = 0;
     if (n_end > a.nc) n_end = a.nc;
 
-    uint64_t phi[AU];
-#pragma unroll
-    for (int u = 0; u < AU; ++u) phi[u] = u < a.Au ? a.phi[u] : 0ull;
-    int lag[CB];
-    bool cj[CB], okc[CB];
-#pragma unroll
-    for (int j = 0; j < CB; ++j) {
+    // per-block constants in shared memory (read as broadcasts): registers stay for the sums
+    __shared__ uint64_t phi[AU];
+    __shared__ int lag[CB];
+    __shared__ bool cj[CB], okc[CB];
+    for (int u = tid; u < AU; u += NT) phi[u] = u < a.Au ? a.phi[u] : 0ull;
+    for (int j = tid; j < CB; j += NT) {
         okc[j] = c0 + j < a.ncols;
         lag[j] = okc[j] ? a.col_lag[c0 + j] : 0;
         cj[j] = okc[j] && a.col_conj[c0 + j];
     }
+    __syncthreads();
     float sr[AU][CB], si[AU][CB];
 #pragma unroll
     for (int u = 0; u < AU; ++u)
@@ -98,12 +99,12 @@ cudaError_t launch(const ProjArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int au_class(int Au) { return Au <= 1 ? 1 : Au <= 2 ? 2 : Au <= 4 ? 4 : Au <= 8 ? 8 : 16; }
+int au_class(int Au) { return Au <= 1 ? 1 : Au <= 2 ? 2 : Au <= 4 ? 4 : Au <= 8 ? 8 : Au <= 16 ? 16 : 32; }
 int cb_of(int Au) { return 64 / au_class(Au) > 32 ? 32 : 64 / au_class(Au); }
 
 }  // namespace
 
-bool small_supported(int Au) { return Au >= 1 && Au <= 16; }
+bool small_supported(int Au) { return Au >= 1 && Au <= 32; }
 
 ProjPlan small_plan(int Au, int ncols, int64_t nc, int num_sms)
 {
@@ -132,7 +133,8 @@ cudaError_t small_launch(const ProjArgs& a, cudaStream_t st)
     case 2: return launch<2, 32>(a, st);
     case 4: return launch<4, 16>(a, st);
     case 8: return launch<8, 8>(a, st);
-    default: return launch<16, 4>(a, st);
+    case 16: return launch<16, 4>(a, st);
+    default: return launch<32, 2>(a, st);
     }
 }
 

@@ -237,8 +237,9 @@ __device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, i
     it.xmask = ~0ull;
     it.x_avail = a.x_avail;
     it.nbase = a.nbase;
-    it.n_beg = (int64_t)bz * a.split_len;
-    it.n_end = it.n_beg + a.split_len < a.nc ? it.n_beg + a.split_len : a.nc;
+    const int64_t b = (int64_t)bz * a.split_len - a.split_off;
+    it.n_beg = b > 0 ? b : 0;
+    it.n_end = b + a.split_len < a.nc ? b + a.split_len : a.nc;
     it.phi = a.phi;
     it.col_lag = a.col_lag;
     it.col_conj = a.col_conj;

@@ -256,10 +256,11 @@ def test_tensor_core_lag_limit(cyc, precision):
     assert e.value.code == cyc.CYC_ENOTSUP
 
 
-@pytest.mark.parametrize("na", [1, 2, 5, 8, 16, 17])
+@pytest.mark.parametrize("na", [1, 2, 5, 8, 16, 17, 32, 33])
 def test_fp32_small_and_general_paths(cyc, na):
-    """FP32 with at most 16 distinct cycle frequencies takes the register/warp-shuffle path,
-    17 and more the GEMM-tiled one; both match the oracle on ragged column counts."""
+    """FP32 with at most 32 distinct cycle frequencies takes the register/warp-shuffle path
+    (classes of 1, 2, 4, 8, 16, 32), 33 and more the GEMM-tiled one; both match the oracle on
+    ragged column counts."""
     x = synth.white(12007, seed=111).astype(np.complex64)
     lags = np.array([0, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89])
     alphas = np.linspace(-0.45, 0.45, na) if na > 1 else np.array([0.2])
