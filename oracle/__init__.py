@@ -183,3 +183,28 @@ def windows(x, y, lags, alphas, win_len: int, hop: int, forms: int = CONV | CONJ
     if rc != 0:
         raise ValueError("oracle: bad arguments")
     return out[:nmax, ..., 0] + 1j * out[:nmax, ..., 1]
+
+
+def lag_window(lags, taper: int) -> np.ndarray:
+    """Lag weights: taper 0 rectangular (1), taper 1 Hann centred on m = 0,
+    w(m) = 0.5 + 0.5 cos(pi m / (Mmax + 1)) with Mmax = max |m|."""
+    lags = np.asarray(lags, dtype=np.float64)
+    if taper == 0:
+        return np.ones_like(lags)
+    mmax = np.max(np.abs(lags))
+    return 0.5 + 0.5 * np.cos(np.pi * lags / (mmax + 1.0))
+
+
+def spectrum(R, lags, Q: int, taper: int = 0) -> np.ndarray:
+    """Cyclic spectrum of an estimate R [F][A][L] over its lags (cyclic correlogram):
+    S[f][a][q] = sum_l w(m_l) R[f][a][l] exp(-j 2 pi f_q m_l), f_q = -1/2 + q/Q.
+    Written as the plain double sum (FP64); complex128 [F][A][Q]."""
+    R = np.asarray(R, dtype=np.complex128)
+    lags = np.asarray(lags)
+    w = lag_window(lags, taper)
+    S = np.zeros(R.shape[:2] + (int(Q),), dtype=np.complex128)
+    for q in range(int(Q)):
+        fq = -0.5 + q / Q
+        e = w * np.exp(-2j * np.pi * np.mod(fq * lags, 1.0))
+        S[..., q] = np.tensordot(R, e, axes=([2], [0]))
+    return S
