@@ -505,9 +505,19 @@ def full_leg(pkg, x_dev, reps=2):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         R = out.cpu().numpy()
+        # f4: cyclic spectra of that estimate, 256 frequencies, Hann lag window
+        spec = torch.empty((NFORMS, NALPHAS, 256, 2), dtype=torch.float64, device="cuda")
+        s.read_spectrum(256, 1, spec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            s.read_spectrum(256, 1, spec)
+        t_spec = (time.perf_counter() - t0) / 5
     m = statistics.median(ms)
     R = R[..., 0] + 1j * R[..., 1]
-    return {"workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
+    return {"spectrum_ms": t_spec * 1e3,
+            "spectrum": "cyc_read_spectrum: 2 x 1024 cycle frequencies x 256 frequencies over 128 lags, Hann, FP64",
+            "workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
                         "%d samples in 2^16 pushes, fp32 products, fp64 fold + DFT" % T,
             "ms": m, "msamples_s": T / (m * 1e-3) / 1e6, "us_per_push": m * 1e3 / (T // C),
             "direct_equivalent_gmac_s": cmac_per_step(T) / (m * 1e-3) / 1e9,

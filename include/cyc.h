@@ -164,6 +164,18 @@ CYC_API int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_strea
 CYC_API int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k);
 
 /*
+ * cyc_read_spectrum: cyclic spectra of the current estimate (the cyclic correlogram; the
+ * paper names cyclic spectra as its next step, Sec. 6): for every form and cycle frequency,
+ *   S[f][a][q] = sum_l w(m_l) R[f][a][l] exp(-j 2 pi f_q m_l),   f_q = -1/2 + q/Q, q < Q,
+ * over the stream's (signed) lags m_l, with R as cyc_read returns it.  taper 0: w = 1;
+ * taper 1: the Hann lag window w(m) = 0.5 + 0.5 cos(pi m / (Mmax + 1)), Mmax = max |m_l|.
+ * out: [F][nalphas][Q] complex FP64, host or device memory of the stream's device;
+ * synchronous.  Q in [1, 65536]; CYC_ENODATA when N_eff is 0.  Device scratch of
+ * nlags * Q + F * nalphas * Q complex doubles is kept with the stream after the first call.
+ */
+CYC_API int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out);
+
+/*
  * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
  * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
  * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read

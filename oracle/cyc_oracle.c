@@ -22,6 +22,10 @@
  * Streaming is not modelled: the streaming estimator over any chunking is, by
  * definition, this batch estimator applied to the concatenation of all pushed samples.
  *
+ * cyco_estimate_xy is the same equation in full (two inputs, signed lags) and cyco_windows
+ * the block's windowed output (window-local phase); both are described where they are
+ * defined below.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction is off so that the
  * x86 and Arm builds round identically).
  */

@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "cyc_create_window": ([P, I64, I64, I64, I, P], I),
         "cyc_create_full": ([P, I32, I, P], I),
         "cyc_read_windows": ([P, P, I64, P, P], I),
+        "cyc_read_spectrum": ([P, I32, I32, P], I),
         "cyc_push": ([P, P, I64, I], I),
         "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
@@ -252,6 +253,18 @@ def cyc_read_windows(h: int, max_win: int, out=None):
     k0 = ctypes.c_int64(0)
     _check(load().cyc_read_windows(h, addr, int(max_win), ctypes.byref(nw), ctypes.byref(k0)))
     return out[:nw.value], int(k0.value)
+
+
+def cyc_read_spectrum(h: int, Q: int, taper: int = 0, out=None):
+    """Cyclic spectra [F][A][Q] (complex128; `out` torch/numpy or a new numpy array)."""
+    F, A, L = cyc_shape(h)
+    if out is None:
+        out = np.empty((F, A, int(Q)), dtype=np.complex128)
+    addr, nbytes, _dev, _keep = _ptr_info(out)
+    if nbytes is not None and nbytes < F * A * int(Q) * 16:
+        raise ValueError("output buffer too small")
+    _check(load().cyc_read_spectrum(h, int(Q), int(taper), addr))
+    return out
 
 
 def cyc_read(h: int, out=None):
@@ -591,6 +604,9 @@ class Stream:
 
     def read_windows(self, max_win: int, out=None):
         return cyc_read_windows(self.h, max_win, out)
+
+    def read_spectrum(self, Q: int, taper: int = 0, out=None):
+        return cyc_read_spectrum(self.h, Q, taper, out)
 
     def sync(self):
         cyc_sync(self.h)

@@ -128,6 +128,11 @@ struct cyc_stream {
     double2* w_sum = nullptr;       // [Au][ncols] sum of those
     double2* w_pend = nullptr;      // [Au][ncols] the hop in progress
     double2* w_out = nullptr;       // [win_cap][Au][ncols] raw sums of completed, unread windows
+    // cyclic spectra (cyc_read_spectrum), allocated on first use
+    int32_t* d_lags = nullptr;      // the signed lags [L]
+    double2* sp_E = nullptr;        // DFT matrix [L][sp_Q]
+    double2* sp_S = nullptr;        // spectrum [F][A][sp_Q] for host outputs
+    int sp_Q = 0;
     std::vector<double> alphas;
     int A = 0;
     std::vector<uint64_t> phi_u;
@@ -168,7 +173,7 @@ struct cyc_stream {
     {
         free_events();
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
-                      part, d_out, d_err, w_ring, w_sum, w_pend, w_out};
+                      part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
@@ -176,6 +181,9 @@ struct cyc_stream {
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
         w_ring = w_sum = w_pend = w_out = nullptr;
+        d_lags = nullptr;
+        sp_E = sp_S = nullptr;
+        sp_Q = 0;
     }
 };
 
@@ -617,6 +625,46 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     s->kernel_launches++;
     if (!dev)
         CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+    return sync_and_check(s);
+}
+
+int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_read_spectrum: handle is NULL");
+    if (Q < 1 || Q > (1 << 16)) return fail(CYC_EINVAL, "cyc_read_spectrum: Q must be in [1, 65536]");
+    if (taper != 0 && taper != 1) return fail(CYC_EINVAL, "cyc_read_spectrum: taper must be 0 or 1");
+    if (s->n_eff == 0) return fail(CYC_ENODATA, "cyc_read_spectrum: N_eff is 0");
+    if (!out) return fail(CYC_EINVAL, "cyc_read_spectrum: out is NULL");
+    DeviceGuard g(s->device);
+    bool wrong = false;
+    const bool dev = is_device_ptr(out, s->device, &wrong);
+    if (wrong) return fail(CYC_EINVAL, "cyc_read_spectrum: out is memory of another device");
+    if (!s->d_lags) {
+        CK(cudaMalloc(&s->d_lags, (size_t)s->L * sizeof(int32_t)));
+        CK(cudaMemcpy(s->d_lags, s->lags.data(), (size_t)s->L * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    if (Q > s->sp_Q) {
+        CK(cudaStreamSynchronize(s->st));
+        if (s->sp_E) cudaFree(s->sp_E);
+        if (s->sp_S) cudaFree(s->sp_S);
+        s->sp_E = s->sp_S = nullptr;
+        s->sp_Q = 0;
+        CK(cudaMalloc(&s->sp_E, (size_t)s->L * Q * sizeof(double2)));
+        CK(cudaMalloc(&s->sp_S, (size_t)s->F * s->A * Q * sizeof(double2)));
+        s->sp_Q = Q;
+    }
+    const double inv_n = 1.0 / (double)s->n_eff;
+    if (s->full)
+        CK(full_read(s->sums, s->Au, s->ncols, s->F, s->L, inv_n, s->d_out, s->st));
+    else
+        CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, inv_n, s->d_out, s->st));
+    double mmax = 0.0;
+    for (int32_t m : s->lags) mmax = std::max(mmax, (double)(m < 0 ? -m : m));
+    double2* dst = dev ? (double2*)out : s->sp_S;
+    CK(spectrum(s->d_out, s->d_lags, s->F * s->A, s->L, Q, taper, mmax, s->sp_E, dst, s->st));
+    s->kernel_launches += 3;
+    if (!dev)
+        CK(cudaMemcpyAsync(out, s->sp_S, (size_t)s->F * s->A * Q * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
     return sync_and_check(s);
 }
 

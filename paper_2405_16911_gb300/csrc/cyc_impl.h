@@ -94,6 +94,12 @@ bool        full_supported(int A);
 cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st);
 cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double inv_n, double2* out, cudaStream_t st);
 
+// Cyclic spectrum (spectrum.cu): S[rows][Q] = R[rows][L] x E[L][Q] in FP64, E[l][q] =
+// w(m_l) exp(-j 2 pi (-1/2 + q/Q) m_l) built into E ([L][Q]) on the device (taper 0: w = 1,
+// 1: Hann 0.5 + 0.5 cos(pi m / (mmax + 1))).  lags: device array [L].
+cudaError_t spectrum(const double2* R, const int32_t* lags, int rows, int L, int Q, int taper, double mmax,
+                     double2* E, double2* S, cudaStream_t st);
+
 // Persistent launch over a device list of work items (taken with an atomic counter that
 // the caller zeroes before the launch); `grid` CTAs, one per SM.  pair = true: `grid`
 // (even) CTAs in two-CTA clusters, each item covering rows u0 .. u0 + 255 (the odd CTA's
