@@ -43,7 +43,7 @@ TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
 # dram__bytes_read.sum + dram__bytes_write.sum per projection launch from one ncu capture,
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu file).
 TRAFFIC = {
-    "proj_tc@2418c9bb884b": 624640 + 76032,     # profiles/proj_tc_pair_bf16x3_cfg1_ncu.md
+    "proj_tc@dbc36542a6c2": 618752 + 86272,     # profiles/proj_tc_pair_bf16x3_cfg1_ncu.md
 }
 
 
@@ -53,7 +53,9 @@ def workload_config(precision):
                     "lags 0..127, 1024 cycle freqs -0.5+k/1024, CONV+CONJ, FP64 running sums" % ARGS_SAMPLES[0],
         "samples_per_step": ARGS_SAMPLES[0], "chunk": CHUNK, "lags": NLAGS, "cycle_freqs": NALPHAS,
         "forms": NFORMS, "projection": precision,
-        "l2": "inputs larger than L2 (512 MB stream per step, 129 MB L2)",
+        "l2": "inputs larger than L2 (%d MB stream per step, 129 MB L2)" % (ARGS_SAMPLES[0] * 8 >> 20)
+              if ARGS_SAMPLES[0] * 8 > (129 << 20) else
+              "stream of %d MB per step, smaller than L2 (a profiling size)" % (ARGS_SAMPLES[0] * 8 >> 20),
     }
 
 
@@ -437,12 +439,12 @@ def window_leg(pkg, x_dev, T=1 << 24, reps=2):
     """The block's windowed output (Eq. (impl-corr) at every window start k * hop, window-local
     phase) at the config-1 shape: windows of N = 65536 reference samples every 4096 samples,
     lags 0..127, 1024 cycle frequencies, both forms, BF16x3, 2^16-sample pushes, every window
-    read into device memory after each push; device time per push next to the running-sum
-    stream, and windows per second."""
+    read into device memory after every second push (the ring holds 32); wall time per push
+    next to the running-sum stream, and windows per second."""
     import torch
     C = CHUNK
     N, H = 1 << 16, 4096
-    cap = 2 * C // H
+    cap = 2 * (C // H)
     lags = np.arange(NLAGS)
     alphas = -0.5 + np.arange(NALPHAS) / NALPHAS
     out = torch.empty((cap, NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
@@ -456,9 +458,12 @@ def window_leg(pkg, x_dev, T=1 << 24, reps=2):
                 nwin[0] = 0
                 for c in range(T // C):
                     s.push(x_dev[2 * c * C:2 * (c + 1) * C])
-                    if window is not None:
+                    if window is not None and c % 2 == 1:       # the ring holds two pushes' windows
                         W, _ = s.read_windows(cap, out)
                         nwin[0] += W.shape[0]
+                if window is not None:
+                    W, _ = s.read_windows(cap, out)
+                    nwin[0] += W.shape[0]
                 s.sync()
             run()
             ms = []

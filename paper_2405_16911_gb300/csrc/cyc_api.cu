@@ -287,6 +287,7 @@ int project(cyc_stream* s, int64_t nc)
     a.x_avail = (s->M + s->max_chunk + kStagePad) & ~(int64_t)1;
     a.y = s->cross ? s->stage_y[s->cur] : nullptr;
     a.D = s->Mneg;
+    a.nforms = s->F;
     // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
     const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
     ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)

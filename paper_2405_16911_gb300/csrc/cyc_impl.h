@@ -36,6 +36,7 @@ struct ProjArgs {
     const float2*   y = nullptr;    // second input, same indexing as x; nullptr: y = x
     int             D = 0;          // offset M^- of the reference sample y[n + D]
     int64_t         split_off = 0;  // split s covers [s * split_len - split_off, + split_len) within [0, nc)
+    int             nforms = 0;     // columns per lag (c = l * nforms + f); 0 where unused
 };
 
 // One work item of the tensor-core projection: 128 cycle frequencies x 128 columns x an

@@ -18,37 +18,57 @@ namespace {
 
 constexpr int FOLD_T = 256;
 
-// Thread (r, c): F_c[r] += sum over pass terms i with (base + i) mod A == r of
-// x[i + col_lag[c]] c(y[i + D]).  Consecutive threads take consecutive residues, so the
-// sample reads of a warp are consecutive.
+// Thread (r, l): the columns of lag l (both forms when F = 2) gain the pass terms i with
+// (base + i) mod A == r.  One pair of sample reads x[i + m], y[i + D] serves both forms;
+// consecutive threads take consecutive residues, so a warp's reads are consecutive, and four
+// terms are loaded ahead.  FP32 runs of at most 64 terms, each added once to FP64.
 __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__ x, const float2* __restrict__ y,
                                                       int D, int64_t nc, int A, int base_mod,
                                                       const int32_t* __restrict__ col_lag,
-                                                      const int8_t* __restrict__ col_conj, int ncols,
+                                                      const int8_t* __restrict__ col_conj, int ncols, int nF,
                                                       double2* __restrict__ F)
 {
     const int r = blockIdx.x * FOLD_T + threadIdx.x;
-    const int c = blockIdx.y;
+    const int c0 = blockIdx.y * nF;
     if (r >= A) return;
-    const int m = col_lag[c];
-    const bool cj = col_conj[c] != 0;
+    const int m = col_lag[c0];
+    const bool cj0 = col_conj[c0] != 0;
     int64_t i = r - base_mod;
     if (i < 0) i += A;
-    double tr = 0.0, ti = 0.0;
-    // FP32 runs of at most 64 terms, each added once to the FP64 total
+    double vr = 0.0, vi = 0.0, jr = 0.0, ji = 0.0;          // CONV and CONJ totals
     while (i < nc) {
-        float sr = 0.f, si = 0.f;
-        for (int q = 0; q < 64 && i < nc; ++q, i += A) {
-            const float2 p = lag_product(__ldg(&x[i + m]), __ldg(&y[i + D]), cj);
-            sr += p.x;
-            si += p.y;
+        float sr = 0.f, si = 0.f, tr = 0.f, ti = 0.f;
+        int q = 0;
+        for (; q < 64 && i + 3 * (int64_t)A < nc; q += 4, i += 4 * (int64_t)A) {
+            float2 xm[4], y0[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                xm[k] = __ldg(&x[i + k * (int64_t)A + m]);
+                y0[k] = __ldg(&y[i + k * (int64_t)A + D]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float a = xm[k].x * y0[k].x, b = xm[k].y * y0[k].y;
+                const float c = xm[k].y * y0[k].x, d = xm[k].x * y0[k].y;
+                sr += a + b;  si += c - d;                   // x[n+m] conj(y[n])
+                tr += a - b;  ti += c + d;                   // x[n+m] y[n]
+            }
         }
-        tr += (double)sr;
-        ti += (double)si;
+        for (; q < 64 && i < nc; ++q, i += A) {
+            const float2 xm = __ldg(&x[i + m]), y0 = __ldg(&y[i + D]);
+            const float a = xm.x * y0.x, b = xm.y * y0.y, c = xm.y * y0.x, d = xm.x * y0.y;
+            sr += a + b;  si += c - d;
+            tr += a - b;  ti += c + d;
+        }
+        vr += (double)sr; vi += (double)si;
+        jr += (double)tr; ji += (double)ti;
     }
-    double2* f = F + (size_t)r * ncols + c;
-    const double2 o = *f;
-    *f = make_double2(o.x + tr, o.y + ti);
+    for (int f = 0; f < nF; ++f) {
+        const bool cj = f == 0 ? cj0 : col_conj[c0 + f] != 0;
+        double2* o = F + (size_t)r * ncols + c0 + f;
+        const double2 v = *o;
+        *o = cj ? make_double2(v.x + jr, v.y + ji) : make_double2(v.x + vr, v.y + vi);
+    }
 }
 
 // Block c: out[f][k][l] = (1/N) sum_r (-1)^r F_c[r] exp(-j 2 pi k r / A) for column
@@ -98,9 +118,11 @@ cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st)
 {
     if (a.nc <= 0) return cudaSuccess;
     const int base_mod = (int)(a.nbase & (uint64_t)(A - 1));
-    dim3 grid((A + FOLD_T - 1) / FOLD_T, a.ncols);
+    // columns c = l nF + f: both forms of a lag share one thread (nF = columns per lag)
+    const int nF = a.nforms > 0 ? a.nforms : 1;
+    dim3 grid((A + FOLD_T - 1) / FOLD_T, a.ncols / nF);
     fold_kernel<<<grid, FOLD_T, 0, st>>>(a.x, a.y ? a.y : a.x, a.D, a.nc, A, base_mod, a.col_lag, a.col_conj,
-                                         a.ncols, F);
+                                         a.ncols, nF, F);
     return cudaGetLastError();
 }
 
