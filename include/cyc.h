@@ -67,7 +67,9 @@ extern "C" {
 #define CYC_P_FP16   1       /* tensor cores, FP16 operands, one pass, FP32 accumulate */
 #define CYC_P_BF16X3 2       /* tensor cores, BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
 /* The tensor-core passes of cyc_push run on pairs of SMs (two-CTA clusters issuing
- * cta_group::2 MMAs) when the device can hold such clusters; the environment variable
+ * cta_group::2 MMAs, each pair taking two 128-row cycle-frequency tiles) when the device can
+ * hold such clusters and the distinct cycle frequencies fill an even number of tiles or at
+ * least five; the environment variable
  * CYC_TC_PAIR=0, read when a stream is created, selects the one-CTA kernel instead.  Both
  * compute the same products in the same order of terms per tile. */
 

@@ -290,7 +290,11 @@ int project(cyc_stream* s, int64_t nc)
     a.nforms = s->F;
     // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
     const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
-    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)
+    // CTA pairs take two 128-row tiles at a time: with 1 or 3 tiles the empty partner would
+    // idle a quarter to half of the SMs, so those run one CTA per tile
+    const int tx = (s->Au + tc_tile_rows() - 1) / tc_tile_rows();
+    const bool pair = s->pair_ctas > 0 && (tx % 2 == 0 || tx >= 5);
+    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, pair ? s->pair_ctas : 0)
                   : small                    ? small_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : fp32_plan(s->Au, s->ncols, nc, s->num_sms);
     if (s->win) {                     // one split per hop (the first and last may be partial)
@@ -314,7 +318,7 @@ int project(cyc_stream* s, int64_t nc)
         CK(cudaEventRecord(ev.first, s->st));
     }
     CK(s->full                    ? full_fold(a, s->Au, s->sums, s->st)
-       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->pair_ctas > 0, s->st)
+       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, pair, s->st)
        : small                    ? small_launch(a, s->st)
                                   : fp32_launch(a, s->st));
     if (s->prof) {

@@ -186,12 +186,14 @@ size_t fp32_max_partials(int Au, int ncols, int num_sms)
 
 cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st)
 {
-    static bool attr_set = false;
+    static bool attr_set[64] = {false};                   // the attribute is per device
     size_t smem = sizeof(Smem);
-    if (!attr_set) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(proj_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     dim3 grid((a.Au + TA - 1) / TA, (a.ncols + TC - 1) / TC, a.nsplit);
     proj_fp32_kernel<<<grid, NT, smem, st>>>(a);

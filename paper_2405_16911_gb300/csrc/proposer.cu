@@ -414,12 +414,14 @@ template <typename TI, typename TO>
 cudaError_t conv(const TI* x, int cin, int cout, const __half* w, const float* bias, int relu, const __half* mask,
                  TO* y, int B, cudaStream_t st)
 {
-    static bool set = false;
-    if (!set) {
+    static bool set[64] = {false};                        // the attribute is per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(conv_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)conv_smem(64));
         if (e != cudaSuccess) return e;
-        set = true;
+        if (dev >= 0 && dev < 64) set[dev] = true;
     }
     dim3 grid(NFFT / 128, (cout + 31) / 32, B);
     conv_kernel<TI, TO><<<grid, 256, conv_smem(cin), st>>>(x, cin, cout, w, bias, relu, mask, y);
@@ -575,11 +577,13 @@ int cyc_features(const void* x, int64_t T, int nsig, void* feats)
     if (!x || !feats || nsig <= 0) return pfail(CYC_EINVAL, "cyc_features: bad argument");
     if (T < (int64_t)NSEG * NFFT + MAXD)
         return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT + MAXD);
-    static bool set = false;
+    static bool set[64] = {false};                        // the attribute is per device
     const int smem = NFFT * 8 + NFFT / 2 * 8 + NFFT * 4;
-    if (!set) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !set[dev]) {
         PCK(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        set = true;
+        if (dev >= 0 && dev < 64) set[dev] = true;
     }
     features_kernel<<<nsig * NIN, 512, smem>>>((const float2*)x, T, (__half*)feats);
     PCK(cudaGetLastError());

@@ -52,6 +52,17 @@ def test_full_grid_two_inputs_signed_lags(cyc):
     assert np.max(np.abs(R - Ro)) / oracle.r00_xy(x, y, 8, 8) < 1e-5
 
 
+def test_full_grid_many_lags_wide_span(cyc):
+    """Several 16-lag groups per block row, unsorted lags spanning 2560 samples."""
+    T, A = 12000, 512
+    x = synth.white(T, seed=174).astype(np.complex64)
+    lags = np.concatenate([np.arange(0, 40), [2560, 1000, 7, 2047]])
+    R, neff = run_full(cyc, x, None, lags, A, [5000, 7000])
+    Ro, no = oracle.estimate(x, lags, grid(A))
+    assert neff == no
+    assert np.max(np.abs(R - Ro)) / oracle.r00(x, 2560) < 1e-5
+
+
 def test_full_grid_largest_A(cyc):
     T, A = 30011, 4096
     x = synth.white(T, seed=172).astype(np.complex64)

@@ -274,8 +274,12 @@ def test_fp32_small_and_general_paths(cyc, na):
 def test_pair_and_single_tensor_core_kernels(cyc, precision, monkeypatch):
     """cyc_push runs the tensor-core projection as two-CTA pairs by default and as single
     CTAs with CYC_TC_PAIR=0: both against the oracle on wide items with an odd number of
-    cycle-frequency tiles, narrow items, and two column tiles."""
-    cases = [(9001, np.arange(128), 300), (7003, np.arange(41), 130), (6007, np.arange(200), 129)]
+    cycle-frequency tiles, narrow items, two column tiles, and tile counts that run single
+    CTAs either way."""
+    # 5 tiles (pairs with one empty partner), 2 tiles narrow, 2 tiles over two column ranges,
+    # 1 and 3 tiles (one CTA per tile even when pairs are on)
+    cases = [(9001, np.arange(128), 600), (7003, np.arange(41), 130), (6007, np.arange(200), 129),
+             (5003, np.arange(64), 100), (4001, np.arange(100), 300)]
     for i, (T, lags, na) in enumerate(cases):
         x = synth.white(T, seed=120 + i).astype(np.complex64)
         alphas = np.random.default_rng(20 + i).uniform(-0.5, 0.5, na)
