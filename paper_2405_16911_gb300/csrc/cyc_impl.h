@@ -66,6 +66,36 @@ struct ProjPlan {
     int64_t split_len;
 };
 
+// Equal n-splits for `tiles` CTAs per split on `slots` co-resident CTAs: the one-wave count
+// slots / tiles, or more splits over several waves when the last wave's idle SMs cost more
+// (time ~ waves(s) / s at least 3 % smaller), at most smax.  Config 2's 64 tile-CTAs per
+// split on 152 SMs: 2 splits (84 % of the SMs busy) become 7 (three waves, 0.43 against 0.5).
+inline int wave_splits(int tiles, int slots, int smax)
+{
+    const int base = slots >= tiles ? slots / tiles : 1;
+    int best = base;
+    double cost = (double)(((int64_t)tiles * base + slots - 1) / slots) / base;
+    for (int s = base + 1; s <= smax; ++s) {
+        const double c = (double)(((int64_t)tiles * s + slots - 1) / slots) / s;
+        if (c < cost * 0.97) {
+            cost = c;
+            best = s;
+        }
+    }
+    return best;
+}
+
+// Splits a stream's partial buffer is sized for: the one-wave count, or up to 64 within
+// 256 MiB of FP32 partials.
+inline int max_splits(int tiles, int slots, int Au, int ncols)
+{
+    const int base = slots >= tiles ? slots / tiles : 1;
+    const int64_t per = (int64_t)Au * ncols * 8;
+    int64_t cap = per > 0 ? ((int64_t)256 << 20) / per : 64;
+    if (cap > 64) cap = 64;
+    return base > cap ? base : (int)cap;
+}
+
 // FP32 CUDA-core projection (proj_fp32.cu).
 ProjPlan    fp32_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st);

@@ -166,7 +166,9 @@ int tiles_of(int Au, int ncols) { return ((Au + TA - 1) / TA) * ((ncols + TC - 1
 ProjPlan fp32_plan(int Au, int ncols, int64_t nc, int num_sms)
 {
     int tiles = tiles_of(Au, ncols);
-    int want = num_sms >= tiles ? num_sms / tiles : 1;     // one wave of one CTA per SM
+    int smax = max_splits(tiles, num_sms, Au, ncols);
+    if ((int64_t)smax > nc / 2048) smax = (int)(nc / 2048);
+    const int want = wave_splits(tiles, num_sms, smax);     // one CTA per SM, whole waves
     int64_t len = (nc + want - 1) / want;
     if (len < 4 * TK) len = 4 * TK;
     len = (len + TK - 1) / TK * TK;
@@ -179,9 +181,7 @@ ProjPlan fp32_plan(int Au, int ncols, int64_t nc, int num_sms)
 
 size_t fp32_max_partials(int Au, int ncols, int num_sms)
 {
-    int tiles = tiles_of(Au, ncols);
-    size_t want = num_sms >= tiles ? (size_t)(num_sms / tiles) : 1;
-    return want * (size_t)Au * (size_t)ncols;
+    return (size_t)max_splits(tiles_of(Au, ncols), num_sms, Au, ncols) * (size_t)Au * (size_t)ncols;
 }
 
 cudaError_t fp32_launch(const ProjArgs& a, cudaStream_t st)

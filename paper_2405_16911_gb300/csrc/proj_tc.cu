@@ -717,12 +717,15 @@ ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
 {
     int tiles = tiles_of(Au, ncols);
     int slots = num_sms;
-    if (pair_ctas > 0) {            // x tiles rounded up to whole pairs, one wave of pairs
+    if (pair_ctas > 0) {            // x tiles rounded up to whole pairs
         const int tx = (Au + BM - 1) / BM;
         tiles = ((tx + 1) & ~1) * ((ncols + BN - 1) / BN);
         slots = pair_ctas < num_sms ? pair_ctas : num_sms;
     }
-    int want = slots >= tiles ? slots / tiles : 1;
+    // splits of at least 2048 samples, within what the partial buffer holds
+    int smax = max_splits(tiles_of(Au, ncols), num_sms, Au, ncols);
+    if ((int64_t)smax > nc / 2048) smax = (int)(nc / 2048);
+    const int want = wave_splits(tiles, slots, smax);
     int64_t len = (nc + want - 1) / want;
     if (len < 256) len = 256;
     len = (len + GS - 1) / GS * GS;
@@ -735,9 +738,7 @@ ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
 
 size_t tc_max_partials(int Au, int ncols, int num_sms)
 {
-    int tiles = tiles_of(Au, ncols);
-    size_t want = num_sms >= tiles ? (size_t)(num_sms / tiles) : 1;
-    return want * (size_t)Au * (size_t)ncols;
+    return (size_t)max_splits(tiles_of(Au, ncols), num_sms, Au, ncols) * (size_t)Au * (size_t)ncols;
 }
 
 cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t st)
