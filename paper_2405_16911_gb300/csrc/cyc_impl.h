@@ -68,7 +68,8 @@ struct ProjPlan {
 
 // Equal n-splits for `tiles` CTAs per split on `slots` co-resident CTAs: the one-wave count
 // slots / tiles, or more splits over several waves when the last wave's idle SMs cost more
-// (time ~ waves(s) / s at least 3 % smaller), at most smax.  Config 2's 64 tile-CTAs per
+// (time ~ waves(s) / s at least 10 % smaller: per-CTA fixed costs eat smaller gains), at
+// most smax.  Config 2's 64 tile-CTAs per
 // split on 152 SMs: 2 splits (84 % of the SMs busy) become 7 (three waves, 0.43 against 0.5).
 inline int wave_splits(int tiles, int slots, int smax)
 {
@@ -77,7 +78,7 @@ inline int wave_splits(int tiles, int slots, int smax)
     double cost = (double)(((int64_t)tiles * base + slots - 1) / slots) / base;
     for (int s = base + 1; s <= smax; ++s) {
         const double c = (double)(((int64_t)tiles * s + slots - 1) / slots) / s;
-        if (c < cost * 0.97) {
+        if (c < cost * 0.90) {
             cost = c;
             best = s;
         }
