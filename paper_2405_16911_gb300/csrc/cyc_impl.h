@@ -58,6 +58,17 @@ struct TcItem {
     const float2*   y;          // second input (linear views only) or nullptr: y = x
     int             D;          // offset of the reference sample y[n + D]
     int64_t         out_peer;   // pair lists: the odd CTA's rows u0 + 128 .. go to out + out_peer
+    // Dual items (pair lists): a second stream with the same cycle frequencies, lags and
+    // forms over a range of the same length.  The even CTA stages and forms the columns of
+    // the first stream, the odd CTA those of the second; the weights follow the first
+    // stream's sample index, so the second stream's sums are rotated by
+    // exp(-j 2 pi a dphase / 2^64) before they are written to out2.
+    const float2*   x2;         // nullptr: not a dual item
+    uint64_t        xmask2;
+    int64_t         n_beg2;
+    float2*         out2;
+    int64_t         out_peer2;  // the odd CTA's rows of the second stream go to out2 + out_peer2
+    uint64_t        dphase;     // (nbase2 + n_beg2) - (nbase + n_beg) mod 2^64
 };
 
 // Launch geometry chosen by a kernel family for one pass.

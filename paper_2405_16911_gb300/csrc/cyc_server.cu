@@ -117,6 +117,7 @@ struct SrvStream {
     int F = 0, L = 0, A = 0, Au = 0, ncols = 0;
     int32_t M = 0;
     int64_t n0 = 0;
+    uint64_t cfg = 0;                 // hash of the cycle frequencies, lags and forms
     float2* ring = nullptr;
     uint64_t cap = 0;
     double2* sums = nullptr;
@@ -218,66 +219,167 @@ int cyc_server::form_and_launch()
     std::vector<std::pair<int, int64_t>> marks;
     const int nstreams = (int)streams.size();
     const int BMr = tc_tile_rows(), BNc = tc_tile_cols();
-    for (int k = 0; k < nstreams; ++k) {
-        const int sid = (rr + k) % nstreams;
-        SrvStream& s = *streams[sid];
-        if (!s.open.load(std::memory_order_acquire) || s.closing.load()) continue;
-        const int64_t upto = s.T.load() - s.M;
-        const int64_t n_sched = s.n_sched.load();
-        if (upto <= n_sched) continue;
-        const int ta = (s.Au + BMr - 1) / BMr, tcn = (s.ncols + BNc - 1) / BNc;
-        // pairs: one item covers tiles 2k and 2k + 1 (the second may not exist)
-        const int tstep = pair ? 2 : 1;
-        const int titems = (ta + tstep - 1) / tstep;
-        int64_t span = upto - n_sched;
-        int pieces = (int)((span + p.item_samples - 1) / p.item_samples);
-        // what still fits into this batch
-        int room_items = (p.max_items - ni) / (titems * tcn);
-        int64_t room_slots = (nslot_cap - ns) / (titems * tstep * tcn);
-        int room_folds = (2 * p.max_items - nf) / (ta * tcn);
-        int fit = (int)std::min<int64_t>(pieces, std::min<int64_t>(room_items, room_slots));
-        if (room_folds <= 0) fit = 0;
-        if (fit <= 0) break;
-        if (fit < pieces) span = (int64_t)fit * p.item_samples;
-        const int64_t nb = n_sched, ne = n_sched + span;
-        for (int ip = 0; ip < titems; ++ip)
-            for (int ic = 0; ic < tcn; ++ic) {
-                for (int k = 0; k < tstep && ip * tstep + k < ta; ++k) {
+    const int64_t IS = p.item_samples;
+    const int64_t TILE = (int64_t)BMr * BNc;
+    // pairs: one item covers tiles 2k and 2k + 1 (the second may not exist)
+    const int tstep = pair ? 2 : 1;
+
+    struct Geo {
+        int ta, tcn, titems;
+    };
+    auto geometry = [&](const SrvStream& s) {
+        Geo g;
+        g.ta = (s.Au + BMr - 1) / BMr;
+        g.tcn = (s.ncols + BNc - 1) / BNc;
+        g.titems = (g.ta + tstep - 1) / tstep;
+        return g;
+    };
+    // folds and partial slots for np pieces of stream s, laid out tile-major:
+    //   slot(ip, ic, k, pc) = base + ((ip tcn + ic) tstep + k) np + pc
+    auto reserve = [&](SrvStream& s, int np) {
+        const Geo g = geometry(s);
+        const int64_t base = ns;
+        for (int ip = 0; ip < g.titems; ++ip)
+            for (int ic = 0; ic < g.tcn; ++ic)
+                for (int k = 0; k < tstep && ip * tstep + k < g.ta; ++k) {
                     Fold& f = folds[nf++];
                     f.sums = s.sums;
                     f.u0 = (ip * tstep + k) * BMr;
                     f.Au = s.Au;
                     f.c0 = ic * BNc;
                     f.ncols = s.ncols;
-                    f.slot0 = ns + (int64_t)k * fit;
-                    f.nslots = fit;
+                    f.slot0 = base + ((int64_t)(ip * g.tcn + ic) * tstep + k) * np;
+                    f.nslots = np;
                 }
-                for (int pc = 0; pc < fit; ++pc) {
-                    TcItem& it = items[ni++];
-                    it.x = s.ring;
-                    it.xmask = s.cap - 1;
-                    it.x_avail = INT64_MAX;
-                    it.nbase = (uint64_t)s.n0;
-                    it.n_beg = nb + (int64_t)pc * p.item_samples;
-                    it.n_end = std::min(ne, it.n_beg + p.item_samples);
-                    it.phi = s.d_phi;
-                    it.col_lag = s.d_col_lag;
-                    it.col_conj = s.d_col_conj;
-                    it.out = slots + (ns + pc) * (int64_t)BMr * BNc;
-                    it.out_stride = BNc;
-                    it.u0 = ip * tstep * BMr;
-                    it.Au = s.Au;
-                    it.c0 = ic * BNc;
-                    it.ncols = s.ncols;
-                    it.M = s.M;
-                    it.y = nullptr;
-                    it.D = 0;
-                    it.out_peer = (int64_t)fit * BMr * BNc;     // the second tile's slots follow
+        ns += (int64_t)g.titems * g.tcn * tstep * np;
+        return base;
+    };
+    auto slot_of = [&](int64_t base, const Geo& g, int np, int ip, int ic, int pc) {
+        return base + (int64_t)(ip * g.tcn + ic) * tstep * np + pc;
+    };
+    auto make_item = [&](SrvStream& s, int ip, int ic, int64_t nb, int64_t len, int64_t slot, int np) -> TcItem& {
+        TcItem& it = items[ni++];
+        it.x = s.ring;
+        it.xmask = s.cap - 1;
+        it.x_avail = INT64_MAX;
+        it.nbase = (uint64_t)s.n0;
+        it.n_beg = nb;
+        it.n_end = nb + len;
+        it.phi = s.d_phi;
+        it.col_lag = s.d_col_lag;
+        it.col_conj = s.d_col_conj;
+        it.out = slots + slot * TILE;
+        it.out_stride = BNc;
+        it.u0 = ip * tstep * BMr;
+        it.Au = s.Au;
+        it.c0 = ic * BNc;
+        it.ncols = s.ncols;
+        it.M = s.M;
+        it.y = nullptr;
+        it.D = 0;
+        it.out_peer = (int64_t)np * TILE;          // the second tile's slots follow
+        it.x2 = nullptr;
+        it.xmask2 = 0;
+        it.n_beg2 = 0;
+        it.out2 = nullptr;
+        it.out_peer2 = 0;
+        it.dphase = 0;
+        return it;
+    };
+    // one stream: as many of its pieces as the batch has room for (false: no room at all)
+    auto single = [&](int sid) -> bool {
+        SrvStream& s = *streams[sid];
+        const int64_t upto = s.T.load() - s.M, n_sched = s.n_sched.load();
+        if (upto <= n_sched) return true;
+        const Geo g = geometry(s);
+        int64_t span = upto - n_sched;
+        const int pieces = (int)((span + IS - 1) / IS);
+        const int room_items = (p.max_items - ni) / (g.titems * g.tcn);
+        const int64_t room_slots = (nslot_cap - ns) / (g.titems * tstep * g.tcn);
+        const int room_folds = (2 * p.max_items - nf) / (g.ta * g.tcn);
+        int fit = (int)std::min<int64_t>(pieces, std::min<int64_t>(room_items, room_slots));
+        if (room_folds <= 0) fit = 0;
+        if (fit <= 0) return false;
+        if (fit < pieces) span = (int64_t)fit * IS;
+        const int64_t base = reserve(s, fit);
+        for (int ip = 0; ip < g.titems; ++ip)
+            for (int ic = 0; ic < g.tcn; ++ic)
+                for (int pc = 0; pc < fit; ++pc)
+                    make_item(s, ip, ic, n_sched + pc * IS, std::min<int64_t>(IS, span - pc * IS),
+                              slot_of(base, g, fit, ip, ic, pc), fit);
+        s.n_sched.store(n_sched + span);
+        marks.emplace_back(sid, n_sched + span);
+        return true;
+    };
+    // two streams with the same cycle frequencies, lags and forms (at most 128 columns):
+    // dual items over their common span -- one CTA pair forms both streams' columns with one
+    // set of weights -- and the rest of the longer stream alone
+    auto dual = [&](int sa, int sb) -> bool {
+        SrvStream& A = *streams[sa];
+        SrvStream& B = *streams[sb];
+        const int64_t ua = A.T.load() - A.M, na = A.n_sched.load();
+        const int64_t ub = B.T.load() - B.M, nbb = B.n_sched.load();
+        const int64_t spa = ua - na, spb = ub - nbb, C = std::min(spa, spb);
+        const Geo g = geometry(A);
+        const int P = (int)((C + IS - 1) / IS);
+        const int ra = (int)((spa - C + IS - 1) / IS), rb = (int)((spb - C + IS - 1) / IS);
+        const int npa = P + ra, npb = P + rb;
+        const int need_items = g.titems * g.tcn * (P + ra + rb);
+        const int64_t need_slots = (int64_t)g.titems * g.tcn * tstep * (npa + npb);
+        if (C <= 0 || ni + need_items > p.max_items || ns + need_slots > nslot_cap ||
+            nf + 2 * g.ta * g.tcn > 2 * p.max_items)
+            return single(sa) && single(sb);
+        const int64_t basea = reserve(A, npa), baseb = reserve(B, npb);
+        const uint64_t dph = ((uint64_t)B.n0 + (uint64_t)nbb) - ((uint64_t)A.n0 + (uint64_t)na);
+        for (int ip = 0; ip < g.titems; ++ip)
+            for (int ic = 0; ic < g.tcn; ++ic) {
+                for (int pc = 0; pc < P; ++pc) {
+                    TcItem& it = make_item(A, ip, ic, na + pc * IS, std::min<int64_t>(IS, C - pc * IS),
+                                           slot_of(basea, g, npa, ip, ic, pc), npa);
+                    it.x2 = B.ring;
+                    it.xmask2 = B.cap - 1;
+                    it.n_beg2 = nbb + pc * IS;
+                    it.out2 = slots + slot_of(baseb, g, npb, ip, ic, pc) * TILE;
+                    it.out_peer2 = (int64_t)npb * TILE;
+                    it.dphase = dph;
                 }
-                ns += (int64_t)tstep * fit;
+                for (int pc = 0; pc < ra; ++pc)
+                    make_item(A, ip, ic, na + C + pc * IS, std::min<int64_t>(IS, spa - C - pc * IS),
+                              slot_of(basea, g, npa, ip, ic, P + pc), npa);
+                for (int pc = 0; pc < rb; ++pc)
+                    make_item(B, ip, ic, nbb + C + pc * IS, std::min<int64_t>(IS, spb - C - pc * IS),
+                              slot_of(baseb, g, npb, ip, ic, P + pc), npb);
             }
-        s.n_sched.store(ne);
-        marks.emplace_back(sid, ne);
+        A.n_sched.store(ua);
+        B.n_sched.store(ub);
+        marks.emplace_back(sa, ua);
+        marks.emplace_back(sb, ub);
+        return true;
+    };
+
+    std::map<uint64_t, int> waiting;                  // a stream waiting for a dual partner, per key
+    bool full = false;
+    for (int k = 0; k < nstreams && !full; ++k) {
+        const int sid = (rr + k) % nstreams;
+        SrvStream& s = *streams[sid];
+        if (!s.open.load(std::memory_order_acquire) || s.closing.load()) continue;
+        if (s.T.load() - s.M <= s.n_sched.load()) continue;
+        if (pair && s.ncols <= BNc / 2) {
+            auto w = waiting.find(s.cfg);
+            if (w == waiting.end()) {
+                waiting.emplace(s.cfg, sid);
+                continue;
+            }
+            const int other = w->second;
+            waiting.erase(w);
+            full = !dual(other, sid);
+        } else {
+            full = !single(sid);
+        }
+    }
+    for (auto& w : waiting) {
+        if (full) break;
+        full = !single(w.second);
     }
     rr = (rr + 1) % (nstreams > 0 ? nstreams : 1);
     if (ni == 0) return 0;
@@ -571,6 +673,19 @@ int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const doubl
     SrvStream& s = *srv->streams[slot];
     s.F = F; s.L = nlags; s.A = nalphas; s.Au = Au; s.ncols = ncols; s.M = M; s.n0 = n0;
     s.cap = cap;
+    {
+        // streams with equal keys share their weights in dual items (FNV-1a over the tables)
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](const void* p, size_t n) {
+            const unsigned char* c = (const unsigned char*)p;
+            for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+        };
+        mix(phi_u.data(), phi_u.size() * sizeof(uint64_t));
+        mix(cl.data(), cl.size() * sizeof(int32_t));
+        mix(cc.data(), cc.size());
+        mix(&M, sizeof M);
+        s.cfg = h;
+    }
     auto fail_free = [&](cudaError_t e, const char* what) {
         s.release();
         return sfail(e == cudaErrorMemoryAllocation ? CYC_EAGAIN : CYC_ECUDA, "cyc_server_open: %s: %s", what,

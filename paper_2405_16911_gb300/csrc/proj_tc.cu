@@ -193,6 +193,35 @@ __device__ __forceinline__ void drain_tile(uint32_t tmem, int q, int lane, const
     float2* out = it.out + (size_t)row * it.out_stride;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     const bool mine = it.u0 + row < it.Au;
+    if (it.x2 != nullptr) {
+        // dual item: D columns [0, 128) are the first stream's tile columns, [128, 256) the
+        // second stream's, rotated onto its own sample index
+        const float2 rot = mine ? phase_rot(it.phi[it.u0 + row], it.dphase) : make_float2(1.f, 0.f);
+        float2* out2 = it.out2 + (size_t)row * it.out_stride;
+        for (int cb = 0; cb < 16; ++cb) {
+            uint32_t dr0[8], di0[8], dr1[8], di1[8];
+            tc::tmem_ld8(lane_addr + TM_DR + cb * 8, dr0);
+            tc::tmem_ld8(lane_addr + TM_DI + cb * 8, di0);
+            tc::tmem_ld8(lane_addr + TM_DR + 128 + cb * 8, dr1);
+            tc::tmem_ld8(lane_addr + TM_DI + 128 + cb * 8, di1);
+            tc::tmem_ld_wait();
+            if (!mine) continue;
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
+                                              __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                put2(out, cb * 8 + j, v, vec, cmax, add);
+                const float ar = __uint_as_float(dr1[j]), ai = __uint_as_float(di1[j]);
+                const float br = __uint_as_float(dr1[j + 1]), bi = __uint_as_float(di1[j + 1]);
+                v = live ? make_float4(ar * rot.x - ai * rot.y, ar * rot.y + ai * rot.x,
+                                       br * rot.x - bi * rot.y, br * rot.y + bi * rot.x)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                put2(out2, cb * 8 + j, v, vec, cmax, add);
+            }
+        }
+        return;
+    }
     for (int cb = 0; cb < 16; ++cb) {
         uint32_t dr0[8], di0[8], dr1[8], di1[8];
         tc::tmem_ld8(lane_addr + TM_DR + cb * 8, dr0);
@@ -253,6 +282,12 @@ __device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, i
     it.y = a.y;
     it.D = a.D;
     it.out_peer = 0;
+    it.x2 = nullptr;
+    it.xmask2 = 0;
+    it.n_beg2 = 0;
+    it.out2 = nullptr;
+    it.out_peer2 = 0;
+    it.dphase = 0;
     return it;
 }
 
@@ -326,6 +361,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             if (cmd == -2) {
                 // the next sub-item of the current item: a fresh TMEM chain that adds
                 idx = bars->item;
+                bars->it.n_beg2 += bars->it.n_end - bars->it.n_beg;     // dual items advance in step
                 bars->it.n_beg = bars->it.n_end;
                 bars->add = 1;
             } else if (cmd >= 0) {
@@ -336,6 +372,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     if (PAIR && crank == 1) {                  // the odd CTA's 128 rows
                         bars->it.u0 += BM;
                         bars->it.out += bars->it.out_peer;
+                        if (bars->it.out2) bars->it.out2 += bars->it.out_peer2;
                     }
                 } else {
                     bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
@@ -366,8 +403,14 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         const int D = it.D;
         const int yoff = (int)((n_beg + D) & 1);
         const int nblocks = (ngroups * GS + XB - 1) / XB;
-        const int xoff = (int)(n_beg & 1);    // bulk copies start at an even sample (16-byte aligned)
-        const bool narrow = it.ncols - it.c0 <= BN / 2;     // N = 128 MMAs, one column per P thread
+        // dual items: each CTA of the pair stages and forms the columns of its own stream
+        const bool dual = PAIR && LIST && it.x2 != nullptr;
+        const bool second = dual && crank == 1;
+        const float2* xsrc = second ? it.x2 : it.x;
+        const uint64_t xmsk = second ? it.xmask2 : it.xmask;
+        const int64_t nsrc = second ? it.n_beg2 : n_beg;    // this CTA's first sample of the range
+        const int xoff = (int)(nsrc & 1);     // bulk copies start at an even sample (16-byte aligned)
+        const bool narrow = !dual && it.ncols - it.c0 <= BN / 2;   // N = 128 MMAs, one column per P thread
 
         if (warp < MMA_WARP && role < P_WARPS) {
             // -------------------------------------------------------- P warps (lag products)
@@ -376,7 +419,9 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             // wide items: columns 2t, 2t+1 -> B rows t, t+128; narrow items: column t -> row t.
             // CTA pairs hold B rows [N/2 rank, N/2 (rank + 1)): wide, thread t forms column
             // 2t + rank (its B row t); narrow, threads t < 64 form column 64 rank + t.
-            const int jA = PAIR ? (narrow ? (t < 64 ? 64 * (int)crank + t : ncols) : 2 * t + (int)crank)
+            // dual items: thread t forms column t of this CTA's stream (its B row t)
+            const int jA = dual ? t
+                         : PAIR ? (narrow ? (t < 64 ? 64 * (int)crank + t : ncols) : 2 * t + (int)crank)
                                 : (narrow ? t : 2 * t);
             const int jB = 2 * t + 1;
             const bool okA = c0 + jA < ncols, okB = !PAIR && !narrow && c0 + jB < ncols;
@@ -510,7 +555,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     give_up(err, bars, 5);
                     break;
                 }
-                const int64_t ns = n_beg + (int64_t)b * XB - xoff;   // even
+                const int64_t ns = nsrc + (int64_t)b * XB - xoff;    // even
                 int64_t cnt = ((int64_t)XB + mpad + xoff + 1) & ~(int64_t)1;
                 if (cnt > it.x_avail - ns) cnt = it.x_avail - ns;
                 int64_t ys = 0, ycnt = 0;
@@ -521,13 +566,13 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                 }
                 tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)((cnt + ycnt) * 8));
                 if (cross) tc::bulk_g2s(xs + slot * XSLOT + YOFF, it.y + ys, (uint32_t)(ycnt * 8), &bars->xfull[slot]);
-                const uint64_t pos = (uint64_t)ns & it.xmask;
-                const uint64_t room = it.xmask - pos + 1;       // samples before the ring wraps
-                if (it.xmask == ~0ull || (uint64_t)cnt <= room) {
-                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(cnt * 8), &bars->xfull[slot]);
+                const uint64_t pos = (uint64_t)ns & xmsk;
+                const uint64_t room = xmsk - pos + 1;           // samples before the ring wraps
+                if (xmsk == ~0ull || (uint64_t)cnt <= room) {
+                    tc::bulk_g2s(xs + slot * XSLOT, xsrc + pos, (uint32_t)(cnt * 8), &bars->xfull[slot]);
                 } else {
-                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(room * 8), &bars->xfull[slot]);
-                    tc::bulk_g2s(xs + slot * XSLOT + room, it.x, (uint32_t)((cnt - room) * 8), &bars->xfull[slot]);
+                    tc::bulk_g2s(xs + slot * XSLOT, xsrc + pos, (uint32_t)(room * 8), &bars->xfull[slot]);
+                    tc::bulk_g2s(xs + slot * XSLOT + room, xsrc, (uint32_t)((cnt - room) * 8), &bars->xfull[slot]);
                 }
                 lastb = (int)bg;
             }

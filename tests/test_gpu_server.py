@@ -133,3 +133,41 @@ def test_ring_backpressure_and_concurrent_submitters(cyc):
             srv.submit(sids[0], np.zeros(ring, np.complex64))
         assert e.value.code == cyc.CYC_EINVAL
     assert sum(eagain) > 0          # the small ring really pushed back
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("fp16", 1e-2)])
+def test_streams_sharing_a_configuration(cyc, precision, tol):
+    """Nine streams with the same cycle frequencies, lags and forms (64 lags x 2 forms: dual
+    items on CTA pairs, one CTA pair forming two streams' columns with one set of weights,
+    the second stream rotated onto its own sample index) and different start indices and
+    chunkings: each stream's result equals the same stream run alone, and the oracle's."""
+    lags = np.arange(64)
+    alphas = -0.5 + np.arange(300) / 300.0
+    rng = np.random.default_rng(77)
+    cases = []
+    for i in range(9):
+        T = int(rng.integers(20000, 90000))
+        x = synth.white(T, seed=3000 + i).astype(np.complex64)
+        cuts = np.sort(rng.choice(np.arange(1, T), size=int(rng.integers(1, 8)), replace=False))
+        n0 = int(rng.integers(0, 1 << 40)) if i % 2 else 0
+        cases.append(dict(x=x, chunks=np.diff(np.concatenate([[0], cuts, [T]])), n0=n0))
+    with cyc.Server(max_streams=16, precision=precision, item_samples=8192) as srv:
+        sids = [srv.open(lags, alphas, 3, c["n0"]) for c in cases]
+        pos, k = [0] * 9, [0] * 9
+        while any(k[i] < len(c["chunks"]) for i, c in enumerate(cases)):
+            for i, c in enumerate(cases):
+                if k[i] < len(c["chunks"]):
+                    n = int(c["chunks"][k[i]])
+                    srv.submit(sids[i], c["x"][pos[i]:pos[i] + n])
+                    pos[i] += n
+                    k[i] += 1
+        srv.drain(120)
+        for i, c in enumerate(cases):
+            R, n = srv.read(sids[i])
+            Ra, na = alone(cyc, c["x"], lags, alphas, 3, c["n0"], precision)
+            assert n == na
+            r00 = oracle.r00(c["x"], 63)
+            assert np.max(np.abs(R - Ra)) / r00 < tol / 5, i
+            if i < 2:
+                Ro, _ = oracle.estimate(c["x"], lags, alphas, 3, n0=c["n0"])
+                assert np.max(np.abs(R - Ro)) / r00 < tol, i
