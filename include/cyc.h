@@ -289,7 +289,10 @@ CYC_API int cyc_server_create(const cyc_server_params* p, cyc_server** out);
 CYC_API int cyc_server_destroy(cyc_server* srv);
 
 /* Open a stream (lags >= 0, max lag <= 2560; arrays copied).  CYC_EAGAIN when no slot is
- * free or its device memory would exceed the budget: retry after a close. */
+ * free or its device memory would exceed the budget: retry after a close.  Streams opened
+ * with the same lags, cycle frequencies and forms, at most 128 columns (lags x forms), may
+ * share work items: two such streams' equal spans of new samples run on one pair of SMs
+ * with one set of weights (the results are each stream's own). */
 CYC_API int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const double* alphas,
                             int nalphas, int conj_flag, int64_t n0, int* sid);
 
