@@ -134,8 +134,9 @@ CYC_API int cyc_create_xy(const cyc_params* p, cyc_stream** out);
  * for fails with CYC_EAGAIN before doing anything (read windows, then push again).
  *   win_len   positive multiple of hop, win_len / hop <= 65536
  *   hop       >= 16 samples between window starts
- *   capacity  1 .. 2^20 windows of F * nalphas * nlags * 16 bytes each (plus device state of
- *             (win_len / hop + capacity + 2) * (distinct a) * F * nlags * 16 bytes)
+ *   capacity  1 .. 2^20 windows of F * (distinct a) * nlags * 8 bytes each (held in FP32
+ *             until read; plus device state of (win_len / hop) * (distinct a) * F * nlags
+ *             * 8 bytes for the hop sums and 2 * (distinct a) * F * nlags * 16 bytes)
  *   cross     0: one input (cyc_push); 1: two inputs (cyc_push_xy), as cyc_create_xy
  * cyc_save / cyc_load return CYC_ENOTSUP for windowed streams.
  */

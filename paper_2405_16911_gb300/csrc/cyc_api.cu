@@ -60,7 +60,7 @@ constexpr int64_t kMaxChunk = 1ll << 28;
 constexpr int32_t kMaxLag = 1 << 20;
 constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
 constexpr int kWinSplits = 64;      // hop-aligned partials per pass of a windowed stream
-constexpr uint32_t kBlobVersion = 1;
+constexpr uint32_t kBlobVersion = 2;       // 2: Full-mode folds stored [columns][residues]
 
 // a (cycles/sample) -> round(a * 2^64) mod 2^64, exactly.  a = m * 2^e with m the 53-bit
 // integer significand, so a * 2^64 = m * 2^(e+64): a left shift (bits beyond 2^64 are
@@ -124,10 +124,10 @@ struct cyc_stream {
     int win_w = 0;                  // hops per window
     int64_t hops = 0;               // hops completed
     int64_t win_made = 0, win_read = 0;
-    double2* w_ring = nullptr;      // [win_w][Au][ncols] the last win_w completed hops
-    double2* w_sum = nullptr;       // [Au][ncols] sum of those
-    double2* w_pend = nullptr;      // [Au][ncols] the hop in progress
-    double2* w_out = nullptr;       // [win_cap][Au][ncols] raw sums of completed, unread windows
+    float2* w_ring = nullptr;       // [win_w][Au][ncols] the last win_w completed hops (FP32)
+    float4* w_sum = nullptr;        // [Au][ncols] sum of those (float-float: re hi, re lo, im hi, im lo)
+    float4* w_pend = nullptr;       // [Au][ncols] the hop in progress (float-float)
+    float2* w_out = nullptr;        // [win_cap][Au][ncols] raw sums of completed, unread windows (FP32)
     // cyclic spectra (cyc_read_spectrum), allocated on first use
     int32_t* d_lags = nullptr;      // the signed lags [L]
     double2* sp_E = nullptr;        // DFT matrix [L][sp_Q]
@@ -180,7 +180,8 @@ struct cyc_stream {
         stage[0] = stage[1] = stage_y[0] = stage_y[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
-        w_ring = w_sum = w_pend = w_out = nullptr;
+        w_ring = w_out = nullptr;
+        w_sum = w_pend = nullptr;
         d_lags = nullptr;
         sp_E = sp_S = nullptr;
         sp_Q = 0;
@@ -254,12 +255,12 @@ int alloc_state(cyc_stream* s)
     CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
     if (s->win) {
         const size_t nuc = (size_t)s->Au * s->ncols;
-        CK(cudaMalloc(&s->w_ring, (size_t)s->win_w * nuc * sizeof(double2)));
-        CK(cudaMalloc(&s->w_sum, nuc * sizeof(double2)));
-        CK(cudaMalloc(&s->w_pend, nuc * sizeof(double2)));
-        CK(cudaMalloc(&s->w_out, (size_t)s->win_cap * nuc * sizeof(double2)));
-        CK(cudaMemset(s->w_sum, 0, nuc * sizeof(double2)));
-        CK(cudaMemset(s->w_pend, 0, nuc * sizeof(double2)));
+        CK(cudaMalloc(&s->w_ring, (size_t)s->win_w * nuc * sizeof(float2)));
+        CK(cudaMalloc(&s->w_sum, nuc * sizeof(float4)));
+        CK(cudaMalloc(&s->w_pend, nuc * sizeof(float4)));
+        CK(cudaMalloc(&s->w_out, (size_t)s->win_cap * nuc * sizeof(float2)));
+        CK(cudaMemset(s->w_sum, 0, nuc * sizeof(float4)));
+        CK(cudaMemset(s->w_pend, 0, nuc * sizeof(float4)));
     }
     CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
     CK(cudaMalloc(&s->d_err, sizeof(int)));
@@ -714,8 +715,8 @@ int cyc_reset(cyc_stream* s)
     DeviceGuard g(s->device);
     CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
     if (s->win) {
-        CK(cudaMemsetAsync(s->w_sum, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
-        CK(cudaMemsetAsync(s->w_pend, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+        CK(cudaMemsetAsync(s->w_sum, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));
+        CK(cudaMemsetAsync(s->w_pend, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));
         s->hops = s->win_made = s->win_read = 0;
     }
     s->T = s->n_eff = s->held = 0;

@@ -28,4 +28,21 @@ __device__ __forceinline__ float2 lag_product(float2 xm, float2 x0, bool conj)
     return make_float2(xm.x * x0.x - xm.y * yi, xm.x * yi + xm.y * x0.x);
 }
 
+// Float-float accumulator: a value held as hi + lo, two FP32 numbers (about 48 significant
+// bits).  This GPU's FP64 rate is a small fraction of its FP32 rate, so sums updated per
+// element and per step are kept as FP32 pairs and updated with error-free transformations
+// (Knuth's TwoSum: s + e == a + b exactly for s = fl(a + b)); FP64 is used only where a
+// value leaves in FP64.  (hi, lo) += v with a relative error of about 2^-46.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v)
+{
+    const float s = hi + v;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (v - bv);
+    const float t = lo + e;
+    const float s2 = s + t;
+    const float bt = s2 - s;
+    lo = (s - (s2 - bt)) + (t - bt);
+    hi = s2;
+}
+
 }  // namespace cyc

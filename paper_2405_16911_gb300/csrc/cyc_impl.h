@@ -167,18 +167,18 @@ struct HopArgs {
     int64_t       off, nc, hop;
     int           w;                // hops per window
     int64_t       hops0;            // hops completed before this pass
-    double2*      ring;             // [w][n_uc]
-    double2*      wsum;             // [n_uc]
-    double2*      pend;             // [n_uc]
+    float2*       ring;             // [w][n_uc] hop sums (FP32)
+    float4*       wsum;             // [n_uc] window sum, float-float (re hi, re lo, im hi, im lo)
+    float4*       pend;             // [n_uc] hop in progress, float-float
     double2*      sums;             // [n_uc]
-    double2*      wout;             // [cap][n_uc]
+    float2*       wout;             // [cap][n_uc] completed window sums (FP32)
     int64_t       cap;
 };
 cudaError_t fold_hops(const HopArgs& h, cudaStream_t st);
 // Windows k0 .. k0 + n - 1 of a windowed stream into out[i][f][a][l]: wout[k % cap][amap[a]]
 // [l F + f] times exp(+j 2 pi phi_a (base + k hop) / 2^64) / N (the window-local phase of
 // Eq. (impl-corr)).
-cudaError_t read_windows(const double2* wout, int64_t cap, int64_t k0, int64_t n, const int32_t* amap,
+cudaError_t read_windows(const float2* wout, int64_t cap, int64_t k0, int64_t n, const int32_t* amap,
                          const uint64_t* phi, int F, int A, int L, int Au, int ncols, uint64_t base, int64_t hop,
                          double inv_n, double2* out, cudaStream_t st);
 // out[f][a][l] = sums[amap[a]][l * F + f] / n_eff

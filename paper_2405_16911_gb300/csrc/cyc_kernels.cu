@@ -1,4 +1,5 @@
 // cyc_kernels.cu -- FP64 running-sum update and normalised read-out of libcyc.
+#include "cyc_device.cuh"
 #include "cyc_impl.h"
 
 namespace cyc {
@@ -66,68 +67,127 @@ __global__ void read_sums_kernel(const double2* __restrict__ sums, const int32_t
     out[e] = make_double2(v.x * inv_n, v.y * inv_n);
 }
 
-// One thread per (u, c) element: the pass's splits in order.  FP64 throughout (the hop
-// sums and the window sums are differences of large running quantities).
-__global__ void fold_hops_kernel(HopArgs h)
+// One thread per (u, c) element: the pass's splits in order.  A hop's sum (its FP32 split
+// partials, added in float-float) is rounded to FP32 once and that value is both kept in the
+// ring and added to the float-float window sum, so dropping it later subtracts exactly what
+// was added; a completed window's sum is stored rounded to FP32 until it is read (the
+// partials carry FP32 rounding already).  No FP64 arithmetic per split: this GPU's FP64
+// rate made an FP64 version of this kernel bound by its FP64 adds and conversions.  The
+// pass total joins the FP64 running sums once, as in reduce_partials.  Splits [0, nend)
+// each end a hop, hop hops0 + s.  When the pass ends at most w hops, every ring slot it
+// touches is read (the hop that leaves the window) before it is written, and no slot twice,
+// so a batch of HOP_B splits issues all its loads before the dependent updates; a longer
+// pass (a chunk longer than the window) runs the splits one at a time.
+constexpr int HOP_T = 256, HOP_B = 8;
+
+__global__ void __launch_bounds__(HOP_T) fold_hops_kernel(HopArgs h)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * HOP_T + threadIdx.x;
     if (e >= h.n_uc) return;
-    double2 pend = h.pend[e], wsum = h.wsum[e];
-    double tr = 0.0, ti = 0.0;
+    const size_t n = (size_t)h.n_uc;
+    const int64_t ends = (h.nc + h.off) / h.hop;
+    const int nend = ends < (int64_t)h.nsplit ? (int)ends : h.nsplit;
+    const bool batched = nend <= h.w;
+    // ring slot of the next hop and window-ring slot of the window it would complete, advanced
+    // one hop at a time (no 64-bit division per hop)
+    int slot = (int)(h.hops0 % h.w);
+    const int64_t kw0 = h.hops0 - h.w + 1;
+    int wslot = (int)(((kw0 % h.cap) + h.cap) % h.cap);
     int64_t hk = h.hops0;
-    for (int s = 0; s < h.nsplit; ++s) {
-        const float2 v = h.part[(size_t)s * h.n_uc + e];
-        pend.x += (double)v.x;
-        pend.y += (double)v.y;
-        tr += (double)v.x;
-        ti += (double)v.y;
-        if ((int64_t)(s + 1) * h.hop - h.off <= h.nc) {            // split s ends hop hk
-            double2* slot = h.ring + (size_t)(hk % h.w) * h.n_uc + e;
-            if (hk >= h.w) {
-                const double2 old = *slot;
-                wsum.x -= old.x;
-                wsum.y -= old.y;
+    float4 P = h.pend[e], W = h.wsum[e];                  // float-float (re hi, re lo, im hi, im lo)
+    float tr = 0.f, ti = 0.f;
+    for (int s0 = 0; s0 < h.nsplit; s0 += HOP_B) {
+        float2 v[HOP_B], old[HOP_B];
+#pragma unroll
+        for (int j = 0; j < HOP_B; ++j) {
+            const int s = s0 + j;
+            v[j] = s < h.nsplit ? h.part[(size_t)s * n + e] : make_float2(0.f, 0.f);
+            int sj = slot + j;                                         // < 2 w when s < nend <= w
+            if (sj >= h.w) sj -= h.w;
+            old[j] = batched && s < nend && hk + j >= h.w ? h.ring[(size_t)sj * n + e] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < HOP_B; ++j) {
+            const int s = s0 + j;
+            if (s >= h.nsplit) break;
+            ff_add(P.x, P.y, v[j].x);
+            ff_add(P.z, P.w, v[j].y);
+            tr += v[j].x;
+            ti += v[j].y;
+            if (s < nend) {                                            // split s ends hop hk
+                float2* rs = h.ring + (size_t)slot * n + e;
+                if (hk >= h.w) {
+                    const float2 o = batched ? old[j] : *rs;
+                    ff_add(W.x, W.y, -o.x);
+                    ff_add(W.z, W.w, -o.y);
+                }
+                const float2 h32 = make_float2(P.x + P.y, P.z + P.w);
+                ff_add(W.x, W.y, h32.x);
+                ff_add(W.z, W.w, h32.y);
+                *rs = h32;
+                if (hk >= h.w - 1) h.wout[(size_t)wslot * n + e] = make_float2(W.x + W.y, W.z + W.w);
+                P = make_float4(0.f, 0.f, 0.f, 0.f);
+                ++hk;
+                if (++slot == h.w) slot = 0;
+                if (++wslot == h.cap) wslot = 0;
             }
-            wsum.x += pend.x;
-            wsum.y += pend.y;
-            *slot = pend;
-            if (hk >= h.w - 1) h.wout[(size_t)((hk - h.w + 1) % h.cap) * h.n_uc + e] = wsum;
-            pend = make_double2(0.0, 0.0);
-            ++hk;
         }
     }
-    h.pend[e] = pend;
-    h.wsum[e] = wsum;
+    h.pend[e] = P;
+    h.wsum[e] = W;
     const double2 o = h.sums[e];
-    h.sums[e] = make_double2(o.x + tr, o.y + ti);
+    h.sums[e] = make_double2(o.x + (double)tr, o.y + (double)ti);
 }
 
-// Block (a, i): window k0 + i, cycle frequency a; the rotation is formed once per block.
-__global__ void read_windows_kernel(const double2* __restrict__ wout, int64_t cap, int64_t k0,
-                                    const int32_t* __restrict__ amap, const uint64_t* __restrict__ phi, int F,
-                                    int A, int L, int Au, int ncols, uint64_t base, int64_t hop, double inv_n,
-                                    double2* __restrict__ out)
+// Block (a-tile, i): window k0 + i for RW_A cycle frequencies.  RW_A threads form the
+// rotations from the exact u64 phase (FP64 sine and cosine, rounded to FP32 once); the
+// products are FP32 (the stored window sums are FP32) and leave as FP64.
+constexpr int RW_T = 256, RW_A = 8, RW_U = 8;
+
+__global__ void __launch_bounds__(RW_T) read_windows_kernel(const float2* __restrict__ wout, int64_t cap,
+                                                            int64_t k0, const int32_t* __restrict__ amap,
+                                                            const uint64_t* __restrict__ phi, int F, int A, int L,
+                                                            int Au, int ncols, uint64_t base, int64_t hop,
+                                                            double inv_n, double2* __restrict__ out)
 {
-    __shared__ double2 rot;
-    const int a = blockIdx.x;
+    __shared__ float2 rot[RW_A];
+    __shared__ int urow[RW_A];
+    const int a0 = blockIdx.x * RW_A;
     const int64_t i = blockIdx.y, k = k0 + i;
-    const int u = amap[a];
-    if (threadIdx.x == 0) {
+    const int na = A - a0 < RW_A ? A - a0 : RW_A;
+    const int FL = F * L;
+    const int total = na * FL;
+    if (threadIdx.x < na) {
+        const int u = amap[a0 + threadIdx.x];
+        urow[threadIdx.x] = u;
         // the window's first reference sample carries phase phi * (base + k hop) mod 2^64 in the
         // running sums; the window-local phase removes it: v * exp(+j 2 pi that / 2^64) / N
         const uint64_t th = phi[u] * (base + (uint64_t)k * (uint64_t)hop);
         const double t = (double)(th >> 11) * 0x1.0p-53;               // cycles in [0, 1)
         double sn, cs;
         sincospi(2.0 * t, &sn, &cs);
-        rot = make_double2(cs * inv_n, sn * inv_n);
+        rot[threadIdx.x] = make_float2((float)(cs * inv_n), (float)(sn * inv_n));
     }
     __syncthreads();
-    const double2* src = wout + (size_t)(k % cap) * (size_t)Au * ncols + (size_t)u * ncols;
+    const float2* src = wout + (size_t)(k % cap) * (size_t)Au * ncols;
     double2* dst = out + (size_t)i * F * A * L;
-    for (int e = threadIdx.x; e < F * L; e += blockDim.x) {
-        const int f = e % F, l = e / F;                                 // source column l F + f
-        const double2 v = src[e];
-        dst[((size_t)f * A + a) * L + l] = make_double2(v.x * rot.x - v.y * rot.y, v.x * rot.y + v.y * rot.x);
+    for (int q0 = 0; q0 < total; q0 += RW_T * RW_U) {
+        float2 v[RW_U];
+#pragma unroll
+        for (int j = 0; j < RW_U; ++j) {
+            const int q = q0 + j * RW_T + threadIdx.x;
+            v[j] = q < total ? src[(size_t)urow[q / FL] * ncols + q % FL] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < RW_U; ++j) {
+            const int q = q0 + j * RW_T + threadIdx.x;
+            if (q >= total) break;
+            const int ar = q / FL, e = q % FL;
+            const int f = e % F, l = e / F;                             // source column l F + f
+            const float2 r = rot[ar];
+            dst[((size_t)f * A + a0 + ar) * L + l] =
+                make_double2((double)(v[j].x * r.x - v[j].y * r.y), (double)(v[j].x * r.y + v[j].y * r.x));
+        }
     }
 }
 
@@ -157,19 +217,19 @@ namespace cyc {
 cudaError_t fold_hops(const HopArgs& h, cudaStream_t st)
 {
     if (h.n_uc <= 0 || h.nsplit <= 0) return cudaSuccess;
-    fold_hops_kernel<<<(h.n_uc + 255) / 256, 256, 0, st>>>(h);
+    fold_hops_kernel<<<(h.n_uc + HOP_T - 1) / HOP_T, HOP_T, 0, st>>>(h);
     return cudaGetLastError();
 }
 
-cudaError_t read_windows(const double2* wout, int64_t cap, int64_t k0, int64_t n, const int32_t* amap,
+cudaError_t read_windows(const float2* wout, int64_t cap, int64_t k0, int64_t n, const int32_t* amap,
                          const uint64_t* phi, int F, int A, int L, int Au, int ncols, uint64_t base, int64_t hop,
                          double inv_n, double2* out, cudaStream_t st)
 {
     if (n <= 0 || A <= 0) return cudaSuccess;
     for (int64_t i0 = 0; i0 < n; i0 += 65535) {
         const int64_t m = n - i0 < 65535 ? n - i0 : 65535;
-        read_windows_kernel<<<dim3(A, (unsigned)m), 128, 0, st>>>(wout, cap, k0 + i0, amap, phi, F, A, L, Au, ncols,
-                                                                  base, hop, inv_n, out + (size_t)i0 * F * A * L);
+        read_windows_kernel<<<dim3((A + RW_A - 1) / RW_A, (unsigned)m), RW_T, 0, st>>>(
+            wout, cap, k0 + i0, amap, phi, F, A, L, Au, ncols, base, hop, inv_n, out + (size_t)i0 * F * A * L);
     }
     return cudaGetLastError();
 }

@@ -9,7 +9,8 @@
 // an A-point DFT of the lag products folded modulo A.  A push only folds (O(samples x
 // columns) work, bound by memory traffic instead of the O(samples x columns x A) projection);
 // the DFT runs when the estimate is read.  F lives in FP64 in the stream's sums array,
-// [A][ncols], so reset, save and load work unchanged.
+// [ncols][A] (a warp's residues are neighbours in memory for the fold and for the read),
+// so reset, save and load work unchanged.
 #include "cyc_device.cuh"
 #include "cyc_impl.h"
 
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__
     }
     for (int f = 0; f < nF; ++f) {
         const bool cj = f == 0 ? cj0 : col_conj[c0 + f] != 0;
-        double2* o = F + (size_t)r * ncols + c0 + f;
+        double2* o = F + (size_t)(c0 + f) * A + r;
         const double2 v = *o;
         *o = cj ? make_double2(v.x + jr, v.y + ji) : make_double2(v.x + vr, v.y + vi);
     }
@@ -85,7 +86,7 @@ __global__ void dft_read_kernel(const double2* __restrict__ F, int A, int logA, 
         tw[j] = make_double2(cs, sn);
     }
     for (int r = threadIdx.x; r < A; r += blockDim.x) {
-        const double2 q = F[(size_t)r * ncols + c];
+        const double2 q = F[(size_t)c * A + r];
         const double s = (r & 1) ? -1.0 : 1.0;
         const unsigned rev = __brev((unsigned)r) >> (32 - logA);       // bit-reversed position
         v[rev] = make_double2(s * q.x, s * q.y);
@@ -131,12 +132,14 @@ cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double 
     int logA = 0;
     while ((1 << logA) < A) ++logA;
     const size_t smem = (size_t)A * 3 / 2 * sizeof(double2);
-    static bool attr = false;
-    if (!attr) {
+    static bool attr_set[64] = {false};                   // the attribute is per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(dft_read_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              4096 * 3 / 2 * 16);
         if (e != cudaSuccess) return e;
-        attr = true;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     dft_read_kernel<<<ncols, 256, smem, st>>>(F, A, logA, ncols, nF, L, inv_n, out);
     return cudaGetLastError();
