@@ -523,7 +523,7 @@ def full_leg(pkg, x_dev, reps=2):
     return {"spectrum_ms": t_spec * 1e3,
             "spectrum": "cyc_read_spectrum: 2 x 1024 cycle frequencies x 256 frequencies over 128 lags, Hann, FP64",
             "workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
-                        "%d samples in 2^16 pushes, fp32 products, fp64 fold + DFT" % T,
+                        "%d samples in 2^16 pushes, fp32 products, float-float fold, fp64 DFT" % T,
             "ms": m, "msamples_s": T / (m * 1e-3) / 1e6, "us_per_push": m * 1e3 / (T // C),
             "direct_equivalent_gmac_s": cmac_per_step(T) / (m * 1e-3) / 1e9,
             "err_rel_r00": stored_error(R, "cfg1", T), "err_tol": TOL["fp32"]}

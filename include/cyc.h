@@ -148,11 +148,11 @@ CYC_API int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop,
  * uniform grid a_k = -1/2 + k/A, k = 0 .. A-1 (p->alphas and p->nalphas are ignored; the
  * output's cycle-frequency index is k).  The result is the same estimator as a stream with
  * those alphas (same layout for cyc_read, same range of n, absolute phase); on this grid the
- * phase depends on n only through n mod A, so a push folds its lag products modulo A in FP64
- * and cyc_read takes one A-point DFT per column: O(samples x columns) work per push instead
- * of O(samples x columns x A).
+ * phase depends on n only through n mod A, so a push folds its lag products modulo A
+ * (float-float sums of FP32 runs, about 48 significant bits) and cyc_read takes one A-point
+ * DFT per column: O(samples x columns) work per push instead of O(samples x columns x A).
  *   A          power of two in [2, 4096]
- *   precision  must be CYC_P_FP32 (FP32 lag products, FP64 folding and DFT); else CYC_EINVAL
+ *   precision  must be CYC_P_FP32 (FP32 lag products, float-float folding, FP64 DFT); else CYC_EINVAL
  *   cross      0: one input (cyc_push); 1: two inputs (cyc_push_xy)
  * cyc_save / cyc_load, cyc_reset work as for any stream; windows are not available.
  */

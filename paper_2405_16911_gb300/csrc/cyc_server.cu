@@ -82,24 +82,37 @@ struct Fold {
     int      nslots;
 };
 
+// A block task is FOLD_Q x blockDim.x consecutive elements of one fold's tile: the fold is
+// found once per task and the element's row and column with 32-bit arithmetic (64-bit
+// division per element cost more than the fold's memory traffic).
+constexpr int FOLD_Q = 8;
+
 __global__ void fold_kernel(const Fold* __restrict__ folds, const int* __restrict__ nfolds,
                             const float2* __restrict__ slots, int tm, int tn)
 {
     const int TILE = tm * tn;
-    const int64_t total = (int64_t)(*nfolds) * TILE;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const Fold f = folds[e / TILE];
-        const int r = (int)((e % TILE) / tn), j = (int)(e % tn);
-        if (f.u0 + r >= f.Au || f.c0 + j >= f.ncols) continue;
-        float sr = 0.f, si = 0.f;
-        for (int k = 0; k < f.nslots; ++k) {
-            float2 v = slots[(f.slot0 + k) * TILE + r * tn + j];
-            sr += v.x;
-            si += v.y;
+    const int per = FOLD_Q * (int)blockDim.x;
+    const int tasks = (TILE + per - 1) / per;             // tasks per fold
+    const int ntask = *nfolds * tasks;
+    for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+        const int fi = t / tasks, ti = t - fi * tasks;
+        const Fold f = folds[fi];
+#pragma unroll
+        for (int q = 0; q < FOLD_Q; ++q) {
+            const int le = ti * per + q * (int)blockDim.x + (int)threadIdx.x;
+            if (le >= TILE) break;
+            const int r = le / tn, j = le - r * tn;
+            if (f.u0 + r >= f.Au || f.c0 + j >= f.ncols) continue;
+            float sr = 0.f, si = 0.f;
+            for (int k = 0; k < f.nslots; ++k) {
+                const float2 v = slots[(size_t)(f.slot0 + k) * TILE + le];
+                sr += v.x;
+                si += v.y;
+            }
+            double2* d = f.sums + (size_t)(f.u0 + r) * f.ncols + f.c0 + j;
+            const double2 o = *d;
+            *d = make_double2(o.x + (double)sr, o.y + (double)si);
         }
-        double2* d = f.sums + (size_t)(f.u0 + r) * f.ncols + f.c0 + j;
-        double2 o = *d;
-        *d = make_double2(o.x + (double)sr, o.y + (double)si);
     }
 }
 

@@ -8,9 +8,12 @@
 //     F_c[r] = sum_{n = r mod A} P_c(n),
 // an A-point DFT of the lag products folded modulo A.  A push only folds (O(samples x
 // columns) work, bound by memory traffic instead of the O(samples x columns x A) projection);
-// the DFT runs when the estimate is read.  F lives in FP64 in the stream's sums array,
-// [ncols][A] (a warp's residues are neighbours in memory for the fold and for the read),
-// so reset, save and load work unchanged.
+// the DFT runs when the estimate is read.  F lives in the stream's sums array as
+// float-float pairs (re hi, re lo, im hi, im lo: 16 bytes like a double2, about 48
+// significant bits), [ncols][A] (a warp's residues are neighbours in memory for the fold
+// and for the read), so reset, save and load work unchanged; the fold does no FP64
+// arithmetic (this GPU's FP64 rate is a small fraction of its FP32 rate) and the read
+// converts to FP64 before its FP64 DFT.
 #include "cyc_device.cuh"
 #include "cyc_impl.h"
 
@@ -22,21 +25,23 @@ constexpr int FOLD_T = 256;
 // Thread (r, l): the columns of lag l (both forms when F = 2) gain the pass terms i with
 // (base + i) mod A == r.  One pair of sample reads x[i + m], y[i + D] serves both forms;
 // consecutive threads take consecutive residues, so a warp's reads are consecutive, and four
-// terms are loaded ahead.  FP32 runs of at most 64 terms, each added once to FP64.
+// terms are loaded ahead.  FP32 runs of at most 64 terms, each added once to a float-float
+// total; the fold's old values are loaded before the terms.
 __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__ x, const float2* __restrict__ y,
                                                       int D, int64_t nc, int A, int base_mod,
                                                       const int32_t* __restrict__ col_lag,
                                                       const int8_t* __restrict__ col_conj, int ncols, int nF,
-                                                      double2* __restrict__ F)
+                                                      float4* __restrict__ F)
 {
     const int r = blockIdx.x * FOLD_T + threadIdx.x;
     const int c0 = blockIdx.y * nF;
     if (r >= A) return;
     const int m = col_lag[c0];
-    const bool cj0 = col_conj[c0] != 0;
+    float4 old[2];
+    for (int f = 0; f < nF; ++f) old[f] = F[(size_t)(c0 + f) * A + r];
     int64_t i = r - base_mod;
     if (i < 0) i += A;
-    double vr = 0.0, vi = 0.0, jr = 0.0, ji = 0.0;          // CONV and CONJ totals
+    float4 V = make_float4(0.f, 0.f, 0.f, 0.f), J = V;        // CONV and CONJ totals, float-float
     while (i < nc) {
         float sr = 0.f, si = 0.f, tr = 0.f, ti = 0.f;
         int q = 0;
@@ -61,20 +66,25 @@ __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__
             sr += a + b;  si += c - d;
             tr += a - b;  ti += c + d;
         }
-        vr += (double)sr; vi += (double)si;
-        jr += (double)tr; ji += (double)ti;
+        ff_add(V.x, V.y, sr);
+        ff_add(V.z, V.w, si);
+        ff_add(J.x, J.y, tr);
+        ff_add(J.z, J.w, ti);
     }
     for (int f = 0; f < nF; ++f) {
-        const bool cj = f == 0 ? cj0 : col_conj[c0 + f] != 0;
-        double2* o = F + (size_t)(c0 + f) * A + r;
-        const double2 v = *o;
-        *o = cj ? make_double2(v.x + jr, v.y + ji) : make_double2(v.x + vr, v.y + vi);
+        const float4 t = col_conj[c0 + f] ? J : V;
+        float4 o = old[f];
+        ff_add(o.x, o.y, t.x);
+        ff_add(o.x, o.y, t.y);
+        ff_add(o.z, o.w, t.z);
+        ff_add(o.z, o.w, t.w);
+        F[(size_t)(c0 + f) * A + r] = o;
     }
 }
 
 // Block c: out[f][k][l] = (1/N) sum_r (-1)^r F_c[r] exp(-j 2 pi k r / A) for column
 // c = l F + f, by an in-place radix-2 FFT in shared memory (FP64).
-__global__ void dft_read_kernel(const double2* __restrict__ F, int A, int logA, int ncols, int nF, int L,
+__global__ void dft_read_kernel(const float4* __restrict__ F, int A, int logA, int ncols, int nF, int L,
                                 double inv_n, double2* __restrict__ out)
 {
     extern __shared__ double2 v[];
@@ -86,7 +96,8 @@ __global__ void dft_read_kernel(const double2* __restrict__ F, int A, int logA, 
         tw[j] = make_double2(cs, sn);
     }
     for (int r = threadIdx.x; r < A; r += blockDim.x) {
-        const double2 q = F[(size_t)c * A + r];
+        const float4 ff = F[(size_t)c * A + r];
+        const double2 q = make_double2((double)ff.x + (double)ff.y, (double)ff.z + (double)ff.w);
         const double s = (r & 1) ? -1.0 : 1.0;
         const unsigned rev = __brev((unsigned)r) >> (32 - logA);       // bit-reversed position
         v[rev] = make_double2(s * q.x, s * q.y);
@@ -123,7 +134,7 @@ cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st)
     const int nF = a.nforms > 0 ? a.nforms : 1;
     dim3 grid((A + FOLD_T - 1) / FOLD_T, a.ncols / nF);
     fold_kernel<<<grid, FOLD_T, 0, st>>>(a.x, a.y ? a.y : a.x, a.D, a.nc, A, base_mod, a.col_lag, a.col_conj,
-                                         a.ncols, nF, F);
+                                         a.ncols, nF, reinterpret_cast<float4*>(F));
     return cudaGetLastError();
 }
 
@@ -141,7 +152,7 @@ cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double 
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dft_read_kernel<<<ncols, 256, smem, st>>>(F, A, logA, ncols, nF, L, inv_n, out);
+    dft_read_kernel<<<ncols, 256, smem, st>>>(reinterpret_cast<const float4*>(F), A, logA, ncols, nF, L, inv_n, out);
     return cudaGetLastError();
 }
 
