@@ -72,6 +72,19 @@ def kernel_hash(precision):
         return f.split(".")[0] + "@" + hashlib.sha256(fh.read()).hexdigest()[:12]
 
 
+def nvtx_range(name):
+    """An NVTX range around one leg, so that a profiler can select its launches
+    (`ncu --nvtx --nvtx-include "<name>/"`); a no-op where NVTX is unavailable."""
+    import contextlib
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+        torch.cuda.nvtx.range_pop()
+        return torch.cuda.nvtx.range(name)
+    except Exception:
+        return contextlib.nullcontext()
+
+
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -705,20 +718,27 @@ def run_ours(args):
                               "steps": k, "err_rel_r00": stored_error(R32, "cfg1", ARGS_SAMPLES[0])}
         line["speedup_vs_plain_fp32"] = value / world / line["plain_fp32"]["value"]
     if rank == 0 and not args.no_serving:
-        line["serving"] = serving_leg(pkg, seconds=args.serving_seconds)
+        with nvtx_range("serving"):
+            line["serving"] = serving_leg(pkg, seconds=args.serving_seconds)
         line["p99_ms"] = line["serving"]["loads"][-1]["p99_ms"]
     if rank == 0 and not args.no_latency:
-        line["cfg0_latency"] = latency_leg(pkg)
+        with nvtx_range("cfg0_latency"):
+            line["cfg0_latency"] = latency_leg(pkg)
     if rank == 0 and not args.no_precisions:
-        line["cfg2_precisions"] = precision_leg(pkg)
+        with nvtx_range("cfg2_precisions"):
+            line["cfg2_precisions"] = precision_leg(pkg)
     if rank == 0 and not args.no_cross:
-        line["f1_cross"] = cross_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
+        with nvtx_range("f1_cross"):
+            line["f1_cross"] = cross_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
     if rank == 0 and not args.no_full:
-        line["f3_full_mode"] = full_leg(pkg, x_dev)
+        with nvtx_range("f3_full_mode"):
+            line["f3_full_mode"] = full_leg(pkg, x_dev)
     if rank == 0 and not args.no_windows:
-        line["f2_windows"] = window_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
+        with nvtx_range("f2_windows"):
+            line["f2_windows"] = window_leg(pkg, x_dev, T=min(1 << 24, ARGS_SAMPLES[0]))
     if rank == 0 and not args.no_proposer:
-        line["cfg4_proposer"] = proposer_leg(pkg)
+        with nvtx_range("cfg4_proposer"):
+            line["cfg4_proposer"] = proposer_leg(pkg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
