@@ -494,14 +494,38 @@ def window_leg(pkg, x_dev, T=1 << 24, reps=2):
     return res
 
 
+def full_big_pushes(pkg, x_dev, out, T, CB, reps):
+    """The Full-mode stream of full_leg pushed in CB-sample chunks: device ms, samples/s."""
+    import torch
+    with pkg.Stream(np.arange(NLAGS), None, pkg.CYC_BOTH, max_chunk=CB, full=NALPHAS) as s:
+        def run_big():
+            s.reset()
+            for c in range(T // CB):
+                s.push(x_dev[2 * c * CB:2 * (c + 1) * CB])
+            s.read(out)
+        run_big()
+        mb = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run_big()
+            e1.record()
+            torch.cuda.synchronize()
+            mb.append(e0.elapsed_time(e1))
+    m2 = statistics.median(mb)
+    return {"ms": m2, "msamples_s": T / (m2 * 1e-3) / 1e6, "us_per_push": m2 * 1e3 / (T // CB)}
+
+
 def full_leg(pkg, x_dev, reps=2):
     """The paper's Full mode on the config-1 workload: every cycle frequency -1/2 + k/1024 (the
     config-1 grid itself), lags 0..127, both forms, the whole stream in 2^16-sample pushes, one
-    read at the end.  The lag products (FP32) are folded modulo 1024 in FP64 and one FP64 DFT
-    per column runs at the read: a different algorithm from the projection, bound by the
-    sample reads of the fold rather than by the tensor pipe.  Reported: device time, samples/s,
-    the direct estimator's complex MACs per second for the same output, and the error on the
-    stored oracle entries."""
+    read at the end.  The lag products (FP32) are folded modulo 1024 in float-float and one
+    FP64 DFT per column runs at the read: a different algorithm from the projection, bound by
+    the latency of the fold's sample reads rather than by the tensor pipe.  Reported: device
+    time, samples/s, the direct estimator's complex MACs per second for the same output, the
+    error on the stored oracle entries, and the same stream pushed in 2^20-sample chunks
+    (fewer per-push copies and launches for the same work)."""
     import torch
     C = CHUNK
     T = x_dev.numel() // 2
@@ -533,7 +557,12 @@ def full_leg(pkg, x_dev, reps=2):
         t_spec = (time.perf_counter() - t0) / 5
     m = statistics.median(ms)
     R = R[..., 0] + 1j * R[..., 1]
+    CB = 1 << 20
+    big = None
+    if T >= 4 * CB:
+        big = full_big_pushes(pkg, x_dev, out, T, CB, reps)
     return {"spectrum_ms": t_spec * 1e3,
+            "pushes_2^20": big,
             "spectrum": "cyc_read_spectrum: 2 x 1024 cycle frequencies x 256 frequencies over 128 lags, Hann, FP64",
             "workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
                         "%d samples in 2^16 pushes, fp32 products, float-float fold, fp64 DFT" % T,
