@@ -40,7 +40,7 @@ NS = (1 << 16) + 16          # 16 x 4096 feature samples plus the largest featur
 LAGS = np.arange(64, dtype=np.int32)
 GRID = -0.5 + np.arange(512) / 512.0
 P_FA = 1e-3
-SEED_TRAIN, SEED_TEST = 0xC7C1_0004, 0xC7C1_8004
+SEED_TRAIN, SEED_VAL, SEED_TEST = 0xC7C1_0004, 0xC7C1_4004, 0xC7C1_8004
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposer_weights.npy")
 
 
@@ -193,6 +193,7 @@ def train(pkg, feats, labels, epochs: int = 30, batch: int = 32, lr: float = 2e-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=16384)
+    ap.add_argument("--val", type=int, default=0, help="validation signals (recall at each tau)")
     ap.add_argument("--test", type=int, default=1024)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch-signals", type=int, default=2048, help="signals generated and labelled per block")
@@ -238,7 +239,17 @@ def main():
     print("test set: %d signals, %d detections" % (args.test, int(lte.sum())))
     net = train(pkg, feats, ltr, epochs=args.epochs)
     np.save(args.out, pkg.cyc_net_get_params(net))
-    for tau in (args.tau, 0.8, 0.5, 0.0):
+    del feats
+    taus = (args.tau, 0.8, 0.5, 0.0)
+    if args.val > 0:
+        xva = make_signals(args.val, SEED_VAL)
+        dva = torch.from_numpy(xva.view(np.float32)).cuda().view(args.val, NS * 2)
+        lva = label(pkg, dva, args.val)
+        print("validation set: %d signals, %d detections" % (args.val, int(lva.sum())))
+        for tau in taus:
+            print("val tau=%.2f:" % tau, recall_and_gain(pkg, net, dva, lva, tau=tau))
+        del dva, xva
+    for tau in taus:
         ms = []
         print("test tau=%.2f:" % tau, recall_and_gain(pkg, net, dte, lte, tau=tau, misses=ms))
         if tau == args.tau:
@@ -247,6 +258,9 @@ def main():
                 print("  missed: signal %d %s a=%+.4f s/nu=%.1f kind %d sps %d snr %.1f f0 %+.4f%s%s" % (
                     i, ("CONV", "CONJ")[f], GRID[b], rte[i][f, b], p["kind"], p["sps"], p["snr_db"], p["f0"],
                     "" if line_bins(p)[f, b] else " (away from every generated line)", " fallback" if fb else ""))
+    if args.test > 1024:
+        print("test, first 1024 signals tau=%.2f:" % args.tau,
+              recall_and_gain(pkg, net, dte[:1024], lte[:1024], tau=args.tau))
     pkg.cyc_net_destroy(net)
 
 
