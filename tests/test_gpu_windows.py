@@ -131,3 +131,30 @@ def test_window_ring_backpressure_and_reset(cyc):
         with pytest.raises(cyc.CycError) as e:
             s.read_windows(1)
         assert e.value.code == cyc.CYC_EINVAL
+
+
+def test_windows_long_stream_no_drift(cyc):
+    """16 384 hops through the add-one/drop-one window update: the last windows equal the
+    oracle's estimate over just their own samples (the window-local phase makes a window
+    depend on nothing else), so error carried along the stream would show here."""
+    import torch
+    T, N, hop, C = 1 << 20, 4096, 64, 1 << 16
+    lags = np.arange(8)
+    alphas = np.concatenate([[0.0], np.random.default_rng(70).uniform(-0.5, 0.5, 19)])
+    x = synth.white(T, seed=170).astype(np.complex64)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    cap = C // hop + 1
+    last, k_last = None, None
+    with cyc.Stream(lags, alphas, 3, precision="fp32", max_chunk=C, window=(N, hop, cap)) as s:
+        for c in range(T // C):
+            s.push(xt[2 * c * C:2 * (c + 1) * C])
+            W, k0 = s.read_windows(cap)
+            if W.shape[0]:
+                last, k_last = W.copy(), k0
+    M = int(lags.max())
+    nrm = oracle.r00_xy(x, None, 0, 0)
+    for i in (0, last.shape[0] // 2, last.shape[0] - 1):
+        k = k_last + i
+        Wo = oracle.windows(x[k * hop:k * hop + N + M], None, lags, alphas, N, hop)[0]
+        assert np.max(np.abs(last[i] - Wo)) / nrm < 1e-5, (k, np.max(np.abs(last[i] - Wo)) / nrm)
+    assert k_last + last.shape[0] - 1 == (T - M - N) // hop
