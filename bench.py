@@ -278,6 +278,7 @@ def serving_leg(pkg, seconds=3.0, loads=(0.5, 0.9), nbase=16, blen=3 << 19):
         out["capacity_msamples_s"] = sat["msamples_s"]
         res = []
         for ld in loads:
+            rng = np.random.default_rng(0xC7C1_0103)         # the same arrival sequence at every load
             r = run(ld * cap / mean_chunk, seconds)
             r["offered_load"] = ld
             r["offered_msamples_s"] = ld * cap / 1e6
