@@ -290,8 +290,9 @@ def serving_leg(pkg, seconds=3.0, loads=(0.5, 0.9), nbase=16, blen=3 << 19):
 def latency_leg(pkg, calls=1000, warm=20):
     """Config 0: one 65536-sample GMSK chunk (BT 0.3, 8 sps, offset 0.05, 10 dB), lags 0..31,
     64 cycle frequencies per form (k/8 CONV and 0.1 + k/8 CONJ, 8 distinct mod 1 each), FP32.
-    One call = reset + push of the resident chunk + read into host memory, on one stream
-    per form; per-call wall time percentiles over `calls` calls."""
+    One call = reset + push of the resident chunk on one stream per form (both queued before
+    either is waited for, so the two forms' GPU work overlaps), then a read of each into host
+    memory; per-call wall time percentiles over `calls` calls."""
     import torch
     from synth import workloads
     w = workloads.config0()
@@ -299,13 +300,18 @@ def latency_leg(pkg, calls=1000, warm=20):
     T = w["x"].size
     lags = w["lags"]
     outs = [np.empty((1, 64, 32), dtype=np.complex128) for _ in range(2)]
-    with pkg.Stream(lags, w["alphas_conv"], pkg.CYC_CONV, precision="fp32", max_chunk=T) as sc, \
-            pkg.Stream(lags, w["alphas_conj"], pkg.CYC_CONJ, precision="fp32", max_chunk=T) as sj:
+    torch.cuda.synchronize()
+    cs = [torch.cuda.Stream(), torch.cuda.Stream()]                 # one CUDA stream per form
+    with pkg.Stream(lags, w["alphas_conv"], pkg.CYC_CONV, precision="fp32", max_chunk=T,
+                    cuda_stream=cs[0].cuda_stream) as sc, \
+            pkg.Stream(lags, w["alphas_conj"], pkg.CYC_CONJ, precision="fp32", max_chunk=T,
+                       cuda_stream=cs[1].cuda_stream) as sj:
         def call():
-            for s, o in ((sc, outs[0]), (sj, outs[1])):
+            for s in (sc, sj):
                 s.reset()
                 s.push(x_dev)
-                s.read(o)
+            sc.read(outs[0])
+            sj.read(outs[1])
         for _ in range(warm):
             call()
         ts = []
@@ -320,7 +326,7 @@ def latency_leg(pkg, calls=1000, warm=20):
                         "0.1 + k/8: %d), CONV+CONJ, fp32" % (au[0], au[1]),
             "calls": calls, "p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99)),
             "mean_us": float(ts.mean()), "gmac_s_at_p50": cmac / (np.percentile(ts, 50) * 1e-6) / 1e9,
-            "call": "reset + push (device chunk) + read (host) for each form"}
+            "call": "reset + push (device chunk) on each form's stream, then read (host) of each"}
 
 
 def precision_leg(pkg, reps=3):
