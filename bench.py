@@ -159,6 +159,19 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def oracle_sample_rate(x, lags, alphas, target_s=10.0, max_T=1 << 16):
     """The FP64 oracle on a prefix of the stream with the full grid; GMAC/s."""
     import oracle
@@ -607,7 +620,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config("fp64 oracle"),
         "msamples_per_s": T_s / dt / 1e6,
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -778,9 +792,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         v, n, dt = oracle_sample_rate(x, lags, alphas, target_s=args.cpu_seconds)
+        n1 = max(256, n // 16)
+        t0 = time.perf_counter()
+        oracle.estimate(x[:n1 + int(np.max(lags))], lags, alphas, threads=1)
+        v1 = n1 * len(lags) * len(alphas) * NFORMS / (time.perf_counter() - t0) / 1e9
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                                 "sample": "first %d committed samples of the stream, full grid "
-                                          "(1024 a x 128 lags x 2 forms), %.1f s" % (n, dt)}
+                                          "(1024 a x 128 lags x 2 forms), %.1f s" % (n, dt),
+                                "value_1core": v1, "sample_1core": "first %d committed samples, one thread" % n1,
+                                "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
