@@ -20,32 +20,41 @@
 namespace cyc {
 namespace {
 
-constexpr int FOLD_T = 256;
+constexpr int FOLD_T = 256, FOLD_R = FOLD_T / 2;       // 128 residues x 2 halves of the terms
 
-// Thread (r, l): the columns of lag l (both forms when F = 2) gain the pass terms i with
-// (base + i) mod A == r.  One pair of sample reads x[i + m], y[i + D] serves both forms;
-// consecutive threads take consecutive residues, so a warp's reads are consecutive, and four
-// terms are loaded ahead.  FP32 runs of at most 64 terms, each added once to a float-float
-// total; the fold's old values are loaded before the terms.
+// Thread (r, h, l): the columns of lag l (both forms when F = 2) gain the pass terms i with
+// (base + i) mod A == r, the first half of them (h = 0) or the second (h = 1).  One pair of
+// sample reads x[i + m], y[i + D] serves both forms; consecutive threads take consecutive
+// residues, so a warp's reads are consecutive, and four terms are loaded ahead.  FP32 runs
+// of at most 64 terms, each added once to a float-float total; the second half's totals
+// join the first's through shared memory (a fixed order), which then updates the fold.
+// Two threads per (residue, lag) halve each thread's chain of dependent load rounds.
 __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__ x, const float2* __restrict__ y,
                                                       int D, int64_t nc, int A, int base_mod,
                                                       const int32_t* __restrict__ col_lag,
                                                       const int8_t* __restrict__ col_conj, int ncols, int nF,
                                                       float4* __restrict__ F)
 {
-    const int r = blockIdx.x * FOLD_T + threadIdx.x;
+    __shared__ float4 half2[2][FOLD_R];                   // the second half's CONV and CONJ totals
+    const int rl = threadIdx.x % FOLD_R, h = threadIdx.x / FOLD_R;
+    const int r = blockIdx.x * FOLD_R + rl;
     const int c0 = blockIdx.y * nF;
-    if (r >= A) return;
+    const bool live = r < A;
     const int m = col_lag[c0];
     float4 old[2];
-    for (int f = 0; f < nF; ++f) old[f] = F[(size_t)(c0 + f) * A + r];
+    if (live && h == 0)
+        for (int f = 0; f < nF; ++f) old[f] = F[(size_t)(c0 + f) * A + r];
     int64_t i = r - base_mod;
     if (i < 0) i += A;
+    const int64_t K = (nc + A - 1) / A;                   // terms per residue, at most
+    const int64_t Kh = (K + 1) / 2;
+    i += h * Kh * (int64_t)A;
+    const int64_t iend = h == 0 ? (i + Kh * (int64_t)A < nc ? i + Kh * (int64_t)A : nc) : nc;
     float4 V = make_float4(0.f, 0.f, 0.f, 0.f), J = V;        // CONV and CONJ totals, float-float
-    while (i < nc) {
+    while (live && i < iend) {
         float sr = 0.f, si = 0.f, tr = 0.f, ti = 0.f;
         int q = 0;
-        for (; q < 64 && i + 3 * (int64_t)A < nc; q += 4, i += 4 * (int64_t)A) {
+        for (; q < 64 && i + 3 * (int64_t)A < iend; q += 4, i += 4 * (int64_t)A) {
             float2 xm[4], y0[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__
                 tr += a - b;  ti += c + d;                   // x[n+m] y[n]
             }
         }
-        for (; q < 64 && i < nc; ++q, i += A) {
+        for (; q < 64 && i < iend; ++q, i += A) {
             const float2 xm = __ldg(&x[i + m]), y0 = __ldg(&y[i + D]);
             const float a = xm.x * y0.x, b = xm.y * y0.y, c = xm.y * y0.x, d = xm.x * y0.y;
             sr += a + b;  si += c - d;
@@ -71,6 +80,21 @@ __global__ void __launch_bounds__(FOLD_T) fold_kernel(const float2* __restrict__
         ff_add(J.x, J.y, tr);
         ff_add(J.z, J.w, ti);
     }
+    if (h == 1) {
+        half2[0][rl] = V;
+        half2[1][rl] = J;
+    }
+    __syncthreads();
+    if (h == 1 || !live) return;
+    const float4 V2 = half2[0][rl], J2 = half2[1][rl];
+    ff_add(V.x, V.y, V2.x);
+    ff_add(V.x, V.y, V2.y);
+    ff_add(V.z, V.w, V2.z);
+    ff_add(V.z, V.w, V2.w);
+    ff_add(J.x, J.y, J2.x);
+    ff_add(J.x, J.y, J2.y);
+    ff_add(J.z, J.w, J2.z);
+    ff_add(J.z, J.w, J2.w);
     for (int f = 0; f < nF; ++f) {
         const float4 t = col_conj[c0 + f] ? J : V;
         float4 o = old[f];
@@ -132,7 +156,7 @@ cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st)
     const int base_mod = (int)(a.nbase & (uint64_t)(A - 1));
     // columns c = l nF + f: both forms of a lag share one thread (nF = columns per lag)
     const int nF = a.nforms > 0 ? a.nforms : 1;
-    dim3 grid((A + FOLD_T - 1) / FOLD_T, a.ncols / nF);
+    dim3 grid((A + FOLD_R - 1) / FOLD_R, a.ncols / nF);
     fold_kernel<<<grid, FOLD_T, 0, st>>>(a.x, a.y ? a.y : a.x, a.D, a.nc, A, base_mod, a.col_lag, a.col_conj,
                                          a.ncols, nF, reinterpret_cast<float4*>(F));
     return cudaGetLastError();
