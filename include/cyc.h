@@ -131,7 +131,10 @@ CYC_API int cyc_create_xy(const cyc_params* p, cyc_stream** out);
  * running sums of cyc_read keep their meaning.  A window is complete once its last x
  * sample has been pushed; completed windows wait in a device ring of `capacity` windows
  * for cyc_read_windows.  A push that would complete more windows than the ring has room
- * for fails with CYC_EAGAIN before doing anything (read windows, then push again).
+ * for fails with CYC_EAGAIN before doing anything (read windows, then push again).  Window
+ * sums are formed from hop sums rounded once to FP32 and wait in FP32 until read (about
+ * 1e-7 of each entry beyond the projection's own error); the update that adds a hop and
+ * drops the oldest cancels exactly, so long streams carry no drift.
  *   win_len   positive multiple of hop, win_len / hop <= 65536
  *   hop       >= 16 samples between window starts
  *   capacity  1 .. 2^20 windows of F * (distinct a) * nlags * 8 bytes each (held in FP32
