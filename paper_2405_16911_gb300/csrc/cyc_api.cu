@@ -60,7 +60,7 @@ constexpr int64_t kMaxChunk = 1ll << 28;
 constexpr int32_t kMaxLag = 1 << 20;
 constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
 constexpr int kWinSplits = 64;      // hop-aligned partials per pass of a windowed stream
-constexpr uint32_t kBlobVersion = 2;       // 2: Full-mode folds stored [columns][residues]
+constexpr uint32_t kBlobVersion = 3;       // 3: tensor-core streams keep their sums in unit order
 
 // a (cycles/sample) -> round(a * 2^64) mod 2^64, exactly.  a = m * 2^e with m the 53-bit
 // integer significand, so a * 2^64 = m * 2^(e+64): a left shift (bits beyond 2^64 are
@@ -138,7 +138,10 @@ struct cyc_stream {
     std::vector<uint64_t> phi_u;
     std::vector<int32_t> amap;
     int Au = 0;
+    UnitLayout units;               // tensor-core streams: phi_u in unit order (order_units)
     int ncols = 0;
+    long long wait_budget = 0;      // SM cycles per bounded device wait (0: the default)
+    int withhold = 0;               // test only (CYC_TEST_WITHHOLD_ARRIVAL=1 at creation)
     int64_t n0 = 0, T = 0, n_eff = 0, held = 0, max_chunk = kDefaultChunk;
     uint64_t fingerprint = 0;
     // device state
@@ -245,7 +248,7 @@ int alloc_state(cyc_stream* s)
     CK(cudaMalloc(&s->d_col_conj, s->ncols * sizeof(int8_t)));
     CK(cudaMemcpy(s->d_col_conj, cc.data(), s->ncols * sizeof(int8_t), cudaMemcpyHostToDevice));
     if (s->precision != CYC_P_FP32)
-        s->part_elems = tc_max_partials(s->Au, s->ncols, s->num_sms);
+        s->part_elems = tc_max_partials(s->units.U, s->Au, s->ncols, s->num_sms);
     else if (small_supported(s->Au))
         s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
     else
@@ -289,13 +292,14 @@ int project(cyc_stream* s, int64_t nc)
     a.y = s->cross ? s->stage_y[s->cur] : nullptr;
     a.D = s->Mneg;
     a.nforms = s->F;
+    a.np = s->units.np;
+    a.nself = s->units.nself;
+    a.U = s->units.U;
+    a.budget = s->wait_budget;
+    a.withhold = s->withhold;
     // FP32 with a handful of distinct cycle frequencies: register sums + warp shuffles
     const bool small = s->precision == CYC_P_FP32 && small_supported(s->Au);
-    // CTA pairs take two 128-row tiles at a time: with 1 or 3 tiles the empty partner would
-    // idle a quarter to half of the SMs, so those run one CTA per tile
-    const int tx = (s->Au + tc_tile_rows() - 1) / tc_tile_rows();
-    const bool pair = s->pair_ctas > 0 && (tx % 2 == 0 || tx >= 5);
-    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->Au, s->ncols, nc, s->num_sms, pair ? s->pair_ctas : 0)
+    ProjPlan pl = s->precision != CYC_P_FP32 ? tc_plan(s->units.U, s->Au, s->ncols, nc, s->num_sms, s->pair_ctas)
                   : small                    ? small_plan(s->Au, s->ncols, nc, s->num_sms)
                                              : fp32_plan(s->Au, s->ncols, nc, s->num_sms);
     if (s->win) {                     // one split per hop (the first and last may be partial)
@@ -319,7 +323,7 @@ int project(cyc_stream* s, int64_t nc)
         CK(cudaEventRecord(ev.first, s->st));
     }
     CK(s->full                    ? full_fold(a, s->Au, s->sums, s->st)
-       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, pair, s->st)
+       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->st)
        : small                    ? small_launch(a, s->st)
                                   : fp32_launch(a, s->st));
     if (s->prof) {
@@ -459,6 +463,7 @@ static int create_impl(const cyc_params* p, bool cross, int64_t win_len, int64_t
         s->amap[i] = it->second;
     }
     s->Au = (int)s->phi_u.size();
+    if (s->precision != CYC_P_FP32) s->units = order_units(s->phi_u, s->amap);
     s->ncols = s->F * s->L;
     s->n0 = p->n0;
     s->max_chunk = p->max_chunk > 0 ? p->max_chunk : kDefaultChunk;
@@ -488,8 +493,14 @@ static int create_impl(const cyc_params* p, bool cross, int64_t win_len, int64_t
         return fail(CYC_ECUDA, "cannot query the SM count");
     }
     if (s->precision != CYC_P_FP32) {
-        const char* ev = getenv("CYC_TC_PAIR");
-        s->pair_ctas = (ev && ev[0] == '0') ? 0 : tc_pair_ctas(s->precision);
+        s->pair_ctas = tc_pair_ctas(s->precision);
+        if (s->pair_ctas < 2) {
+            delete s;
+            return fail(CYC_ENOTSUP, "the tensor-core projection needs two-CTA clusters, which this device cannot "
+                                     "hold; use CYC_P_FP32");
+        }
+        const char* ev = getenv("CYC_TEST_WITHHOLD_ARRIVAL");
+        s->withhold = (ev && ev[0] == '1') ? 1 : 0;
     }
     rc = alloc_state(s);
     if (rc) {

@@ -4,12 +4,18 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cyc.h"
 
 namespace cyc {
+
+// Bounded device waits give up after this many SM cycles unless the caller sets another
+// budget (about one second at 2 GHz).
+constexpr long long kDefaultWaitBudget = 2000000000ll;
 
 // One projection pass over a contiguous view of the stream (Sec. 4, Eq. (impl-corr)):
 //   part[s][u][c] = sum over n in split s of  W(u, n) * P_c(n)
@@ -37,39 +43,109 @@ struct ProjArgs {
     int             D = 0;          // offset M^- of the reference sample y[n + D]
     int64_t         split_off = 0;  // split s covers [s * split_len - split_off, + split_len) within [0, nc)
     int             nforms = 0;     // columns per lag (c = l * nforms + f); 0 where unused
+    // tensor-core passes: phi in unit order (order_units) with np pairs, nself values of
+    // {0, 1/2}, U units in all
+    int             np = 0, nself = 0, U = 0;
+    long long       budget = 0;     // SM cycles per bounded wait (0: kDefaultWaitBudget)
+    int             withhold = 0;   // test only: the projection leaves one producer arrival out
 };
 
-// One work item of the tensor-core projection: 128 cycle frequencies x 128 columns x an
-// n-range of one stream.  Sample n of the stream is x[n & xmask] (xmask = ring capacity - 1,
-// or all ones for a linear view with x_avail readable samples).  Result element (row r,
-// tile column j) goes to out[r * out_stride + j] for u0 + r < Au and c0 + j < ncols.
+// One work item of the tensor-core projection: 128 units of cycle frequencies (up to 256
+// distinct a) x 128 columns x an n-range of one stream, run by one pair of CTAs.  Sample n
+// of the stream is x[n & xmask] (xmask = ring capacity - 1, or all ones for a linear view
+// with x_avail readable samples).  The result for distinct cycle frequency d (row of the
+// unit order) and tile column j goes to out[(d - d_lo) * out_stride + j] for c0 + j < ncols.
 struct TcItem {
     const float2*   x;
     uint64_t        xmask;
     int64_t         x_avail;
     uint64_t        nbase;      // absolute index of stream sample 0, mod 2^64
     int64_t         n_beg, n_end;
-    const uint64_t* phi;
+    const uint64_t* phi;        // distinct cycle frequencies in unit order
     const int32_t*  col_lag;
     const int8_t*   col_conj;
     float2*         out;
     int             out_stride;
-    int             u0, Au, c0, ncols, M;
+    int             u0;         // first unit of the tile (a multiple of 128)
+    int             d_lo;       // distinct row of the tile's first output
+    int             np, nself, U;
+    int             c0, ncols, M;
     const float2*   y;          // second input (linear views only) or nullptr: y = x
     int             D;          // offset of the reference sample y[n + D]
-    int64_t         out_peer;   // pair lists: the odd CTA's rows u0 + 128 .. go to out + out_peer
-    // Dual items (pair lists): a second stream with the same cycle frequencies, lags and
-    // forms over a range of the same length.  The even CTA stages and forms the columns of
-    // the first stream, the odd CTA those of the second; the weights follow the first
-    // stream's sample index, so the second stream's sums are rotated by
-    // exp(-j 2 pi a dphase / 2^64) before they are written to out2.
-    const float2*   x2;         // nullptr: not a dual item
-    uint64_t        xmask2;
-    int64_t         n_beg2;
-    float2*         out2;
-    int64_t         out_peer2;  // the odd CTA's rows of the second stream go to out2 + out_peer2
-    uint64_t        dphase;     // (nbase2 + n_beg2) - (nbase + n_beg) mod 2^64
 };
+
+// Unit order of the distinct cycle frequencies for the tensor-core projection: every a whose
+// negative -a (mod 1) is also present forms a pair with it (rows 2k: the one seen first,
+// 2k + 1: its negative), then the self-conjugate values 0 and 1/2 (one unit of real weight
+// rows), then the rest, one unit each.  A pair costs the same tensor work as one complex
+// cycle frequency, because exp(+j 2 pi a n) is the conjugate of exp(-j 2 pi a n) (see
+// proj_tc.cu).  phi_u is reordered in place and amap remapped; the result is a pure function
+// of the distinct list, so equal lists give equal orders.
+struct UnitLayout {
+    int np = 0, nself = 0, ns = 0, U = 0;
+};
+
+inline UnitLayout order_units(std::vector<uint64_t>& phi_u, std::vector<int32_t>& amap)
+{
+    const int Au = (int)phi_u.size();
+    std::vector<int> where(Au, -1);
+    std::vector<std::pair<uint64_t, int>> sorted(Au);
+    for (int i = 0; i < Au; ++i) sorted[i] = {phi_u[i], i};
+    std::sort(sorted.begin(), sorted.end());
+    auto find = [&](uint64_t v) -> int {
+        auto itv = std::lower_bound(sorted.begin(), sorted.end(), std::make_pair(v, -1));
+        return (itv != sorted.end() && itv->first == v) ? itv->second : -1;
+    };
+    std::vector<int> pairs, selfs, singles;
+    std::vector<char> used(Au, 0);
+    for (int i = 0; i < Au; ++i) {
+        if (used[i]) continue;
+        const uint64_t v = phi_u[i];
+        if (v == 0 || v == (1ull << 63)) {
+            selfs.push_back(i);
+            used[i] = 1;
+            continue;
+        }
+        const int j = find(~v + 1ull);
+        if (j >= 0 && !used[j]) {
+            pairs.push_back(i);
+            pairs.push_back(j);
+            used[i] = used[j] = 1;
+        } else {
+            singles.push_back(i);
+            used[i] = 1;
+        }
+    }
+    std::vector<int> order;
+    order.reserve(Au);
+    order.insert(order.end(), pairs.begin(), pairs.end());
+    order.insert(order.end(), selfs.begin(), selfs.end());
+    order.insert(order.end(), singles.begin(), singles.end());
+    std::vector<uint64_t> nphi(Au);
+    for (int k = 0; k < Au; ++k) {
+        nphi[k] = phi_u[order[k]];
+        where[order[k]] = k;
+    }
+    phi_u.swap(nphi);
+    for (auto& a : amap) a = where[a];
+    UnitLayout L;
+    L.np = (int)pairs.size() / 2;
+    L.nself = (int)selfs.size();
+    L.ns = (int)singles.size();
+    L.U = L.np + (L.nself > 0 ? 1 : 0) + L.ns;
+    return L;
+}
+
+// Distinct row (in unit order) of output h (0, 1) of unit k, or -1: a pair gives rows 2k
+// and 2k + 1, the real unit rows 2 np .. 2 np + nself - 1, a single unit one row.
+__host__ __device__ inline int unit_row(int k, int h, int np, int nself, int U)
+{
+    if (k < 0 || k >= U) return -1;
+    if (k < np) return 2 * k + h;
+    const int nr = nself > 0 ? 1 : 0;
+    if (k < np + nr) return h < nself ? 2 * np + h : -1;
+    return h == 0 ? 2 * np + nself + (k - np - nr) : -1;
+}
 
 // Launch geometry chosen by a kernel family for one pass.
 struct ProjPlan {
@@ -120,16 +196,18 @@ ProjPlan    small_plan(int Au, int ncols, int64_t nc, int num_sms);
 cudaError_t small_launch(const ProjArgs& a, cudaStream_t st);
 size_t      small_max_partials(int Au, int ncols, int num_sms);
 
-// Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu).
+// Tensor-core projection, FP16 single pass or BF16 three-product split (proj_tc.cu), on
+// pairs of CTAs (two-CTA clusters issuing cta_group::2 MMAs).
 bool        tc_supported(int ncols, int M);
-// pair_ctas: CTAs that can run as resident two-CTA clusters (tc_pair_ctas), 0 for the
-// one-CTA kernel; tc_launch(pair = true) then runs cta_group::2 pairs.
+// CTAs that can run as resident two-CTA clusters (0: cluster launches unavailable, and the
+// tensor-core precisions with them).
 int         tc_pair_ctas(int precision);
-ProjPlan    tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas);
-cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t st);
-size_t      tc_max_partials(int Au, int ncols, int num_sms);
-int         tc_tile_rows();     // cycle frequencies per work item
-int         tc_tile_cols();     // columns per work item
+ProjPlan    tc_plan(int U, int Au, int ncols, int64_t nc, int num_sms, int pair_ctas);
+cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st);
+size_t      tc_max_partials(int U, int Au, int ncols, int num_sms);
+int         tc_pair_units();    // units per work item (128)
+int         tc_tile_rows();     // rows of an item's partial tile (2 outputs per unit: 256)
+int         tc_tile_cols();     // columns per work item (128)
 // The uniform grid a_k = -1/2 + k/A (full_mode.cu): fold a pass's lag products modulo A into
 // F ([A][ncols], FP64, accumulated), and at read time the A-point DFT of every column into
 // out[f][k][l] / N.  A a power of two in [2, 4096].
@@ -144,11 +222,9 @@ cudaError_t spectrum(const double2* R, const int32_t* lags, int rows, int L, int
                      double2* E, double2* S, cudaStream_t st);
 
 // Persistent launch over a device list of work items (taken with an atomic counter that
-// the caller zeroes before the launch); `grid` CTAs, one per SM.  pair = true: `grid`
-// (even) CTAs in two-CTA clusters, each item covering rows u0 .. u0 + 255 (the odd CTA's
-// half written at out + out_peer).
-cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, bool pair,
-                            int* err, cudaStream_t st);
+// the caller zeroes before the launch); `grid` (even) CTAs in two-CTA clusters, one per SM.
+cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, int* err,
+                            long long budget, cudaStream_t st);
 
 // Sets the calling thread's message returned by cyc_last_error() (cyc_api.cu).
 void record_error(const char* msg);

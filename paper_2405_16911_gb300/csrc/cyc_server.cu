@@ -3,9 +3,10 @@
 // Each stream keeps its samples in a device ring (power-of-two capacity), its FP64 sums and
 // its tables on the device.  cyc_server_submit copies a chunk into the ring on a copy stream
 // and returns once it has landed.  The engine thread forms batches: for every open stream
-// with new samples, the committed range [n_sched, T - M) becomes work items of 128 cycle
-// frequencies x 128 columns x at most item_samples terms (tile-major, so the items of one
-// stream tile are consecutive and share one fold).  A batch is launched as
+// with new samples, the committed range [n_sched, T - M) becomes work items of 128 units of
+// cycle frequencies (a and -a share a unit: up to 256 distinct values) x 128 columns x at
+// most item_samples terms (tile-major, so the items of one stream tile are consecutive and
+// share one fold).  A batch is launched as
 //     H2D copy of the item and fold lists  ->  CUDA graph [zero the item counter ->
 //     persistent tensor-core kernel over the items -> FP64 fold of the item partials]
 // with two batches in flight, so chunks that arrive while one batch runs join the next.
@@ -73,11 +74,11 @@ struct DevGuard {
     }
 };
 
-// sums[(u0+r)*ncols + c0+j] += sum over the item partials of one stream tile (FP32 adds
-// over the items, one FP64 add per value).
+// sums[(d_lo+r)*ncols + c0+j] += sum over the item partials of one stream tile (FP32 adds
+// over the items, one FP64 add per value); rows r < nrows of the tile exist.
 struct Fold {
     double2* sums;
-    int      u0, Au, c0, ncols;
+    int      d_lo, nrows, c0, ncols;
     int64_t  slot0;      // first partial tile (units of one tile of float2)
     int      nslots;
 };
@@ -102,14 +103,14 @@ __global__ void fold_kernel(const Fold* __restrict__ folds, const int* __restric
             const int le = ti * per + q * (int)blockDim.x + (int)threadIdx.x;
             if (le >= TILE) break;
             const int r = le / tn, j = le - r * tn;
-            if (f.u0 + r >= f.Au || f.c0 + j >= f.ncols) continue;
+            if (r >= f.nrows || f.c0 + j >= f.ncols) continue;
             float sr = 0.f, si = 0.f;
             for (int k = 0; k < f.nslots; ++k) {
                 const float2 v = slots[(size_t)(f.slot0 + k) * TILE + le];
                 sr += v.x;
                 si += v.y;
             }
-            double2* d = f.sums + (size_t)(f.u0 + r) * f.ncols + f.c0 + j;
+            double2* d = f.sums + (size_t)(f.d_lo + r) * f.ncols + f.c0 + j;
             const double2 o = *d;
             *d = make_double2(o.x + (double)sr, o.y + (double)si);
         }
@@ -128,9 +129,9 @@ struct SrvStream {
     std::atomic<bool> open{false};
     std::atomic<bool> closing{false};
     int F = 0, L = 0, A = 0, Au = 0, ncols = 0;
+    UnitLayout units;                 // phi in unit order (order_units)
     int32_t M = 0;
     int64_t n0 = 0;
-    uint64_t cfg = 0;                 // hash of the cycle frequencies, lags and forms
     float2* ring = nullptr;
     uint64_t cap = 0;
     double2* sums = nullptr;
@@ -167,8 +168,7 @@ struct Batch {
 struct cyc_server {
     cyc_server_params p;
     int num_sms = 1;
-    int grid = 1;               // CTAs of the persistent launch
-    bool pair = false;          // items run on two-CTA pairs (256 cycle-frequency rows each)
+    int grid = 2;               // CTAs of the persistent launch (two-CTA pairs)
     cudaStream_t cst = nullptr, xst = nullptr;
     std::vector<std::unique_ptr<SrvStream>> streams;
     std::mutex admin;
@@ -231,168 +231,79 @@ int cyc_server::form_and_launch()
     int64_t ns = 0;
     std::vector<std::pair<int, int64_t>> marks;
     const int nstreams = (int)streams.size();
-    const int BMr = tc_tile_rows(), BNc = tc_tile_cols();
+    const int UP = tc_pair_units(), TR = tc_tile_rows(), BNc = tc_tile_cols();
     const int64_t IS = p.item_samples;
-    const int64_t TILE = (int64_t)BMr * BNc;
-    // pairs: one item covers tiles 2k and 2k + 1 (the second may not exist)
-    const int tstep = pair ? 2 : 1;
+    const int64_t TILE = (int64_t)TR * BNc;
 
-    struct Geo {
-        int ta, tcn, titems;
-    };
-    auto geometry = [&](const SrvStream& s) {
-        Geo g;
-        g.ta = (s.Au + BMr - 1) / BMr;
-        g.tcn = (s.ncols + BNc - 1) / BNc;
-        g.titems = (g.ta + tstep - 1) / tstep;
-        return g;
-    };
-    // folds and partial slots for np pieces of stream s, laid out tile-major:
-    //   slot(ip, ic, k, pc) = base + ((ip tcn + ic) tstep + k) np + pc
-    auto reserve = [&](SrvStream& s, int np) {
-        const Geo g = geometry(s);
-        const int64_t base = ns;
-        for (int ip = 0; ip < g.titems; ++ip)
-            for (int ic = 0; ic < g.tcn; ++ic)
-                for (int k = 0; k < tstep && ip * tstep + k < g.ta; ++k) {
-                    Fold& f = folds[nf++];
-                    f.sums = s.sums;
-                    f.u0 = (ip * tstep + k) * BMr;
-                    f.Au = s.Au;
-                    f.c0 = ic * BNc;
-                    f.ncols = s.ncols;
-                    f.slot0 = base + ((int64_t)(ip * g.tcn + ic) * tstep + k) * np;
-                    f.nslots = np;
-                }
-        ns += (int64_t)g.titems * g.tcn * tstep * np;
-        return base;
-    };
-    auto slot_of = [&](int64_t base, const Geo& g, int np, int ip, int ic, int pc) {
-        return base + (int64_t)(ip * g.tcn + ic) * tstep * np + pc;
-    };
-    auto make_item = [&](SrvStream& s, int ip, int ic, int64_t nb, int64_t len, int64_t slot, int np) -> TcItem& {
-        TcItem& it = items[ni++];
-        it.x = s.ring;
-        it.xmask = s.cap - 1;
-        it.x_avail = INT64_MAX;
-        it.nbase = (uint64_t)s.n0;
-        it.n_beg = nb;
-        it.n_end = nb + len;
-        it.phi = s.d_phi;
-        it.col_lag = s.d_col_lag;
-        it.col_conj = s.d_col_conj;
-        it.out = slots + slot * TILE;
-        it.out_stride = BNc;
-        it.u0 = ip * tstep * BMr;
-        it.Au = s.Au;
-        it.c0 = ic * BNc;
-        it.ncols = s.ncols;
-        it.M = s.M;
-        it.y = nullptr;
-        it.D = 0;
-        it.out_peer = (int64_t)np * TILE;          // the second tile's slots follow
-        it.x2 = nullptr;
-        it.xmask2 = 0;
-        it.n_beg2 = 0;
-        it.out2 = nullptr;
-        it.out_peer2 = 0;
-        it.dphase = 0;
-        return it;
-    };
-    // one stream: as many of its pieces as the batch has room for (false: no room at all)
+    // one stream: as many of its pieces as the batch has room for (false: no room at all).
+    // Items and their partial slots are tile-major: slot(ip, ic, pc) = base + (ip tcn + ic) np + pc
     auto single = [&](int sid) -> bool {
         SrvStream& s = *streams[sid];
         const int64_t upto = s.T.load() - s.M, n_sched = s.n_sched.load();
         if (upto <= n_sched) return true;
-        const Geo g = geometry(s);
+        const int ta = (s.units.U + UP - 1) / UP, tcn = (s.ncols + BNc - 1) / BNc;
         int64_t span = upto - n_sched;
         const int pieces = (int)((span + IS - 1) / IS);
-        const int room_items = (p.max_items - ni) / (g.titems * g.tcn);
-        const int64_t room_slots = (nslot_cap - ns) / (g.titems * tstep * g.tcn);
-        const int room_folds = (2 * p.max_items - nf) / (g.ta * g.tcn);
+        const int room_items = (p.max_items - ni) / (ta * tcn);
+        const int64_t room_slots = (nslot_cap - ns) / (ta * tcn);
+        const int room_folds = (p.max_items - nf) / (ta * tcn);
         int fit = (int)std::min<int64_t>(pieces, std::min<int64_t>(room_items, room_slots));
         if (room_folds <= 0) fit = 0;
         if (fit <= 0) return false;
         if (fit < pieces) span = (int64_t)fit * IS;
-        const int64_t base = reserve(s, fit);
-        for (int ip = 0; ip < g.titems; ++ip)
-            for (int ic = 0; ic < g.tcn; ++ic)
-                for (int pc = 0; pc < fit; ++pc)
-                    make_item(s, ip, ic, n_sched + pc * IS, std::min<int64_t>(IS, span - pc * IS),
-                              slot_of(base, g, fit, ip, ic, pc), fit);
+        const int64_t base = ns;
+        ns += (int64_t)ta * tcn * fit;
+        for (int ip = 0; ip < ta; ++ip) {
+            const int u0 = ip * UP;
+            const int d_lo = unit_row(u0, 0, s.units.np, s.units.nself, s.units.U);
+            const int d_hi = ip + 1 < ta ? unit_row(u0 + UP, 0, s.units.np, s.units.nself, s.units.U) : s.Au;
+            for (int ic = 0; ic < tcn; ++ic) {
+                const int64_t slot0 = base + (int64_t)(ip * tcn + ic) * fit;
+                Fold& f = folds[nf++];
+                f.sums = s.sums;
+                f.d_lo = d_lo;
+                f.nrows = d_hi - d_lo;
+                f.c0 = ic * BNc;
+                f.ncols = s.ncols;
+                f.slot0 = slot0;
+                f.nslots = fit;
+                for (int pc = 0; pc < fit; ++pc) {
+                    TcItem& it = items[ni++];
+                    it.x = s.ring;
+                    it.xmask = s.cap - 1;
+                    it.x_avail = INT64_MAX;
+                    it.nbase = (uint64_t)s.n0;
+                    it.n_beg = n_sched + pc * IS;
+                    it.n_end = it.n_beg + std::min<int64_t>(IS, span - pc * IS);
+                    it.phi = s.d_phi;
+                    it.col_lag = s.d_col_lag;
+                    it.col_conj = s.d_col_conj;
+                    it.out = slots + (slot0 + pc) * TILE;
+                    it.out_stride = BNc;
+                    it.u0 = u0;
+                    it.d_lo = d_lo;
+                    it.np = s.units.np;
+                    it.nself = s.units.nself;
+                    it.U = s.units.U;
+                    it.c0 = ic * BNc;
+                    it.ncols = s.ncols;
+                    it.M = s.M;
+                    it.y = nullptr;
+                    it.D = 0;
+                }
+            }
+        }
         s.n_sched.store(n_sched + span);
         marks.emplace_back(sid, n_sched + span);
         return true;
     };
-    // two streams with the same cycle frequencies, lags and forms (at most 128 columns):
-    // dual items over their common span -- one CTA pair forms both streams' columns with one
-    // set of weights -- and the rest of the longer stream alone
-    auto dual = [&](int sa, int sb) -> bool {
-        SrvStream& A = *streams[sa];
-        SrvStream& B = *streams[sb];
-        const int64_t ua = A.T.load() - A.M, na = A.n_sched.load();
-        const int64_t ub = B.T.load() - B.M, nbb = B.n_sched.load();
-        const int64_t spa = ua - na, spb = ub - nbb, C = std::min(spa, spb);
-        const Geo g = geometry(A);
-        const int P = (int)((C + IS - 1) / IS);
-        const int ra = (int)((spa - C + IS - 1) / IS), rb = (int)((spb - C + IS - 1) / IS);
-        const int npa = P + ra, npb = P + rb;
-        const int need_items = g.titems * g.tcn * (P + ra + rb);
-        const int64_t need_slots = (int64_t)g.titems * g.tcn * tstep * (npa + npb);
-        if (C <= 0 || ni + need_items > p.max_items || ns + need_slots > nslot_cap ||
-            nf + 2 * g.ta * g.tcn > 2 * p.max_items)
-            return single(sa) && single(sb);
-        const int64_t basea = reserve(A, npa), baseb = reserve(B, npb);
-        const uint64_t dph = ((uint64_t)B.n0 + (uint64_t)nbb) - ((uint64_t)A.n0 + (uint64_t)na);
-        for (int ip = 0; ip < g.titems; ++ip)
-            for (int ic = 0; ic < g.tcn; ++ic) {
-                for (int pc = 0; pc < P; ++pc) {
-                    TcItem& it = make_item(A, ip, ic, na + pc * IS, std::min<int64_t>(IS, C - pc * IS),
-                                           slot_of(basea, g, npa, ip, ic, pc), npa);
-                    it.x2 = B.ring;
-                    it.xmask2 = B.cap - 1;
-                    it.n_beg2 = nbb + pc * IS;
-                    it.out2 = slots + slot_of(baseb, g, npb, ip, ic, pc) * TILE;
-                    it.out_peer2 = (int64_t)npb * TILE;
-                    it.dphase = dph;
-                }
-                for (int pc = 0; pc < ra; ++pc)
-                    make_item(A, ip, ic, na + C + pc * IS, std::min<int64_t>(IS, spa - C - pc * IS),
-                              slot_of(basea, g, npa, ip, ic, P + pc), npa);
-                for (int pc = 0; pc < rb; ++pc)
-                    make_item(B, ip, ic, nbb + C + pc * IS, std::min<int64_t>(IS, spb - C - pc * IS),
-                              slot_of(baseb, g, npb, ip, ic, P + pc), npb);
-            }
-        A.n_sched.store(ua);
-        B.n_sched.store(ub);
-        marks.emplace_back(sa, ua);
-        marks.emplace_back(sb, ub);
-        return true;
-    };
 
-    std::map<uint64_t, int> waiting;                  // a stream waiting for a dual partner, per key
-    bool full = false;
-    for (int k = 0; k < nstreams && !full; ++k) {
+    for (int k = 0; k < nstreams; ++k) {
         const int sid = (rr + k) % nstreams;
         SrvStream& s = *streams[sid];
         if (!s.open.load(std::memory_order_acquire) || s.closing.load()) continue;
         if (s.T.load() - s.M <= s.n_sched.load()) continue;
-        if (pair && s.ncols <= BNc / 2) {
-            auto w = waiting.find(s.cfg);
-            if (w == waiting.end()) {
-                waiting.emplace(s.cfg, sid);
-                continue;
-            }
-            const int other = w->second;
-            waiting.erase(w);
-            full = !dual(other, sid);
-        } else {
-            full = !single(sid);
-        }
-    }
-    for (auto& w : waiting) {
-        if (full) break;
-        full = !single(w.second);
+        if (!single(sid)) break;
     }
     rr = (rr + 1) % (nstreams > 0 ? nstreams : 1);
     if (ni == 0) return 0;
@@ -498,7 +409,7 @@ int capture_graph(cyc_server* s, int b)
     cudaGraph_t g = nullptr;
     SCK(cudaStreamBeginCapture(s->cst, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->cst);
-    tc_launch_items(s->d_items[b], s->d_counts[b], s->d_counter, s->grid, s->p.precision, s->pair, s->d_err, s->cst);
+    tc_launch_items(s->d_items[b], s->d_counts[b], s->d_counter, s->grid, s->p.precision, s->d_err, 0, s->cst);
     fold_kernel<<<s->num_sms * 4, 256, 0, s->cst>>>(s->d_folds[b], s->d_counts[b] + 1, s->slots, tc_tile_rows(),
                                                     tc_tile_cols());
     cudaError_t e = cudaStreamEndCapture(s->cst, &g);
@@ -550,7 +461,7 @@ int cyc_server_create(const cyc_server_params* pp, cyc_server** out)
     *out = nullptr;
     cyc_server_params p = *pp;
     if (p.max_streams <= 0) p.max_streams = 256;
-    if (p.max_items <= 0) p.max_items = 4096;
+    if (p.max_items <= 0) p.max_items = 1024;
     if (p.item_samples <= 0) p.item_samples = 65536;
     if (p.ring_samples <= 0) p.ring_samples = 1 << 22;
     if (p.precision != CYC_P_FP16 && p.precision != CYC_P_BF16X3)
@@ -582,18 +493,19 @@ int cyc_server_create(const cyc_server_params* pp, cyc_server** out)
     chk(cudaStreamCreateWithFlags(&s->xst, cudaStreamNonBlocking), "copy stream");
     const int64_t tile = (int64_t)tc_tile_rows() * tc_tile_cols();
     {
-        const char* ev = getenv("CYC_TC_PAIR");
-        const int pc = (ev && ev[0] == '0') ? 0 : tc_pair_ctas(p.precision);
-        s->pair = pc >= 2;
-        s->grid = s->pair ? (pc < s->num_sms ? pc : s->num_sms) & ~1 : s->num_sms;
+        const int pc = tc_pair_ctas(p.precision);
+        if (pc < 2 && rc == CYC_OK)
+            rc = sfail(CYC_ENOTSUP, "cyc_server_create: the device cannot hold the two-CTA clusters the server runs on");
+        s->grid = (pc < s->num_sms ? pc : s->num_sms) & ~1;
+        if (s->grid < 2) s->grid = 2;
     }
-    s->nslot_cap = (s->pair ? 2 : 1) * (int64_t)p.max_items;      // one partial tile per item and tile
+    s->nslot_cap = (int64_t)p.max_items;                 // one partial tile per item
     for (int b = 0; b < 2 && rc == CYC_OK; ++b) {
         chk(cudaMallocHost(&s->h_items[b], sizeof(TcItem) * p.max_items), "pinned items");
-        chk(cudaMallocHost(&s->h_folds[b], sizeof(Fold) * 2 * p.max_items), "pinned folds");
+        chk(cudaMallocHost(&s->h_folds[b], sizeof(Fold) * p.max_items), "pinned folds");
         chk(cudaMallocHost(&s->h_counts[b], 2 * sizeof(int)), "pinned counts");
         chk(cudaMalloc(&s->d_items[b], sizeof(TcItem) * p.max_items), "items");
-        chk(cudaMalloc(&s->d_folds[b], sizeof(Fold) * 2 * p.max_items), "folds");
+        chk(cudaMalloc(&s->d_folds[b], sizeof(Fold) * p.max_items), "folds");
         chk(cudaMalloc(&s->d_counts[b], 2 * sizeof(int)), "counts");
         if (rc == CYC_OK) chk(cudaMemset(s->d_counts[b], 0, 2 * sizeof(int)), "counts");
     }
@@ -604,8 +516,8 @@ int cyc_server_create(const cyc_server_params* pp, cyc_server** out)
     if (rc == CYC_OK) {
         // an empty launch fixes the kernel's shared-memory attribute before capture
         chk(cudaMemset(s->d_counter, 0, sizeof(int)), "counter");
-        chk(tc_launch_items(s->d_items[0], s->d_counts[0], s->d_counter, s->pair ? 2 : 1, p.precision, s->pair,
-                            s->d_err, s->cst), "warm-up");
+        chk(tc_launch_items(s->d_items[0], s->d_counts[0], s->d_counter, 2, p.precision, s->d_err, 0, s->cst),
+            "warm-up");
         chk(cudaStreamSynchronize(s->cst), "warm-up");
     }
     for (int b = 0; b < 2 && rc == CYC_OK; ++b) rc = capture_graph(s, b);
@@ -660,6 +572,7 @@ int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const doubl
         amap[i] = it->second;
     }
     const int Au = (int)phi_u.size(), ncols = nlags * F;
+    const UnitLayout units = order_units(phi_u, amap);
     const int forms[2] = {conj_flag & CYC_CONV ? CYC_CONV : CYC_CONJ, CYC_CONJ};
     std::vector<int32_t> cl(ncols);
     std::vector<int8_t> cc(ncols);
@@ -686,19 +599,7 @@ int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const doubl
     SrvStream& s = *srv->streams[slot];
     s.F = F; s.L = nlags; s.A = nalphas; s.Au = Au; s.ncols = ncols; s.M = M; s.n0 = n0;
     s.cap = cap;
-    {
-        // streams with equal keys share their weights in dual items (FNV-1a over the tables)
-        uint64_t h = 1469598103934665603ull;
-        auto mix = [&h](const void* p, size_t n) {
-            const unsigned char* c = (const unsigned char*)p;
-            for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
-        };
-        mix(phi_u.data(), phi_u.size() * sizeof(uint64_t));
-        mix(cl.data(), cl.size() * sizeof(int32_t));
-        mix(cc.data(), cc.size());
-        mix(&M, sizeof M);
-        s.cfg = h;
-    }
+    s.units = units;
     auto fail_free = [&](cudaError_t e, const char* what) {
         s.release();
         return sfail(e == cudaErrorMemoryAllocation ? CYC_EAGAIN : CYC_ECUDA, "cyc_server_open: %s: %s", what,

@@ -1,54 +1,69 @@
 // proj_tc.cu -- tensor-core a-projection (tcgen05, sm_103a): FP16 single pass and the
 // BF16 three-product split, FP32 accumulation in tensor memory (TMEM).
 //
-// A work item is 128 cycle frequencies (MMA M) x 256 columns (MMA N) x a range of committed
-// n.  The complex GEMM  S[u][c] = sum_n W[u][n] P_c(n)  (Sec. 4 Set mode: the per-alpha
-// projection of the lag products; W = exp(-j 2 pi a n), P = x[n+m] x*[n] or x[n+m] x[n],
-// Eqs. (ACF-def), (CCF-def)) runs as two real GEMMs over K = (re, im) of 8 samples per
-// K = 16 step:
-//     D_r += [Wr | -Wi] . [Pr ; Pi]        D_i += [Wi | Wr] . [Pr ; Pi]
-// D_r and D_i live in TMEM columns [0, 256) and [256, 512).  The weights carry the absolute
-// sample index, so an item accumulates in TMEM without any per-tile rotation.  The tensor
-// core's FP32 accumulation drifts with the length of the chain (on the mean-power entry,
-// about 2e-3 of its value over 2^19 samples), so an item longer than Cfg::SUBN samples (4096
-// for BF16x3, 65536 for FP16) runs as consecutive sub-items, each a fresh TMEM chain: the
-// first writes the item's FP32 partial tile, the later ones add to it.
-// Operands go through a ring of shared-memory stages (one 8-sample group each), K-major,
-// no swizzle, 8-row x 16-byte core matrices:
-//   P block: row r (column), chunk k (0: Pr, 1: Pi) at (r/8)*256 + k*128 + (r%8)*16
-//   W block: row r (cycle freq), chunk k (0: Wi, 1: Wr, 2: -Wi) at (r/8)*384 + k*128 + (r%8)*16
-// so that [Wr | -Wi] starts at chunk 1 and [Wi | Wr] at chunk 0, both with LBO = 128.
-// The samples x[n .. n + XB + M) of each block are staged in shared memory by TMA bulk
-// copies (a ring of two slots), so that the lag-product warps read shared memory only.
-// BF16x3: v = hi + lo, hi = bf16(v), lo = bf16(v - hi); products hi.hi, hi.lo, lo.hi.
+// The projection (Sec. 4 Set mode: the per-alpha correlation of the lag products;
+// Eqs. (ACF-def), (CCF-def)) is  S_a[c] = sum_n W_a(n) P_c(n)  with W_a(n) = exp(-j 2 pi a n)
+// and P_c the lag product of column c.  Writing W = Wr + j Wi and P = Pr + j Pi, the four
+// real sums  Trr = sum Wr Pr,  Tii = sum Wi Pi,  Tri = sum Wr Pi,  Tir = sum Wi Pr  give both
+//     S_a  = (Trr - Tii) + j (Tri + Tir)          (weights W_a)
+//     S_-a = (Trr + Tii) + j (Tri - Tir)          (weights conj(W_a) = W_-a)
+// so a cycle frequency and its negative cost one real GEMM of two weight rows (Wr, Wi) by
+// two lag-product rows (Pr, Pi): 2 real multiply-adds per complex term instead of the 4 of
+// a complex GEMM.  The distinct cycle frequencies are ordered into *units* of two weight
+// rows (see order_units in cyc_impl.h):
+//   pair    (a, -a)            rows Wr(a), Wi(a)      -> S_a and S_-a
+//   real    (0 and/or 1/2)     rows W(0), W(1/2)      -> each row's own (Tr, Ti); W is real
+//   single  a without partner  rows Wr(a), Wi(a)      -> S_a only
+// A uniform grid -1/2 + k/A (A even) is A/2 - 1 pairs and one real unit: no row is idle.
 //
-// Items with at most 128 columns ("narrow", e.g. 64 lags x 2 forms) issue N = 128 MMAs: each
-// P thread forms one column (B row = tile column) and the epilogue reads 128 D columns.
+// Work item: 256 units (512 weight rows) x 128 complex columns x a range of committed n, on a
+// pair of CTAs (a cluster of two issuing cta_group::2 MMAs with M = 256, N = 256, K = 16
+// samples).  The units form two sub-tiles of 128; CTA r holds the weight rows of units
+// u0 + 128 q + 64 r .. + 63 of sub-tile q (A operands A_0, A_1: 128 rows each, its TMEM lanes)
+// and forms the lag products of tile columns 64 r .. 64 r + 63 (B operand: B rows 128 r ..
+// 128 r + 127 of the pair's 256).  Every stage issues D_q += A_q B for both sub-tiles, so one
+// stage of lag products serves 512 weight rows, and each CTA's TMEM holds two accumulators
+// (D_0, D_1) of its 128 rows times all 256 real columns.
 //
-// Warp roles (576 threads).  Two producer sets; set k produces the groups G = k mod 2 of
-// the CTA's running group counter G, so one set's latencies hide behind the other's work:
-//   set k, warps 8k+0..3  P warps: thread t forms tile columns 2t, 2t+1 (with lag-major
-//                         columns both forms of one lag) -> B rows t and t + 128
-//   set k, warps 8k+4..7  W warps: thread t forms the weights of cycle-frequency row t;
-//                         set 0's are also the epilogue (TMEM lane quadrant = warp % 4)
-//   warp 16  TMEM allocation; lane 0 issues every tcgen05.mma and commit
-//   warp 17  lane 0: the TMA sample loader
-// Items may start at any sample; the staged block then starts one sample earlier (bulk
-// copies need 16-byte alignment) and readers skip it.  The linear view needs x_avail even.
-// Barriers: full[s] (8 producer warps -> MMA), empty[s] (tcgen05.commit -> producers),
-// xfull/xempty for the sample slots, done (last MMA of an item -> epilogue).  Every wait is
-// bounded; a wait that gives up sets the caller's status word and the CTA winds down.
+// Shared-memory operands per stage (16 samples), K-major, no swizzle, 8-row x 16-byte core
+// matrices, row r and sample chunk k (0: samples 0-7, 1: 8-15) at (r/8)*256 + k*128 + (r%8)*16:
+//   A_q: rows 2i / 2i + 1 = the two weight rows of unit i of the sub-tile
+//   B: for slot s < 32 (tile column 64 r + 2 s): Pr at row s, Pi at row 32 + s;
+//      for slot s >= 32 (tile column 64 r + 2 (s - 32) + 1): Pr at 64 + s - 32, Pi at 96 + s - 32
+// so every store of a warp covers 32 consecutive B rows (no bank conflicts).  A stage holds
+// per level [A_0 | A_1 | B]; BF16x3 (v = hi + lo, hi = bf16(v), lo = bf16(v - hi)) issues
+// hi.hi, hi.lo and lo.hi, the hi level first.
 //
-// Two launch modes share the code: one item per CTA derived from the grid (cyc_push), and a
-// persistent list of items taken with an atomic counter (the multi-stream server).
+// The tensor core's FP32 accumulation drifts with the length of the chain, so an item runs as
+// chains of at most Cfg::SUBN samples, each a fresh accumulator; the first chain writes the
+// item's FP32 partial tile and later ones add to it.
 //
-// CTA pairs (grid mode): a cluster of two CTAs on two SMs takes two neighbouring 128-row
-// cycle-frequency tiles over the same columns and samples and issues cta_group::2 MMAs with
-// M = 256.  Each CTA forms the weights of its own 128 rows (A) and half of the B rows: the
-// even CTA B rows [0, N/2), the odd one [N/2, N) -- so each SM forms half the lag products
-// and its tensor core reads half of B from its own shared memory.  Producers of both CTAs
-// arrive on the even CTA's full[s]; the even CTA's MMA thread signals empty[s] and done in
-// both CTAs through a multicast commit.
+// Warp roles (704 threads):
+//   set k = 0, 1 (stages G with G mod 2 = k, so one set's latency hides behind the other's):
+//     warps 8k + 0..3   P warps: warp 8k + p, lane t forms slot 32 (p & 1) + t for the samples
+//                       8 (p >> 1) .. + 7 of the stage
+//     warps 8k + 4..7   W warps: thread i forms both weight rows of unit i % 64 of sub-tile
+//                       i / 64 (one rotation gives the real and the imaginary part)
+//   warps 16..19        epilogue (TMEM lane quadrant = warp % 4)
+//   warp 20             TMEM allocation; lane 0 of the even CTA issues every MMA and commit
+//   warp 21             lane 0: TMA loader of the sample blocks (ring of two slots)
+// A set's eight warps meet at a named barrier after writing a stage, and one thread per CTA
+// then arrives on the even CTA's full barrier: two arrivals per stage (one arrival per warp,
+// 12 or more per stage, serialised on the barrier and cost more than a stage of MMAs).
+// Barriers: full[s] (one arrival per CTA of the pair -> the even CTA's MMA thread),
+// empty[s] (MMA commit -> producers of both CTAs), xfull / xempty (sample slots), done
+// (last MMA of a chain -> epilogues of both CTAs), tfree (epilogues of both CTAs -> MMA).
+//
+// Every wait is bounded by a cycle budget given at launch.  A wait that gives up sets the
+// caller's status word and an abort flag in shared memory of both CTAs; every other wait
+// polls the flag and fails at once, so one lost arrival ends the whole pair within one
+// budget.  Before the CTAs exit, issued sample copies and MMAs are waited for (bounded,
+// ignoring the flag), and the pair deallocates its TMEM after a cluster barrier.
+//
+// Two launch modes share the code: one item per CTA pair derived from the grid (cyc_push),
+// and a persistent list of items taken with an atomic counter (the multi-stream server),
+// where the even CTA fetches and hands the item index to the odd one through distributed
+// shared memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -59,41 +74,33 @@
 namespace cyc {
 namespace {
 
-constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int GS = 8;                    // samples per group (one K = 16 step)
-constexpr int NSET = 2;                  // producer sets
+constexpr int ROWS = 128;                // weight rows per CTA and sub-tile (64 units)
+constexpr int CTA_UNITS = 64;
+constexpr int SUB_UNITS = 128;           // units of a sub-tile (both CTAs)
+constexpr int NSUB = 2;                  // sub-tiles per item
+constexpr int ITEM_UNITS = NSUB * SUB_UNITS;
+constexpr int TILE_CC = 128;             // complex columns per item
+constexpr int GS = 16;                   // samples per stage (one K = 16 step)
+constexpr int NSET = 2;
 constexpr int P_WARPS = 4, W_WARPS = 4, SET_WARPS = P_WARPS + W_WARPS;
-constexpr int MMA_WARP = NSET * SET_WARPS;
+constexpr int EPI_WARP = NSET * SET_WARPS;
+constexpr int MMA_WARP = EPI_WARP + 4;
 constexpr int LOAD_WARP = MMA_WARP + 1;
 constexpr int NTHREADS = (LOAD_WARP + 1) * 32;
-constexpr int P_BYTES = 8192, W_BYTES = 6144;
-constexpr uint32_t P_LBO = 128, P_SBO = 256, W_LBO = 128, W_SBO = 384;
+constexpr int OPB = 4096;                // one operand block of one level: 128 rows x 16 samples x 2 B
+constexpr int LEVEL_BYTES = (NSUB + 1) * OPB;   // [A_0 | A_1 | B]
+constexpr uint32_t LBO = 128, SBO = 256;
 constexpr int XSLOT = 3072;              // samples per staging slot (block + halo)
-constexpr int MAX_LAG = 2560;            // leaves blocks of at least 512 samples
-constexpr uint32_t TM_DR = 0, TM_DI = 256;
-constexpr long long WAIT_BUDGET = 2000000000ll;   // SM cycles (about one second)
-
-// Waits and arrivals on the stage barriers: cluster scope when the pair shares them.
-template <bool PAIR>
-__device__ __forceinline__ bool bwait(void* bar, uint32_t parity)
-{
-    if constexpr (PAIR) return tc::mbar_wait_cluster(bar, parity, WAIT_BUDGET);
-    else return tc::mbar_wait(bar, parity, WAIT_BUDGET);
-}
-
-template <bool PAIR>
-__device__ __forceinline__ void full_arrive(void* bar)
-{
-    if constexpr (PAIR) tc::mbar_arrive_remote(bar, 0);     // the even CTA's barrier
-    else tc::mbar_arrive(bar);
-}
+constexpr int MAX_LAG = 2560;            // leaves blocks of at least 240 samples
+constexpr int TM_COLS = 256;             // one accumulator
+constexpr int FULL_ARRIVALS = 2;         // one per CTA and stage (after the set's named barrier)
+constexpr int TFREE_ARRIVALS = 2 * 4;    // epilogue warps of both CTAs
 
 template <int PREC>
 struct Cfg;
 template <>
 struct Cfg<CYC_P_FP16> {
-    static constexpr int NLEV = 1, NPASS = 1, NSTAGE = 10;
+    static constexpr int NLEV = 1, NPASS = 1, NSTAGE = 12;
     static constexpr bool BF = false;
     static constexpr int SUBN = 1 << 16;     // samples per TMEM chain (drift ~4e-4 against 1e-2)
 };
@@ -101,15 +108,16 @@ template <>
 struct Cfg<CYC_P_BF16X3> {
     static constexpr int NLEV = 2, NPASS = 3, NSTAGE = 6;
     static constexpr bool BF = true;
-    static constexpr int SUBN = 1 << 12;     // samples per TMEM chain (drift ~1.6e-5 against 1e-4)
+    static constexpr int SUBN = 1 << 13;     // samples per TMEM chain (drift ~1e-5 against 1e-4)
 };
 
 template <int PREC>
-__host__ __device__ constexpr int stage_bytes() { return Cfg<PREC>::NLEV * (P_BYTES + W_BYTES); }
+__host__ __device__ constexpr int stage_bytes() { return Cfg<PREC>::NLEV * LEVEL_BYTES; }
 template <int PREC>
 __host__ __device__ constexpr int xslots_off() { return Cfg<PREC>::NSTAGE * stage_bytes<PREC>(); }
 template <int PREC>
 __host__ __device__ constexpr int smem_bytes() { return xslots_off<PREC>() + 2 * XSLOT * 8 + 1024; }
+static_assert(smem_bytes<CYC_P_BF16X3>() <= 227 * 1024 && smem_bytes<CYC_P_FP16>() <= 227 * 1024, "shared memory");
 
 // ---- packing: 8 floats -> 16 bytes of FP16 / BF16 (+ BF16 remainders) --------------------
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -128,7 +136,7 @@ __device__ __forceinline__ uint32_t pack_b2(float a, float b, uint32_t* lo)
 }
 
 template <bool BF>
-__device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&hi)[4], uint32_t (&lo)[4])
+__device__ __forceinline__ void pack8(const float* v, uint32_t (&hi)[4], uint32_t (&lo)[4])
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -142,124 +150,130 @@ __device__ __forceinline__ void st16(unsigned char* p, const uint32_t (&v)[4])
     *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
+__device__ __forceinline__ uint32_t op_off(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * SBO + chunk * LBO + (row & 7) * 16);
+}
+
+// Named barrier `id` (1 + producer set) over the set's warps: every warp of a set passes it
+// once per stage of the set, whatever happened, so it can never wait for a warp that left.
+__device__ __forceinline__ void set_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "n"(SET_WARPS * 32) : "memory");
+}
+
 struct Bars {
-    uint64_t full[16];
-    uint64_t empty[16];
+    uint64_t full[12];
+    uint64_t empty[12];
     uint64_t xfull[2];
     uint64_t xempty[2];
     uint64_t done;
+    uint64_t tfree;
+    uint64_t fin;
     uint32_t tmem;
     int item;
-    int abort;
-    int add;                                    // this sub-item adds to the partial tile
-    int cmd;                                    // loop control: -1 stop, -2 next sub-item, >= 0 item
-    int64_t sub_end;                            // n_end of the whole item
+    int cmd;                                    // loop control: -1 stop, >= 0 item
+    volatile int abort;
     TcItem it;
 };
+static_assert(sizeof(Bars) <= 1024, "barrier block");
 
-// Columns c, c + 1 of one partial-tile row (only those below cmax exist), written or added.
-__device__ __forceinline__ void put2(float2* out, int c, float4 v, bool vec, int cmax, bool add)
+// Eight partial-tile columns c0 .. c0 + 7 of one row (only those below cmax exist), written
+// or added; the old values are all loaded before any store.
+__device__ __forceinline__ void put8(float2* out, int c0, const float (&v)[16], bool vec, int cmax, bool add)
 {
-    if (vec && c + 1 < cmax) {
-        float4* o = reinterpret_cast<float4*>(&out[c]);
+    if (vec && c0 + 7 < cmax) {
+        float4* o = reinterpret_cast<float4*>(out + c0);
+        float4 q[4];
         if (add) {
-            const float4 q = *o;
-            v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = o[k];
         }
-        *o = v;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 w = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            if (add) { w.x += q[k].x; w.y += q[k].y; w.z += q[k].z; w.w += q[k].w; }
+            o[k] = w;
+        }
         return;
     }
-    if (c < cmax) {
-        float2 w = make_float2(v.x, v.y);
-        if (add) { w.x += out[c].x; w.y += out[c].y; }
-        out[c] = w;
-    }
-    if (c + 1 < cmax) {
-        float2 w = make_float2(v.z, v.w);
-        if (add) { w.x += out[c + 1].x; w.y += out[c + 1].y; }
-        out[c + 1] = w;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (c0 + k < cmax) {
+            float2 w = make_float2(v[2 * k], v[2 * k + 1]);
+            if (add) { w.x += out[c0 + k].x; w.y += out[c0 + k].y; }
+            out[c0 + k] = w;
+        }
     }
 }
 
-// Epilogue warp (TMEM lane quadrant q): its 32 rows of the item's D tile into the FP32
-// partial tile.  Wide items: D columns r, r + 128 <-> tile columns 2r, 2r + 1; narrow items:
-// D column r <-> tile column r.  live = false writes zeros.
-__device__ __forceinline__ void drain_tile(uint32_t tmem, int q, int lane, const TcItem& it, bool narrow,
+// Epilogue warp (TMEM lane quadrant q) of CTA `rank`: its 32 weight rows of sub-tile `sub`
+// (accumulator `tbuf`) into the item's partial tile.  Lanes 2i and 2i + 1 hold the two rows
+// of one unit and swap their values by a shuffle.  live = false writes zeros.
+__device__ __forceinline__ void drain_tile(uint32_t tbuf, int q, int lane, const TcItem& it, int rank, int sub,
                                            bool live, bool add)
 {
-    const int row = q * 32 + lane;
+    const int rho = q * 32 + lane;
+    const int unit = it.u0 + sub * SUB_UNITS + rank * CTA_UNITS + (rho >> 1), h = rho & 1;
+    const int d = unit_row(unit, h, it.np, it.nself, it.U);
+    const int kind = unit >= it.U ? -1 : unit < it.np ? 0 : unit < it.np + (it.nself > 0 ? 1 : 0) ? 1 : 2;
     const bool vec = (it.out_stride & 1) == 0;
     const int cmax = it.ncols - it.c0;
-    float2* out = it.out + (size_t)row * it.out_stride;
-    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    const bool mine = it.u0 + row < it.Au;
-    if (it.x2 != nullptr) {
-        // dual item: D columns [0, 128) are the first stream's tile columns, [128, 256) the
-        // second stream's, rotated onto its own sample index
-        const float2 rot = mine ? phase_rot(it.phi[it.u0 + row], it.dphase) : make_float2(1.f, 0.f);
-        float2* out2 = it.out2 + (size_t)row * it.out_stride;
-        for (int cb = 0; cb < 16; ++cb) {
-            uint32_t dr0[8], di0[8], dr1[8], di1[8];
-            tc::tmem_ld8(lane_addr + TM_DR + cb * 8, dr0);
-            tc::tmem_ld8(lane_addr + TM_DI + cb * 8, di0);
-            tc::tmem_ld8(lane_addr + TM_DR + 128 + cb * 8, dr1);
-            tc::tmem_ld8(lane_addr + TM_DI + 128 + cb * 8, di1);
-            tc::tmem_ld_wait();
-            if (!mine) continue;
-#pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-                float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                              __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                put2(out, cb * 8 + j, v, vec, cmax, add);
-                const float ar = __uint_as_float(dr1[j]), ai = __uint_as_float(di1[j]);
-                const float br = __uint_as_float(dr1[j + 1]), bi = __uint_as_float(di1[j + 1]);
-                v = live ? make_float4(ar * rot.x - ai * rot.y, ar * rot.y + ai * rot.x,
-                                       br * rot.x - bi * rot.y, br * rot.y + bi * rot.x)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                put2(out2, cb * 8 + j, v, vec, cmax, add);
+    float2* out = d >= 0 ? it.out + (size_t)(d - it.d_lo) * it.out_stride : nullptr;
+    const uint32_t lane_addr = tbuf + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll 1
+        for (int s0 = 0; s0 < 32; s0 += 4) {
+            uint32_t pr0[4], pi0[4], pr1[4], pi1[4];
+            if (live) {
+                const uint32_t col = lane_addr + (uint32_t)(128 * r + s0);
+                tc::tmem_ld4(col, pr0);
+                tc::tmem_ld4(col + 32, pi0);
+                tc::tmem_ld4(col + 64, pr1);
+                tc::tmem_ld4(col + 96, pi1);
+                tc::tmem_ld_wait();
             }
-        }
-        return;
-    }
-    for (int cb = 0; cb < 16; ++cb) {
-        uint32_t dr0[8], di0[8], dr1[8], di1[8];
-        tc::tmem_ld8(lane_addr + TM_DR + cb * 8, dr0);
-        tc::tmem_ld8(lane_addr + TM_DI + cb * 8, di0);
-        if (!narrow) {
-            tc::tmem_ld8(lane_addr + TM_DR + 128 + cb * 8, dr1);
-            tc::tmem_ld8(lane_addr + TM_DI + 128 + cb * 8, di1);
-        }
-        tc::tmem_ld_wait();
-        if (!mine) continue;
-        if (narrow) {
+            float o[16];                        // tile columns 64 r + 2 s0 + 2 i + qq
 #pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-                const float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                                    __uint_as_float(dr0[j + 1]), __uint_as_float(di0[j + 1]))
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                put2(out, cb * 8 + j, v, vec, cmax, add);
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    const float own_r = live ? __uint_as_float(qq ? pr1[i] : pr0[i]) : 0.f;
+                    const float own_i = live ? __uint_as_float(qq ? pi1[i] : pi0[i]) : 0.f;
+                    const float oth_r = __shfl_xor_sync(0xffffffffu, own_r, 1);
+                    const float oth_i = __shfl_xor_sync(0xffffffffu, own_i, 1);
+                    const float trr = h ? oth_r : own_r, tri = h ? oth_i : own_i;
+                    const float tir = h ? own_r : oth_r, tii = h ? own_i : oth_i;
+                    float vr = own_r, vi = own_i;          // real unit: the row's own sums
+                    if (kind == 0 || kind == 2) {
+                        vr = h ? trr + tii : trr - tii;
+                        vi = h ? tri - tir : tri + tir;
+                    }
+                    o[4 * i + 2 * qq] = vr;
+                    o[4 * i + 2 * qq + 1] = vi;
+                }
             }
-            continue;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float4 v = live ? make_float4(__uint_as_float(dr0[j]), __uint_as_float(di0[j]),
-                                                __uint_as_float(dr1[j]), __uint_as_float(di1[j]))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-            put2(out, 2 * (cb * 8 + j), v, vec, cmax, add);
+            if (out) put8(out, 64 * r + 2 * s0, o, vec, cmax, add);
         }
     }
 }
 
-__device__ __forceinline__ void give_up(int* err, Bars* b, int code)
+struct Ctl {
+    int*      err;
+    long long budget;        // SM cycles per wait
+    int       withhold;      // test only: one producer arrival of CTA (0, 0, 0) is left out
+};
+
+__device__ __forceinline__ void give_up(const Ctl& ctl, Bars* b, int code, uint32_t crank)
 {
     b->abort = 1;
-    if (err) atomicCAS(err, 0, code);
+    tc::st_remote_s32((void*)&b->abort, crank ^ 1u, 1);      // the partner CTA of the pair
+    if (ctl.err) atomicCAS(ctl.err, 0, code);
 }
 
-// The item of CTA (bx, by, bz) for a single cyc_push pass.
-__device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, int bz)
+// The item of CTA pair (px, by, bz) for a single cyc_push pass.
+__device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int px, int by, int bz)
 {
     TcItem it;
     it.x = a.x;
@@ -272,40 +286,71 @@ __device__ __forceinline__ TcItem grid_item(const ProjArgs& a, int bx, int by, i
     it.phi = a.phi;
     it.col_lag = a.col_lag;
     it.col_conj = a.col_conj;
-    it.u0 = bx * BM;
-    it.c0 = by * BN;
-    it.Au = a.Au;
+    it.np = a.np;
+    it.nself = a.nself;
+    it.U = a.U;
+    it.u0 = px * ITEM_UNITS;
+    it.d_lo = unit_row(it.u0, 0, a.np, a.nself, a.U);
+    if (it.d_lo < 0) it.d_lo = 0;
+    it.c0 = by * TILE_CC;
     it.ncols = a.ncols;
     it.M = a.M;
-    it.out = a.part + ((size_t)bz * a.Au + (size_t)it.u0) * a.ncols + it.c0;
+    it.out = a.part + ((size_t)bz * a.Au + (size_t)it.d_lo) * a.ncols + it.c0;
     it.out_stride = a.ncols;
     it.y = a.y;
     it.D = a.D;
-    it.out_peer = 0;
-    it.x2 = nullptr;
-    it.xmask2 = 0;
-    it.n_beg2 = 0;
-    it.out2 = nullptr;
-    it.out_peer2 = 0;
-    it.dphase = 0;
     return it;
 }
 
-template <int PREC, bool LIST, bool PAIR>
+// Weights of one unit for the W warps: its two rows (real and imaginary part of
+// exp(-j 2 pi phi n / 2^64) for pairs and singles; W(0) = 1 and W(1/2) = (-1)^n, exactly, for
+// the real unit).
+struct UnitW {
+    uint64_t phi;
+    bool     live[2];
+    bool     real;            // the real unit: row h holds W of realphi[h]
+    uint64_t realphi[2];
+};
+
+__device__ __forceinline__ UnitW unit_weights(const TcItem& it, int unit)
+{
+    UnitW u;
+    u.phi = 0;
+    u.real = false;
+    u.live[0] = u.live[1] = unit < it.U;
+    u.realphi[0] = u.realphi[1] = 0;
+    const int nr = it.nself > 0 ? 1 : 0;
+    if (unit >= it.U) return u;
+    if (unit < it.np) {
+        u.phi = it.phi[2 * unit];
+    } else if (unit < it.np + nr) {
+        u.real = true;
+        u.live[1] = it.nself > 1;
+        u.realphi[0] = it.phi[2 * it.np];
+        u.realphi[1] = it.nself > 1 ? it.phi[2 * it.np + 1] : 0;
+    } else {
+        u.phi = it.phi[2 * it.np + it.nself + (unit - it.np - nr)];
+    }
+    return u;
+}
+
+template <int PREC, bool LIST>
 __global__ void __launch_bounds__(NTHREADS, 1)
-proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restrict__ nitems, int* counter, int* err)
+proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restrict__ nitems, int* counter, Ctl ctl)
 {
     using C = Cfg<PREC>;
+    constexpr int CG = C::SUBN / GS;                 // stages per chain
     extern __shared__ __align__(1024) unsigned char smem[];
     Bars* bars = reinterpret_cast<Bars*>(smem + xslots_off<PREC>() + 2 * XSLOT * 8);
     float2* xs = reinterpret_cast<float2*>(smem + xslots_off<PREC>());
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (!LIST) err = pa.err;
-    const uint32_t crank = PAIR ? tc::cluster_rank() : 0u;
+    const uint32_t crank = tc::cluster_rank();
+    const long long budget = ctl.budget;
+    const volatile int* ab = &bars->abort;
 
     if (tid == 0) {
         for (int s = 0; s < C::NSTAGE; ++s) {
-            tc::mbar_init(&bars->full[s], PAIR ? 2 * SET_WARPS : SET_WARPS);
+            tc::mbar_init(&bars->full[s], FULL_ARRIVALS);
             tc::mbar_init(&bars->empty[s], 1);
         }
         for (int k = 0; k < 2; ++k) {
@@ -313,77 +358,52 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
             tc::mbar_init(&bars->xempty[k], NSET * P_WARPS);
         }
         tc::mbar_init(&bars->done, 1);
+        tc::mbar_init(&bars->tfree, TFREE_ARRIVALS);
+        tc::mbar_init(&bars->fin, 1);
         bars->abort = 0;
-        bars->add = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == MMA_WARP) {
-        if constexpr (PAIR) tc::tmem_alloc_pair<512>(&bars->tmem);
-        else tc::tmem_alloc<512>(&bars->tmem);
-    }
+    if (warp == MMA_WARP) tc::tmem_alloc_pair<NSUB * TM_COLS>(&bars->tmem);
     tc::tc_fence_before();
     __syncthreads();
-    if constexpr (PAIR) tc::cluster_sync();        // the other CTA's barriers exist before any arrival
+    tc::cluster_sync();                              // the other CTA's barriers exist before any arrival
     tc::tc_fence_after();
     const uint32_t tmem = bars->tmem;
 
-    const int pset = warp < MMA_WARP ? warp / SET_WARPS : 0;
-    const int role = warp % SET_WARPS;              // 0-1 P, 2-5 W
-    uint32_t G = 0;                                 // groups this CTA has run (all items)
-    uint32_t Bk = 0;                                // sample blocks this CTA has staged
-    uint32_t nit = 0;                               // items this CTA has run
-    int lastb = -1;                                 // loader: last block issued (running count)
+    const int pset = warp < EPI_WARP ? warp / SET_WARPS : 0;
+    const int role = warp % SET_WARPS;               // 0-3 P, 4-7 W
+    uint32_t G = 0;                                  // stages this CTA has run (all items)
+    uint32_t Bk = 0;                                 // sample blocks this CTA has staged
+    uint32_t J = 0;                                  // accumulator chains this CTA has run
+    uint32_t nit = 0;                                // items this CTA has run
+    int lastb = -1;                                  // loader: last block issued (running count)
+    bool mma_issued = false;
 
     for (;;) {
-        // ---- next (sub-)item (thread 0 fetches; everybody reads it after the barrier) ----
-        // cmd: -1 stop, -2 the next sub-item of the current item, >= 0 a new item.  CTA pairs
-        // on an item list follow the even CTA's cmd, handed over through distributed shared
-        // memory, so that both always run the same items and the same number of iterations.
-        if (tid == 0 && (!(PAIR && LIST) || crank == 0)) {
+        // ---- next item (cmd -1: stop).  Pairs on an item list follow the even CTA's cmd,
+        // handed over through distributed shared memory, so that both always run the same
+        // items; in grid mode both CTAs of a pair derive the same item from the grid.
+        if (tid == 0 && (!LIST || crank == 0)) {
             int cmd = -1;
-            if (!bars->abort) {
-                if (nit > 0 && bars->it.n_end < bars->sub_end) {
-                    cmd = -2;
-                } else if (LIST) {
+            if (LIST) {
+                if (!bars->abort) {
                     cmd = atomicAdd(counter, 1);
                     if (cmd >= *nitems) cmd = -1;
-                } else if (nit == 0) {
-                    cmd = 0;
                 }
+                tc::st_remote_s32(&bars->cmd, 1, cmd);
+            } else if (nit == 0) {
+                cmd = 0;
             }
-            if constexpr (PAIR && LIST) tc::st_remote_s32(&bars->cmd, 1, cmd);
             bars->cmd = cmd;
         }
-        if constexpr (PAIR && LIST) tc::cluster_sync();
+        if constexpr (LIST) tc::cluster_sync();
         if (tid == 0) {
             const int cmd = bars->cmd;
-            int idx = -1;
-            if (cmd == -2) {
-                // the next sub-item of the current item: a fresh TMEM chain that adds
-                idx = bars->item;
-                bars->it.n_beg2 += bars->it.n_end - bars->it.n_beg;     // dual items advance in step
-                bars->it.n_beg = bars->it.n_end;
-                bars->add = 1;
-            } else if (cmd >= 0) {
-                idx = cmd;
-                bars->add = 0;
-                if constexpr (LIST) {
-                    bars->it = items[cmd];
-                    if (PAIR && crank == 1) {                  // the odd CTA's 128 rows
-                        bars->it.u0 += BM;
-                        bars->it.out += bars->it.out_peer;
-                        if (bars->it.out2) bars->it.out2 += bars->it.out_peer2;
-                    }
-                } else {
-                    bars->it = grid_item(pa, blockIdx.x, blockIdx.y, blockIdx.z);
-                }
-                bars->sub_end = bars->it.n_end;
+            if (cmd >= 0) {
+                if constexpr (LIST) bars->it = items[cmd];
+                else bars->it = grid_item(pa, blockIdx.x >> 1, blockIdx.y, blockIdx.z);
             }
-            if (idx >= 0) {
-                const int64_t e = bars->it.n_beg + C::SUBN;
-                bars->it.n_end = e < bars->sub_end ? e : bars->sub_end;
-            }
-            bars->item = idx;
+            bars->item = cmd;
         }
         tc::tc_fence_before();
         __syncthreads();
@@ -393,6 +413,7 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         const int64_t n_beg = it.n_beg, n_end = it.n_end;
         const int64_t span = n_end - n_beg;
         const int ngroups = span > 0 ? (int)((span + GS - 1) / GS) : 0;
+        const int nchains = (ngroups + CG - 1) / CG;
         const int mpad = (it.M + 1) & ~1;
         // a slot holds x[block start - xoff .. + XB + M] and, for a second input, y[block
         // start + D - yoff .. + XB] from YOFF on (both copies start at an even sample)
@@ -402,40 +423,26 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         const int YOFF = XB + mpad + 2;
         const int D = it.D;
         const int yoff = (int)((n_beg + D) & 1);
+        const int xoff = (int)(n_beg & 1);    // bulk copies start at an even sample (16-byte aligned)
         const int nblocks = (ngroups * GS + XB - 1) / XB;
-        // dual items: each CTA of the pair stages and forms the columns of its own stream
-        const bool dual = PAIR && LIST && it.x2 != nullptr;
-        const bool second = dual && crank == 1;
-        const float2* xsrc = second ? it.x2 : it.x;
-        const uint64_t xmsk = second ? it.xmask2 : it.xmask;
-        const int64_t nsrc = second ? it.n_beg2 : n_beg;    // this CTA's first sample of the range
-        const int xoff = (int)(nsrc & 1);     // bulk copies start at an even sample (16-byte aligned)
-        const bool narrow = !dual && it.ncols - it.c0 <= BN / 2;   // N = 128 MMAs, one column per P thread
 
-        if (warp < MMA_WARP && role < P_WARPS) {
+        if (warp < EPI_WARP && role < P_WARPS) {
             // -------------------------------------------------------- P warps (lag products)
-            const int t = (warp - pset * SET_WARPS) * 32 + lane;     // 0..127
-            const int c0 = it.c0, ncols = it.ncols;
-            // wide items: columns 2t, 2t+1 -> B rows t, t+128; narrow items: column t -> row t.
-            // CTA pairs hold B rows [N/2 rank, N/2 (rank + 1)): wide, thread t forms column
-            // 2t + rank (its B row t); narrow, threads t < 64 form column 64 rank + t.
-            // dual items: thread t forms column t of this CTA's stream (its B row t)
-            const int jA = dual ? t
-                         : PAIR ? (narrow ? (t < 64 ? 64 * (int)crank + t : ncols) : 2 * t + (int)crank)
-                                : (narrow ? t : 2 * t);
-            const int jB = 2 * t + 1;
-            const bool okA = c0 + jA < ncols, okB = !PAIR && !narrow && c0 + jB < ncols;
-            const int mA = okA ? it.col_lag[c0 + jA] : 0, mB = okB ? it.col_lag[c0 + jB] : 0;
-            const bool cjA = okA && it.col_conj[c0 + jA], cjB = okB && it.col_conj[c0 + jB];
-            const bool same_lag = okB && mA == mB;
-            const uint32_t offA = (t / 8) * P_SBO + (t % 8) * 16;             // B row t
-            const uint32_t offB = ((t + 128) / 8) * P_SBO + (t % 8) * 16;     // B row t + 128
-            bool run = true;
-            for (int b = 0; b < nblocks && run; ++b) {
+            // slot 32 sg + t: tile column 64 r + 2 t + sg, B rows (Pr, Pi) = (64 sg + t, 64 sg + 32 + t)
+            const int sg = role & 1, hk = role >> 1;                 // samples 8 hk .. 8 hk + 7
+            const int t = lane;
+            const int cA = it.c0 + 64 * (int)crank + 2 * t + sg;
+            const bool okA = cA < it.ncols;
+            const int mA = okA ? it.col_lag[cA] : 0;
+            const bool cjA = okA && it.col_conj[cA];
+            const uint32_t oR = NSUB * OPB + op_off(64 * sg + t, hk);
+            const uint32_t oI = NSUB * OPB + op_off(64 * sg + 32 + t, hk);
+            bool bad = false;
+            for (int b = 0; b < nblocks; ++b) {
                 const uint32_t bg = Bk + b;
-                if (!tc::mbar_wait(&bars->xfull[bg & 1], (bg >> 1) & 1, WAIT_BUDGET)) {
-                    give_up(err, bars, 4);
-                    break;
+                if (!bad && !tc::mbar_wait_ab<false>(&bars->xfull[bg & 1], (bg >> 1) & 1, budget, ab)) {
+                    give_up(ctl, bars, 4, crank);
+                    bad = true;
                 }
                 const float2* xsl = xs + (bg & 1) * XSLOT;
                 const int g_lo = b * (XB / GS), g_hi = min(ngroups, (b + 1) * (XB / GS));
@@ -443,186 +450,215 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
                     const uint32_t Gg = G + g;
                     if ((int)(Gg % NSET) != pset) continue;
                     const int s = Gg % C::NSTAGE;
-                    if (Gg >= (uint32_t)C::NSTAGE && !bwait<PAIR>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1)) {
-                        give_up(err, bars, 1);
-                        run = false;
-                        break;
+                    if (!bad && Gg >= (uint32_t)C::NSTAGE &&
+                        !tc::mbar_wait_ab<true>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, budget, ab)) {
+                        give_up(ctl, bars, 1, crank);
+                        bad = true;
                     }
-                    const float2* xb = xsl + xoff + (g * GS - b * XB);
-                    const float2* yb = cross ? xsl + YOFF + yoff + (g * GS - b * XB) : xb + D;
-                    const int64_t n = n_beg + (int64_t)g * GS;
-                    float prA[8], piA[8], prB[8], piB[8];
+                    if (!bad) {
+                        const int o = g * GS - b * XB + 8 * hk;
+                        const float2* xb = xsl + xoff + o;
+                        const float2* yb = cross ? xsl + YOFF + yoff + o : xb + D;
+                        const int64_t left = n_end - (n_beg + (int64_t)g * GS + 8 * hk);
+                        const int lim = okA ? (left < 8 ? (int)left : 8) : 0;   // samples of this chunk in range
+                        float pr[8], pi[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float2 pA = make_float2(0.f, 0.f), pB = make_float2(0.f, 0.f);
-                        if (n + i < n_end) {
-                            float2 x0 = yb[i];                  // reference sample y[n + D]
-                            float2 xa = okA ? xb[i + mA] : make_float2(0.f, 0.f);
-                            float2 xv = same_lag ? xa : (okB ? xb[i + mB] : make_float2(0.f, 0.f));
-                            if (okA) pA = lag_product(xa, x0, cjA);
-                            if (okB) pB = lag_product(xv, x0, cjB);
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 xv = xb[i + mA], y0 = yb[i];          // x[n + m], y[n + D]
+                            const float yi = cjA ? y0.y : -y0.y;
+                            const bool in = i < lim;
+                            pr[i] = in ? xv.x * y0.x - xv.y * yi : 0.f;
+                            pi[i] = in ? xv.x * yi + xv.y * y0.x : 0.f;
                         }
-                        prA[i] = pA.x; piA[i] = pA.y; prB[i] = pB.x; piB[i] = pB.y;
+                        unsigned char* st = smem + s * stage_bytes<PREC>();     // hi level
+                        uint32_t hv[4], lv[4];
+                        pack8<C::BF>(pr, hv, lv);
+                        st16(st + oR, hv);
+                        if (C::BF) st16(st + LEVEL_BYTES + oR, lv);
+                        pack8<C::BF>(pi, hv, lv);
+                        st16(st + oI, hv);
+                        if (C::BF) st16(st + LEVEL_BYTES + oI, lv);
+                        tc::fence_async_smem();
                     }
-                    unsigned char* st = smem + s * stage_bytes<PREC>();
-                    unsigned char* sl = st + P_BYTES + W_BYTES;             // lo level
-                    uint32_t h[4], l[4];
-                    pack8<C::BF>(prA, h, l);
-                    st16(st + offA, h);
-                    if (C::BF) st16(sl + offA, l);
-                    pack8<C::BF>(piA, h, l);
-                    st16(st + offA + P_LBO, h);
-                    if (C::BF) st16(sl + offA + P_LBO, l);
-                    if (!PAIR && !narrow) {
-                        pack8<C::BF>(prB, h, l);
-                        st16(st + offB, h);
-                        if (C::BF) st16(sl + offB, l);
-                        pack8<C::BF>(piB, h, l);
-                        st16(st + offB + P_LBO, h);
-                        if (C::BF) st16(sl + offB + P_LBO, l);
-                    }
-                    tc::fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) full_arrive<PAIR>(&bars->full[s]);
+                    set_sync(1 + pset);
                 }
                 __syncwarp();
-                if (run && lane == 0) tc::mbar_arrive(&bars->xempty[bg & 1]);
+                if (!bad && lane == 0) tc::mbar_arrive(&bars->xempty[bg & 1]);
             }
-        } else if (warp < MMA_WARP) {
+        } else if (warp < EPI_WARP) {
             // -------------------------------------------------------- W warps (weights)
-            const int row = (warp - pset * SET_WARPS - P_WARPS) * 32 + lane;   // 0..127
-            const bool ok = it.u0 + row < it.Au;
-            const uint64_t phi = ok ? it.phi[it.u0 + row] : 0ull;
+            const int wt = (role - P_WARPS) * 32 + lane;                 // 0..127
+            const int sub = wt >> 6, ui = wt & 63;
+            const UnitW uw = unit_weights(it, it.u0 + sub * SUB_UNITS + (int)crank * CTA_UNITS + ui);
             const uint64_t nb = it.nbase + (uint64_t)n_beg;
-            const uint32_t offW = (row / 8) * W_SBO + (row % 8) * 16;
-            // R_i = exp(-j 2 pi phi i / 2^64): the weights of a group are its anchor W_0 (from
-            // the exact u64 phase) times R_i, one sine/cosine pair per group instead of eight
-            float rr[8], ri[8];
+            // row 2 ui: Wr, row 2 ui + 1: Wi
+            const uint32_t ob = (uint32_t)sub * OPB;
+            const uint32_t oR0 = ob + op_off(2 * ui, 0), oR1 = ob + op_off(2 * ui, 1);
+            const uint32_t oI0 = ob + op_off(2 * ui + 1, 0), oI1 = ob + op_off(2 * ui + 1, 1);
+            // W(n0 + i) = W0 R_i with R_i = exp(-j 2 pi phi i / 2^64) and W0 the stage's anchor
+            // (exact u64 phase): one sine/cosine pair per stage and unit.  The real unit's rows
+            // are W(0) = 1 and W(1/2) = (-1)^n, formed exactly.
+            float rr[GS], ri[GS];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float2 r = phase_rot(phi, (uint64_t)i);
+            for (int i = 0; i < GS; ++i) {
+                const float2 r = phase_rot(uw.phi, (uint64_t)i);
                 rr[i] = r.x;
                 ri[i] = r.y;
             }
+            const bool arriver = role == P_WARPS && lane == 0;
+            bool bad = false;
             for (int g = 0; g < ngroups; ++g) {
                 const uint32_t Gg = G + g;
                 if ((int)(Gg % NSET) != pset) continue;
                 const int s = Gg % C::NSTAGE;
-                if (Gg >= (uint32_t)C::NSTAGE && !bwait<PAIR>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1)) {
-                    give_up(err, bars, 1);
+                if (!bad && Gg >= (uint32_t)C::NSTAGE &&
+                    !tc::mbar_wait_ab<true>(&bars->empty[s], ((Gg / C::NSTAGE) - 1) & 1, budget, ab)) {
+                    give_up(ctl, bars, 1, crank);
+                    bad = true;
+                }
+                if (!bad) {
+                    const uint64_t n = nb + (uint64_t)g * GS;
+                    unsigned char* st = smem + s * stage_bytes<PREC>();     // hi level
+                    uint32_t hv[4], lv[4];
+                    if (!uw.real) {
+                        const float2 w0 = uw.live[0] ? phase_rot(uw.phi, n) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            float re[8], im[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                re[k] = w0.x * rr[8 * half + k] - w0.y * ri[8 * half + k];
+                                im[k] = w0.x * ri[8 * half + k] + w0.y * rr[8 * half + k];
+                            }
+                            const uint32_t orr = half ? oR1 : oR0, oii = half ? oI1 : oI0;
+                            pack8<C::BF>(re, hv, lv);
+                            st16(st + orr, hv);
+                            if (C::BF) st16(st + LEVEL_BYTES + orr, lv);
+                            pack8<C::BF>(im, hv, lv);
+                            st16(st + oii, hv);
+                            if (C::BF) st16(st + LEVEL_BYTES + oii, lv);
+                        }
+                    } else {
+                        // W(0) = 1, W(1/2) = (-1)^n: exact in every format, the lo level is zero
+                        const bool odd = (n & 1) != 0;        // GS is even: sample i has parity odd ^ (i & 1)
+                        const uint32_t one = C::BF ? 0x3F80u : 0x3C00u, sgn = 0x8000u;
+                        uint32_t r0[4], r1[4], zero[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t a = one | (odd ? sgn : 0u), b = one | (odd ? 0u : sgn);
+                            const uint32_t alt = a | (b << 16);           // samples 2k, 2k + 1
+                            const uint32_t flat = one | (one << 16);
+                            r0[k] = uw.realphi[0] ? alt : flat;
+                            r1[k] = uw.live[1] ? (uw.realphi[1] ? alt : flat) : 0u;
+                        }
+                        st16(st + oR0, r0);
+                        st16(st + oR1, r0);
+                        st16(st + oI0, r1);
+                        st16(st + oI1, r1);
+                        if (C::BF) {
+                            st16(st + LEVEL_BYTES + oR0, zero);
+                            st16(st + LEVEL_BYTES + oR1, zero);
+                            st16(st + LEVEL_BYTES + oI0, zero);
+                            st16(st + LEVEL_BYTES + oI1, zero);
+                        }
+                    }
+                    tc::fence_async_smem();
+                }
+                set_sync(1 + pset);
+                const bool hold = ctl.withhold && !LIST && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
+                                  Gg == 0;
+                if (arriver && !hold && !*ab) tc::mbar_arrive_remote(&bars->full[s], 0);
+            }
+        } else if (warp < MMA_WARP) {
+            // -------------------------------------------------------- epilogue
+            const int q = warp & 3;
+            if (nchains == 0)
+                for (int sub = 0; sub < NSUB; ++sub) drain_tile(0, q, lane, it, (int)crank, sub, false, false);
+            for (int j = 0; j < nchains; ++j) {
+                const uint32_t Jg = J + j;
+                if (!tc::mbar_wait_ab<true>(&bars->done, Jg & 1, budget, ab)) {
+                    give_up(ctl, bars, 3, crank);
                     break;
                 }
-                float wr[8], wi[8];
-                if (ok) {
-                    const float2 w0 = phase_rot(phi, nb + (uint64_t)g * GS);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        wr[i] = w0.x * rr[i] - w0.y * ri[i];
-                        wi[i] = w0.x * ri[i] + w0.y * rr[i];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) { wr[i] = 0.f; wi[i] = 0.f; }
-                }
-                uint32_t rh[4], rl[4], ih[4], il[4], nh[4], nl[4];
-                pack8<C::BF>(wr, rh, rl);
-                pack8<C::BF>(wi, ih, il);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {           // -Wi: round-to-nearest is odd-symmetric
-                    nh[k] = ih[k] ^ 0x80008000u;
-                    nl[k] = il[k] ^ 0x80008000u;
-                }
-                unsigned char* st = smem + s * stage_bytes<PREC>() + P_BYTES;
-                st16(st + offW + 0 * W_LBO, ih);
-                st16(st + offW + 1 * W_LBO, rh);
-                st16(st + offW + 2 * W_LBO, nh);
-                if (C::BF) {
-                    unsigned char* sl = st + P_BYTES + W_BYTES;
-                    st16(sl + offW + 0 * W_LBO, il);
-                    st16(sl + offW + 1 * W_LBO, rl);
-                    st16(sl + offW + 2 * W_LBO, nl);
-                }
-                tc::fence_async_smem();
+                tc::tc_fence_after();
+                for (int sub = 0; sub < NSUB; ++sub)
+                    drain_tile(tmem + sub * TM_COLS, q, lane, it, (int)crank, sub, true, j > 0);
+                tc::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) full_arrive<PAIR>(&bars->full[s]);
+                if (lane == 0) tc::mbar_arrive_remote(&bars->tfree, 0);
             }
         } else if (warp == LOAD_WARP && lane == 0) {
             // -------------------------------------------------------- sample loader (TMA)
             for (int b = 0; b < nblocks; ++b) {
                 const uint32_t bg = Bk + b;
                 const int slot = bg & 1;
-                if (bg >= 2 && !tc::mbar_wait(&bars->xempty[slot], ((bg >> 1) - 1) & 1, WAIT_BUDGET)) {
-                    give_up(err, bars, 5);
+                if (bg >= 2 && !tc::mbar_wait_ab<false>(&bars->xempty[slot], ((bg >> 1) - 1) & 1, budget, ab)) {
+                    give_up(ctl, bars, 5, crank);
                     break;
                 }
-                const int64_t ns = nsrc + (int64_t)b * XB - xoff;    // even
+                const int64_t ns = n_beg + (int64_t)b * XB - xoff;        // even
                 int64_t cnt = ((int64_t)XB + mpad + xoff + 1) & ~(int64_t)1;
                 if (cnt > it.x_avail - ns) cnt = it.x_avail - ns;
                 int64_t ys = 0, ycnt = 0;
                 if (cross) {
-                    ys = n_beg + (int64_t)b * XB + D - yoff;          // even
+                    ys = n_beg + (int64_t)b * XB + D - yoff;              // even
                     ycnt = ((int64_t)XB + yoff + 1) & ~(int64_t)1;
                     if (ycnt > it.x_avail - ys) ycnt = it.x_avail - ys;
                 }
                 tc::mbar_arrive_expect_tx(&bars->xfull[slot], (uint32_t)((cnt + ycnt) * 8));
                 if (cross) tc::bulk_g2s(xs + slot * XSLOT + YOFF, it.y + ys, (uint32_t)(ycnt * 8), &bars->xfull[slot]);
-                const uint64_t pos = (uint64_t)ns & xmsk;
-                const uint64_t room = xmsk - pos + 1;           // samples before the ring wraps
-                if (xmsk == ~0ull || (uint64_t)cnt <= room) {
-                    tc::bulk_g2s(xs + slot * XSLOT, xsrc + pos, (uint32_t)(cnt * 8), &bars->xfull[slot]);
+                const uint64_t pos = (uint64_t)ns & it.xmask;
+                const uint64_t room = it.xmask - pos + 1;        // samples before the ring wraps
+                if (it.xmask == ~0ull || (uint64_t)cnt <= room) {
+                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(cnt * 8), &bars->xfull[slot]);
                 } else {
-                    tc::bulk_g2s(xs + slot * XSLOT, xsrc + pos, (uint32_t)(room * 8), &bars->xfull[slot]);
-                    tc::bulk_g2s(xs + slot * XSLOT + room, xsrc, (uint32_t)((cnt - room) * 8), &bars->xfull[slot]);
+                    tc::bulk_g2s(xs + slot * XSLOT, it.x + pos, (uint32_t)(room * 8), &bars->xfull[slot]);
+                    tc::bulk_g2s(xs + slot * XSLOT + room, it.x, (uint32_t)((cnt - room) * 8), &bars->xfull[slot]);
                 }
                 lastb = (int)bg;
             }
         } else if (warp == MMA_WARP && lane == 0 && crank == 0) {
             // -------------------------------------------------------- MMA issuer
-            const uint32_t idesc = tc::idesc_f16(PAIR ? 2 * BM : BM, narrow ? BN / 2 : BN, C::BF);
+            const uint32_t idesc = tc::idesc_f16(2 * ROWS, 2 * TILE_CC, C::BF);
             const uint32_t pbase = tc::smem_u32(smem);
-            for (int g = 0; g < ngroups; ++g) {
-                const uint32_t Gg = G + g;
-                const int s = Gg % C::NSTAGE;
-                if (!bwait<PAIR>(&bars->full[s], (Gg / C::NSTAGE) & 1)) {
-                    give_up(err, bars, 2);
+            bool stop = false;
+            for (int j = 0; j < nchains && !stop; ++j) {
+                const uint32_t Jg = J + j;
+                if (Jg >= 1 && !tc::mbar_wait_ab<true>(&bars->tfree, (Jg - 1) & 1, budget, ab)) {
+                    give_up(ctl, bars, 6, crank);
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t sb = pbase + s * stage_bytes<PREC>();
-#pragma unroll
-                for (int p = 0; p < C::NPASS; ++p) {
-                    const int la = (p == 2) ? 1 : 0, lb = (p == 1) ? 1 : 0;
-                    const uint32_t pb = sb + lb * (P_BYTES + W_BYTES);
-                    const uint32_t wb = sb + la * (P_BYTES + W_BYTES) + P_BYTES;
-                    const uint64_t bdesc = tc::smem_desc(pb, P_LBO, P_SBO);
-                    const uint64_t ar = tc::smem_desc(wb + 1 * W_LBO, W_LBO, W_SBO);
-                    const uint64_t ai = tc::smem_desc(wb + 0 * W_LBO, W_LBO, W_SBO);
-                    const uint32_t acc = (g > 0 || p > 0) ? 1u : 0u;
-                    if constexpr (PAIR) {
-                        tc::mma_f16_pair(tmem + TM_DR, ar, bdesc, idesc, acc);
-                        tc::mma_f16_pair(tmem + TM_DI, ai, bdesc, idesc, acc);
-                    } else {
-                        tc::mma_f16(tmem + TM_DR, ar, bdesc, idesc, acc);
-                        tc::mma_f16(tmem + TM_DI, ai, bdesc, idesc, acc);
+                const int g0 = j * CG, g1 = min(ngroups, g0 + CG);
+                for (int g = g0; g < g1; ++g) {
+                    const uint32_t Gg = G + g;
+                    const int s = Gg % C::NSTAGE;
+                    if (!tc::mbar_wait_ab<true>(&bars->full[s], (Gg / C::NSTAGE) & 1, budget, ab)) {
+                        give_up(ctl, bars, 2, crank);
+                        stop = true;
+                        break;
                     }
+                    tc::tc_fence_after();
+                    const uint32_t sb = pbase + s * stage_bytes<PREC>();
+#pragma unroll
+                    for (int p = 0; p < C::NPASS; ++p) {
+                        const int la = (p == 2) ? 1 : 0, lb = (p == 1) ? 1 : 0;
+                        const uint64_t bdesc = tc::smem_desc(sb + lb * LEVEL_BYTES + NSUB * OPB, LBO, SBO);
+#pragma unroll
+                        for (int sub = 0; sub < NSUB; ++sub) {
+                            const uint64_t adesc = tc::smem_desc(sb + la * LEVEL_BYTES + sub * OPB, LBO, SBO);
+                            tc::mma_f16_pair(tmem + sub * TM_COLS, adesc, bdesc, idesc, (g > g0 || p > 0) ? 1u : 0u);
+                        }
+                    }
+                    mma_issued = true;
+                    tc::mma_commit_pair(&bars->empty[s], 3);
                 }
-                if constexpr (PAIR) tc::mma_commit_pair(&bars->empty[s], 3);
-                else tc::mma_commit(&bars->empty[s]);
+                if (!stop) tc::mma_commit_pair(&bars->done, 3);
             }
-            if constexpr (PAIR) tc::mma_commit_pair(&bars->done, 3);
-            else tc::mma_commit(&bars->done);
-        }
-
-        // ------------------------------------------------------------ epilogue (set 0 W warps)
-        if (warp >= P_WARPS && warp < SET_WARPS) {
-            const bool got = bwait<PAIR>(&bars->done, nit & 1);
-            if (!got) give_up(err, bars, 3);
-            tc::tc_fence_after();
-            const bool live = got && ngroups > 0 && !bars->abort;
-            drain_tile(tmem, warp & 3, lane, it, narrow, live, bars->add != 0);
         }
         G += ngroups;
         Bk += nblocks;
+        J += nchains;
         ++nit;
         // everybody is done with this item's descriptor before thread 0 replaces it
         tc::tc_fence_before();
@@ -630,101 +666,63 @@ proj_tc_kernel(ProjArgs pa, const TcItem* __restrict__ items, const int* __restr
         tc::tc_fence_after();
     }
 
-    // no sample copy may still be landing when the CTA exits
+    // no sample copy may still be landing and no MMA still running when the CTAs exit
+    // (these waits ignore the abort flag: the copies and MMAs complete on their own)
     if (warp == LOAD_WARP && lane == 0)
         for (int b = lastb > 0 ? lastb - 1 : 0; b <= lastb; ++b)
-            if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, WAIT_BUDGET);
+            if (b >= 0) tc::mbar_wait(&bars->xfull[b & 1], (b >> 1) & 1, budget);
+    if (warp == MMA_WARP && lane == 0 && crank == 0 && mma_issued) {
+        tc::mma_commit_pair(&bars->fin, 1);
+        tc::mbar_wait(&bars->fin, 0, budget);
+    }
     tc::tc_fence_before();
     __syncthreads();
-    if constexpr (PAIR) tc::cluster_sync();        // no MMA of the pair still reads this CTA
+    tc::cluster_sync();                              // no MMA of the pair still uses this CTA
     if (warp == MMA_WARP) {
         tc::tc_fence_after();
-        if constexpr (PAIR) tc::tmem_dealloc_pair<512>(tmem);
-        else tc::tmem_dealloc<512>(tmem);
+        tc::tmem_dealloc_pair<NSUB * TM_COLS>(tmem);
     }
 }
 
-int tiles_of(int Au, int ncols) { return ((Au + BM - 1) / BM) * ((ncols + BN - 1) / BN); }
-
-template <int PREC, bool LIST, bool PAIR>
+template <int PREC, bool LIST>
 cudaError_t set_smem()
 {
     static bool done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC, LIST, PAIR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<PREC>());
+    cudaError_t e = cudaFuncSetAttribute(proj_tc_kernel<PREC, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes<PREC>());
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-template <int PREC>
-cudaError_t launch_grid(const ProjArgs& a, bool pair, cudaStream_t st)
+template <int PREC, bool LIST>
+cudaError_t launch_pairs(dim3 grid, const ProjArgs& a, const TcItem* items, const int* nitems, int* counter,
+                         const Ctl& ctl, cudaStream_t st)
 {
-    int gx = (a.Au + BM - 1) / BM;
-    const dim3 block(NTHREADS);
-    if (pair) {
-        cudaError_t e = set_smem<PREC, false, true>();
-        if (e != cudaSuccess) return e;
-        gx = (gx + 1) & ~1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(gx, (a.ncols + BN - 1) / BN, a.nsplit);
-        cfg.blockDim = block;
-        cfg.dynamicSmemBytes = smem_bytes<PREC>();
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, proj_tc_kernel<PREC, false, true>, a, (const TcItem*)nullptr,
-                                  (const int*)nullptr, (int*)nullptr, (int*)nullptr);
-    }
-    cudaError_t e = set_smem<PREC, false, false>();
+    cudaError_t e = set_smem<PREC, LIST>();
     if (e != cudaSuccess) return e;
-    dim3 grid(gx, (a.ncols + BN - 1) / BN, a.nsplit);
-    proj_tc_kernel<PREC, false, false><<<grid, block, smem_bytes<PREC>(), st>>>(a, nullptr, nullptr, nullptr, nullptr);
-    return cudaGetLastError();
-}
-
-template <int PREC>
-cudaError_t launch_list(const TcItem* items, const int* nitems, int* counter, int grid, bool pair, int* err,
-                        cudaStream_t st)
-{
-    ProjArgs none;
-    none.x = nullptr; none.nc = 0; none.nbase = 0; none.phi = nullptr; none.Au = 0; none.col_lag = nullptr;
-    none.col_conj = nullptr; none.ncols = 0; none.nsplit = 0; none.split_len = 0; none.part = nullptr;
-    if (pair) {
-        cudaError_t e = set_smem<PREC, true, true>();
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((grid + 1) & ~1);
-        cfg.blockDim = dim3(NTHREADS);
-        cfg.dynamicSmemBytes = smem_bytes<PREC>();
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, proj_tc_kernel<PREC, true, true>, none, items, nitems, counter, err);
-    }
-    cudaError_t e = set_smem<PREC, true, false>();
-    if (e != cudaSuccess) return e;
-    proj_tc_kernel<PREC, true, false><<<grid, NTHREADS, smem_bytes<PREC>(), st>>>(none, items, nitems, counter, err);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem_bytes<PREC>();
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, proj_tc_kernel<PREC, LIST>, a, items, nitems, counter, ctl);
 }
 
 // CTA pairs that can be resident at once (0: cluster launches unavailable).
 template <int PREC>
 int pair_slots()
 {
-    if (set_smem<PREC, false, true>() != cudaSuccess) return 0;
+    if (set_smem<PREC, false>() != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, 1, 1);
     cfg.blockDim = dim3(NTHREADS);
@@ -737,19 +735,28 @@ int pair_slots()
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, proj_tc_kernel<PREC, false, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, proj_tc_kernel<PREC, false>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
+ProjArgs empty_args()
+{
+    ProjArgs none;
+    none.x = nullptr; none.nc = 0; none.nbase = 0; none.phi = nullptr; none.Au = 0; none.col_lag = nullptr;
+    none.col_conj = nullptr; none.ncols = 0; none.nsplit = 0; none.split_len = 0; none.part = nullptr;
+    return none;
+}
+
 }  // namespace
 
 bool tc_supported(int ncols, int M) { return ncols > 0 && M >= 0 && M <= MAX_LAG; }
 
-int tc_tile_rows() { return BM; }
-int tc_tile_cols() { return BN; }
+int tc_pair_units() { return ITEM_UNITS; }
+int tc_tile_cols() { return TILE_CC; }
+int tc_tile_rows() { return 2 * ITEM_UNITS; }
 
 int tc_pair_ctas(int precision)
 {
@@ -758,19 +765,20 @@ int tc_pair_ctas(int precision)
     return 2 * n;
 }
 
-ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
+// CTAs per split: two per (unit tile, column tile).
+static int tc_ctas(int U, int ncols)
 {
-    int tiles = tiles_of(Au, ncols);
-    int slots = num_sms;
-    if (pair_ctas > 0) {            // x tiles rounded up to whole pairs
-        const int tx = (Au + BM - 1) / BM;
-        tiles = ((tx + 1) & ~1) * ((ncols + BN - 1) / BN);
-        slots = pair_ctas < num_sms ? pair_ctas : num_sms;
-    }
+    return 2 * ((U + ITEM_UNITS - 1) / ITEM_UNITS) * ((ncols + TILE_CC - 1) / TILE_CC);
+}
+
+ProjPlan tc_plan(int U, int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
+{
+    const int tiles = tc_ctas(U, ncols);
+    const int slots = pair_ctas < num_sms ? pair_ctas : num_sms;
     // splits of at least 2048 samples, within what the partial buffer holds
-    int smax = max_splits(tiles_of(Au, ncols), num_sms, Au, ncols);
+    int smax = max_splits(tiles, num_sms, Au, ncols);
     if ((int64_t)smax > nc / 2048) smax = (int)(nc / 2048);
-    const int want = wave_splits(tiles, slots, smax);
+    const int want = wave_splits(tiles, slots > 0 ? slots : 1, smax);
     int64_t len = (nc + want - 1) / want;
     if (len < 256) len = 256;
     len = (len + GS - 1) / GS * GS;
@@ -781,23 +789,31 @@ ProjPlan tc_plan(int Au, int ncols, int64_t nc, int num_sms, int pair_ctas)
     return p;
 }
 
-size_t tc_max_partials(int Au, int ncols, int num_sms)
+size_t tc_max_partials(int U, int Au, int ncols, int num_sms)
 {
-    return (size_t)max_splits(tiles_of(Au, ncols), num_sms, Au, ncols) * (size_t)Au * (size_t)ncols;
+    return (size_t)max_splits(tc_ctas(U, ncols), num_sms, Au, ncols) * (size_t)Au * (size_t)ncols;
 }
 
-cudaError_t tc_launch(const ProjArgs& a, int precision, bool pair, cudaStream_t st)
+cudaError_t tc_launch(const ProjArgs& a, int precision, cudaStream_t st)
 {
-    if (precision == CYC_P_FP16) return launch_grid<CYC_P_FP16>(a, pair, st);
-    if (precision == CYC_P_BF16X3) return launch_grid<CYC_P_BF16X3>(a, pair, st);
+    const dim3 grid(2 * ((a.U + ITEM_UNITS - 1) / ITEM_UNITS), (a.ncols + TILE_CC - 1) / TILE_CC, a.nsplit);
+    const Ctl ctl{a.err, a.budget > 0 ? a.budget : kDefaultWaitBudget, a.withhold};
+    if (precision == CYC_P_FP16)
+        return launch_pairs<CYC_P_FP16, false>(grid, a, nullptr, nullptr, nullptr, ctl, st);
+    if (precision == CYC_P_BF16X3)
+        return launch_pairs<CYC_P_BF16X3, false>(grid, a, nullptr, nullptr, nullptr, ctl, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision,
-                            bool pair, int* err, cudaStream_t st)
+cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, int* err,
+                            long long budget, cudaStream_t st)
 {
-    if (precision == CYC_P_FP16) return launch_list<CYC_P_FP16>(items, nitems, counter, grid, pair, err, st);
-    if (precision == CYC_P_BF16X3) return launch_list<CYC_P_BF16X3>(items, nitems, counter, grid, pair, err, st);
+    const Ctl ctl{err, budget > 0 ? budget : kDefaultWaitBudget, 0};
+    const dim3 g((grid + 1) & ~1);
+    if (precision == CYC_P_FP16)
+        return launch_pairs<CYC_P_FP16, true>(g, empty_args(), items, nitems, counter, ctl, st);
+    if (precision == CYC_P_BF16X3)
+        return launch_pairs<CYC_P_BF16X3, true>(g, empty_args(), items, nitems, counter, ctl, st);
     return cudaErrorInvalidValue;
 }
 

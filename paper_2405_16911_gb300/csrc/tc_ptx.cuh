@@ -104,6 +104,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr));
 }
 
+// 32 lanes x 4 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- mbarriers ----------------------------------------------------------------------------
@@ -118,12 +126,16 @@ __device__ __forceinline__ void mbar_arrive(void* bar)
                  :: "r"(smem_u32(bar)) : "memory");
 }
 
+// The waiting thread is suspended until the phase completes or kSuspendNs pass, so that
+// waiting warps do not take issue slots from the producers by polling.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_try_wait(void* bar, uint32_t parity)
 {
     uint32_t ok;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
                  "selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs) : "memory");
     return ok != 0;
 }
 
@@ -137,6 +149,13 @@ __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, long long 
         if (clock64() - t0 > budget) return false;
     return true;
 }
+
+// Bounded wait that also gives up as soon as the word *abort (shared memory) is non-zero:
+// once one role of a CTA (or of its pair partner) has given up, every other wait of the
+// kernel fails at its next poll instead of spending its own budget.  CL: cluster-scope
+// acquire (arrivals or commits that come from the other CTA of a pair).
+template <bool CL>
+__device__ __forceinline__ bool mbar_wait_ab(void* bar, uint32_t parity, long long budget, const volatile int* abort);
 
 // Arrive once and add `bytes` to the transaction count the current phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(void* bar, uint32_t bytes)
@@ -223,9 +242,9 @@ __device__ __forceinline__ void st_remote_s32(void* p, uint32_t rank, int v)
 __device__ __forceinline__ bool mbar_try_wait_cluster(void* bar, uint32_t parity)
 {
     uint32_t ok;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
                  "selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs) : "memory");
     return ok != 0;
 }
 
@@ -237,6 +256,19 @@ __device__ __forceinline__ bool mbar_wait_cluster(void* bar, uint32_t parity, lo
     while (!mbar_try_wait_cluster(bar, parity))
         if (clock64() - t0 > budget) return false;
     return true;
+}
+
+template <bool CL>
+__device__ __forceinline__ bool mbar_wait_ab(void* bar, uint32_t parity, long long budget, const volatile int* abort)
+{
+    auto ready = [&]() { return CL ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
+    if (ready()) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (ready()) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > budget) return false;
+    }
 }
 
 }  // namespace tc

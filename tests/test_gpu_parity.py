@@ -271,27 +271,27 @@ def test_fp32_small_and_general_paths(cyc, na):
 
 
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16"])
-def test_pair_and_single_tensor_core_kernels(cyc, precision, monkeypatch):
-    """cyc_push runs the tensor-core projection as two-CTA pairs by default and as single
-    CTAs with CYC_TC_PAIR=0: both against the oracle on wide items with an odd number of
-    cycle-frequency tiles, narrow items, two column tiles, and tile counts that run single
-    CTAs either way."""
-    # 5 tiles (pairs with one empty partner), 2 tiles narrow, 2 tiles over two column ranges,
-    # 1 and 3 tiles (one CTA per tile even when pairs are on)
-    cases = [(9001, np.arange(128), 600), (7003, np.arange(41), 130), (6007, np.arange(200), 129),
-             (5003, np.arange(64), 100), (4001, np.arange(100), 300)]
-    for i, (T, lags, na) in enumerate(cases):
+def test_tensor_core_unit_kinds(cyc, precision):
+    """The tensor-core projection takes a and -a together (one pair of weight rows), 0 and
+    1/2 as one unit of real rows, and every other a alone: symmetric grids, grids without
+    a = 0 or 1/2, one-sided random sets, their mix with duplicates and aliases, several
+    units tiles (pairs of CTAs, the odd CTA sometimes empty), two column tiles and a ragged
+    last column tile, all against the oracle."""
+    rng = np.random.default_rng(40)
+    cases = [
+        (9001, np.arange(128), -0.5 + np.arange(512) / 512),                 # 255 pairs + {0, 1/2}
+        (7003, np.arange(41), (np.arange(130) - 64.5) / 130),                # 65 pairs, no self-conjugate a
+        (6007, np.arange(200), rng.uniform(0.01, 0.49, 129)),                # 129 singles, 2 column tiles
+        (5003, np.arange(64), np.concatenate([[0.0], rng.uniform(-0.5, 0.5, 40), [0.5]])),
+        (4001, np.arange(100), np.concatenate([-0.5 + np.arange(300) / 300, [0.25, 1.25, -0.75, 0.1]])),
+        (3001, np.array([0, 3, 1, 3, 17]), np.array([0.5, -0.5, 0.0, 1.0, 0.3, -0.3, 0.7])),
+    ]
+    for i, (T, lags, alphas) in enumerate(cases):
         x = synth.white(T, seed=120 + i).astype(np.complex64)
-        alphas = np.random.default_rng(20 + i).uniform(-0.5, 0.5, na)
         Ro, no = oracle.estimate(x, lags, alphas)
-        out = {}
-        for pair in ("1", "0"):
-            monkeypatch.setenv("CYC_TC_PAIR", pair)
-            R, neff = run_gpu(cyc, x, lags, alphas, precision=precision, chunks=[T // 3, T - T // 3])
-            assert neff == no
-            assert rel_err(R, Ro, x, int(lags.max())) < TOL[precision], (i, pair)
-            out[pair] = R
-        assert rel_err(out["1"], out["0"], x, int(lags.max())) < TOL[precision] / 10
+        R, neff = run_gpu(cyc, x, lags, alphas, precision=precision, chunks=[T // 3, T - T // 3])
+        assert neff == no
+        assert rel_err(R, Ro, x, int(lags.max())) < TOL[precision], i
 
 
 @pytest.mark.parametrize("precision", PRECS)

@@ -33,12 +33,11 @@ def stream_case(i):
     return dict(lags=lags, alphas=alphas, forms=forms, n0=n0, x=x, chunks=chunks)
 
 
-@pytest.mark.parametrize("pair", ["1", "0"])
 @pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("fp16", 1e-2)])
-def test_mix_equals_alone(cyc, precision, tol, pair, monkeypatch):
-    """pair = "1": items run on two-CTA pairs (the default where the GPU holds such clusters);
-    "0": one CTA per item (CYC_TC_PAIR=0)."""
-    monkeypatch.setenv("CYC_TC_PAIR", pair)
+def test_mix_equals_alone(cyc, precision, tol):
+    """Twelve streams of different lags, cycle frequencies, forms, start indices and chunkings
+    in one server: each stream's result equals the same stream run alone through cyc_push,
+    and the oracle's."""
     cases = [stream_case(i) for i in range(12)]
     with cyc.Server(max_streams=16, precision=precision, item_samples=4096) as srv:
         sids = [srv.open(c["lags"], c["alphas"], c["forms"], c["n0"]) for c in cases]
@@ -137,10 +136,9 @@ def test_ring_backpressure_and_concurrent_submitters(cyc):
 
 @pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("fp16", 1e-2)])
 def test_streams_sharing_a_configuration(cyc, precision, tol):
-    """Nine streams with the same cycle frequencies, lags and forms (64 lags x 2 forms: dual
-    items on CTA pairs, one CTA pair forming two streams' columns with one set of weights,
-    the second stream rotated onto its own sample index) and different start indices and
-    chunkings: each stream's result equals the same stream run alone, and the oracle's."""
+    """Nine streams with the same symmetric cycle-frequency grid (pairs a, -a and the real
+    unit), lags and forms (64 lags x 2 forms: one column tile) and different start indices
+    and chunkings: each stream's result equals the same stream run alone, and the oracle's."""
     lags = np.arange(64)
     alphas = -0.5 + np.arange(300) / 300.0
     rng = np.random.default_rng(77)
