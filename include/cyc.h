@@ -66,12 +66,10 @@ extern "C" {
 #define CYC_P_FP32   0       /* FP32 CUDA-core complex GEMM, FP32 accumulate */
 #define CYC_P_FP16   1       /* tensor cores, FP16 operands, one pass, FP32 accumulate */
 #define CYC_P_BF16X3 2       /* tensor cores, BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
-/* The tensor-core passes of cyc_push run on pairs of SMs (two-CTA clusters issuing
- * cta_group::2 MMAs, each pair taking two 128-row cycle-frequency tiles) when the device can
- * hold such clusters and the distinct cycle frequencies fill an even number of tiles or at
- * least five; the environment variable
- * CYC_TC_PAIR=0, read when a stream is created, selects the one-CTA kernel instead.  Both
- * compute the same products in the same order of terms per tile. */
+/* The tensor-core precisions run on pairs of SMs (two-CTA clusters issuing cta_group::2
+ * MMAs); a device that cannot hold such clusters reports CYC_ENOTSUP for them.  A cycle
+ * frequency a and its negative -a (mod 1), when both are in a stream's list, share one pair
+ * of real weight rows and cost the tensor work of one; 0 and 1/2 share one more. */
 
 typedef struct cyc_stream cyc_stream;   /* opaque, owned by the library */
 
@@ -182,6 +180,28 @@ CYC_API int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_
 CYC_API int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out);
 
 /*
+ * cyc_detect: cycle-frequency estimation (the paper's next step, Sec. 6) on the stream's
+ * current estimate R (as cyc_read would return it), per form, reading the stream's cycle-
+ * frequency list as a circular grid in the order given (the uniform grid -1/2 + k/A is the
+ * intended use).  A constant-false-alarm rule:
+ *   s(a)   = max over lags m of |R^a(m)|^2; 0 for the conventional form at a = 0 (mod 1, in
+ *            the fixed point of cyc_phase_increment) of a one-input stream, whose entry is
+ *            the signal's power
+ *   nu(a)  = median of s over the list positions a +- 2 .. a +- win (indices modulo nalphas;
+ *            the mean of the two middle values of the 2 (win - 1))
+ *   flags[f][a] bit 1 (value 2): s(a) >= s(a - 1) and s(a) >= s(a + 1)  (a local maximum)
+ *   flags[f][a] bit 0 (value 1): a local maximum with s(a) > kappa * nu(a)  (detected)
+ *   ratio[f][a] = s(a) / nu(a) (nu floored at 1e-300), FP32
+ * kappa > 0 (8.4 gives about 1e-3 false alarms per signal on 512 a x 64 lags x 2 forms of
+ * the serving mix of modulated signals); win in [2, 32] (16 is the usual choice).  flags
+ * ([F][nalphas] bytes) and ratio ([F][nalphas] floats, may be NULL) are host or device
+ * memory of the stream's device; *ndetected (optional) receives the number of detections.
+ * Synchronous.  CYC_ENODATA when N_eff is 0.  Device scratch of F * nalphas * 13 bytes is
+ * kept with the stream after the first call.
+ */
+CYC_API int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* ratio, int32_t* ndetected);
+
+/*
  * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
  * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
  * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read
@@ -257,7 +277,8 @@ CYC_API int cyc_phase_increment(double a, uint64_t* phi);
  * (admitted only if their device memory fits the budget and a slot is free), chunks are
  * submitted from any thread, and the engine repeatedly forms a batch from every open
  * stream that has new samples: the new committed n-range of each stream becomes work
- * items (128 cycle frequencies x 128 columns x at most item_samples terms) for one
+ * items (up to 512 cycle frequencies -- 256 pairs a, -a -- x 128 columns x at most
+ * item_samples terms) for one
  * persistent tensor-core kernel, followed by an FP64 fold into each stream's sums, both
  * replayed from a captured CUDA graph.  Chunks that arrive while a batch runs join the
  * next one, so streams of very different rates share the GPU.  Each stream computes the
@@ -270,7 +291,7 @@ typedef struct cyc_server_params {
     int32_t  precision;     /* CYC_P_BF16X3 or CYC_P_FP16 */
     uint64_t mem_budget;    /* device bytes for stream state; 0 selects half the free memory */
     int64_t  ring_samples;  /* per-stream sample ring (rounded up to a power of two); 0: 1 << 22 */
-    int32_t  max_items;     /* work items per batch; 0 selects 4096 */
+    int32_t  max_items;     /* work items per batch; 0 selects 1024 (512 KiB of partials each) */
     int64_t  item_samples;  /* committed terms per work item at most; 0 selects 65536 */
     int32_t  device;        /* CUDA device ordinal */
 } cyc_server_params;
@@ -293,10 +314,7 @@ CYC_API int cyc_server_create(const cyc_server_params* p, cyc_server** out);
 CYC_API int cyc_server_destroy(cyc_server* srv);
 
 /* Open a stream (lags >= 0, max lag <= 2560; arrays copied).  CYC_EAGAIN when no slot is
- * free or its device memory would exceed the budget: retry after a close.  Streams opened
- * with the same lags, cycle frequencies and forms, at most 128 columns (lags x forms), may
- * share work items: two such streams' equal spans of new samples run on one pair of SMs
- * with one set of weights (the results are each stream's own). */
+ * free or its device memory would exceed the budget: retry after a close. */
 CYC_API int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const double* alphas,
                             int nalphas, int conj_flag, int64_t n0, int* sid);
 

@@ -34,8 +34,10 @@ def hann(n: int = NFFT) -> np.ndarray:
     return 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(n) / n)
 
 
-def features(x, nseg: int = NSEG, nfft: int = NFFT, eps: float = 1e-12) -> np.ndarray:
-    """[NIN][nfft] float64 standardised log spectra (see module doc)."""
+def welch(x, nseg: int = NSEG, nfft: int = NFFT) -> np.ndarray:
+    """[NIN][nfft] float64: the mean over nseg consecutive segments of nfft samples of the
+    periodogram |FFT(y w)|^2 (Hann window w, no other scaling, FFT bin order) of each channel
+    y: x, x^2 and the lag products x[n+d] conj(x[n])."""
     x = np.asarray(x, dtype=np.complex128)
     assert x.size >= nseg * nfft + max(LAG_CHANNELS)
     w = hann(nfft)
@@ -47,7 +49,12 @@ def features(x, nseg: int = NSEG, nfft: int = NFFT, eps: float = 1e-12) -> np.nd
         for c, y in enumerate(ys):
             Y = np.fft.fft(y * w)
             out[c] += np.abs(Y) ** 2
-    out = np.log10(out / nseg + eps)
+    return out / nseg
+
+
+def features(x, nseg: int = NSEG, nfft: int = NFFT, eps: float = 1e-12) -> np.ndarray:
+    """[NIN][nfft] float64 standardised log spectra (see module doc)."""
+    out = np.log10(welch(x, nseg, nfft) + eps)
     out = np.roll(out, nfft // 2, axis=1)                 # bin j <-> frequency -1/2 + j/nfft
     mu = out.mean(axis=1, keepdims=True)
     sd = out.std(axis=1, keepdims=True)

@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "cyc_create_full": ([P, I32, I, P], I),
         "cyc_read_windows": ([P, P, I64, P, P], I),
         "cyc_read_spectrum": ([P, I32, I32, P], I),
+        "cyc_detect": ([P, ctypes.c_double, I32, P, P, P], I),
         "cyc_push": ([P, P, I64, I], I),
         "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
@@ -265,6 +266,25 @@ def cyc_read_spectrum(h: int, Q: int, taper: int = 0, out=None):
         raise ValueError("output buffer too small")
     _check(load().cyc_read_spectrum(h, int(Q), int(taper), addr))
     return out
+
+
+def cyc_detect(h: int, kappa: float = 8.4, win: int = 16, flags=None, ratio=None):
+    """Cycle-frequency detection on the stream's estimate: (flags [F][A] uint8 -- bit 0
+    detected, bit 1 local maximum --, ratio [F][A] float32 or None, number detected).
+    `flags` / `ratio` may be torch tensors or numpy arrays (host or device); by default new
+    numpy arrays."""
+    F, A, L = cyc_shape(h)
+    if flags is None:
+        flags = np.empty((F, A), dtype=np.uint8)
+    if ratio is None:
+        ratio = np.empty((F, A), dtype=np.float32)
+    faddr, fn, _d1, _k1 = _ptr_info(flags)
+    raddr, rn, _d2, _k2 = _ptr_info(ratio) if ratio is not False else (None, None, None, None)
+    if (fn is not None and fn < F * A) or (rn is not None and rn < F * A * 4):
+        raise ValueError("output buffer too small")
+    nd = ctypes.c_int32(0)
+    _check(load().cyc_detect(h, float(kappa), int(win), faddr, raddr, ctypes.byref(nd)))
+    return flags, (None if ratio is False else ratio), int(nd.value)
 
 
 def cyc_read(h: int, out=None):
@@ -607,6 +627,9 @@ class Stream:
 
     def read_spectrum(self, Q: int, taper: int = 0, out=None):
         return cyc_read_spectrum(self.h, Q, taper, out)
+
+    def detect(self, kappa: float = 8.4, win: int = 16, flags=None, ratio=None):
+        return cyc_detect(self.h, kappa, win, flags, ratio)
 
     def sync(self):
         cyc_sync(self.h)

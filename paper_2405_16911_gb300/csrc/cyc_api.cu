@@ -133,6 +133,12 @@ struct cyc_stream {
     double2* sp_E = nullptr;        // DFT matrix [L][sp_Q]
     double2* sp_S = nullptr;        // spectrum [F][A][sp_Q] for host outputs
     int sp_Q = 0;
+    // cycle-frequency detection (cyc_detect), allocated on first use
+    double* dt_s = nullptr;         // statistic [F][A]
+    uint8_t* dt_flags = nullptr;    // [F][A] for host outputs
+    float* dt_ratio = nullptr;      // [F][A] for host outputs
+    uint8_t* dt_dc = nullptr;       // [A] 1 where the conventional a = 0 entry is left out
+    int* dt_count = nullptr;
     std::vector<double> alphas;
     int A = 0;
     std::vector<uint64_t> phi_u;
@@ -176,7 +182,8 @@ struct cyc_stream {
     {
         free_events();
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
-                      part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S};
+                      part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S,
+                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
@@ -188,6 +195,7 @@ struct cyc_stream {
         d_lags = nullptr;
         sp_E = sp_S = nullptr;
         sp_Q = 0;
+        dt_s = nullptr; dt_flags = nullptr; dt_ratio = nullptr; dt_dc = nullptr; dt_count = nullptr;
     }
 };
 
@@ -683,6 +691,50 @@ int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
     if (!dev)
         CK(cudaMemcpyAsync(out, s->sp_S, (size_t)s->F * s->A * Q * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
     return sync_and_check(s);
+}
+
+int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* ratio, int32_t* ndetected)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_detect: handle is NULL");
+    if (ndetected) *ndetected = 0;
+    if (!flags) return fail(CYC_EINVAL, "cyc_detect: flags is NULL");
+    if (!(kappa > 0.0) || !isfinite(kappa)) return fail(CYC_EINVAL, "cyc_detect: kappa must be positive and finite");
+    if (!detect_supported(win)) return fail(CYC_EINVAL, "cyc_detect: win must be in [2, 32]");
+    if (s->n_eff == 0) return fail(CYC_ENODATA, "cyc_detect: N_eff is 0");
+    DeviceGuard g(s->device);
+    bool wrong = false;
+    const bool fdev = is_device_ptr(flags, s->device, &wrong);
+    if (wrong) return fail(CYC_EINVAL, "cyc_detect: flags is memory of another device");
+    const bool rdev = ratio && is_device_ptr(ratio, s->device, &wrong);
+    if (wrong) return fail(CYC_EINVAL, "cyc_detect: ratio is memory of another device");
+    const size_t nfa = (size_t)s->F * s->A;
+    if (!s->dt_s) {
+        CK(cudaMalloc(&s->dt_s, nfa * sizeof(double)));
+        CK(cudaMalloc(&s->dt_flags, nfa));
+        CK(cudaMalloc(&s->dt_ratio, nfa * sizeof(float)));
+        CK(cudaMalloc(&s->dt_count, sizeof(int)));
+        CK(cudaMalloc(&s->dt_dc, (size_t)s->A));
+        std::vector<uint8_t> dc(s->A);
+        for (int i = 0; i < s->A; ++i) dc[i] = (!s->cross && alpha_to_phi(s->alphas[i]) == 0) ? 1 : 0;
+        CK(cudaMemcpy(s->dt_dc, dc.data(), (size_t)s->A, cudaMemcpyHostToDevice));
+    }
+    const double inv_n = 1.0 / (double)s->n_eff;
+    if (s->full)
+        CK(full_read(s->sums, s->Au, s->ncols, s->F, s->L, inv_n, s->d_out, s->st));
+    else
+        CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, inv_n, s->d_out, s->st));
+    const int conv_f = s->forms[0] == CYC_CONV ? 0 : -1;
+    uint8_t* fl = fdev ? flags : s->dt_flags;
+    float* ra = ratio ? (rdev ? ratio : s->dt_ratio) : nullptr;
+    CK(detect(s->d_out, s->F, s->A, s->L, s->dt_dc, conv_f, win, kappa, s->dt_s, fl, ra, s->dt_count, s->st));
+    s->kernel_launches += 3;
+    if (!fdev) CK(cudaMemcpyAsync(flags, s->dt_flags, nfa, cudaMemcpyDeviceToHost, s->st));
+    if (ratio && !rdev) CK(cudaMemcpyAsync(ratio, s->dt_ratio, nfa * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+    int count = 0;
+    CK(cudaMemcpyAsync(&count, s->dt_count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    const int rc = sync_and_check(s);
+    if (ndetected) *ndetected = count;
+    return rc;
 }
 
 int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k)

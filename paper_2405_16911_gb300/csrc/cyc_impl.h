@@ -221,6 +221,15 @@ cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double 
 cudaError_t spectrum(const double2* R, const int32_t* lags, int rows, int L, int Q, int taper, double mmax,
                      double2* E, double2* S, cudaStream_t st);
 
+// Cycle-frequency detection (detect.cu): per form and cycle frequency of R [F][A][L] (FP64),
+// the statistic s = max over lags |R|^2 (0 for form conv_f where dc[a]), the median of s over
+// the offsets +-2 .. +-win (circular), and flags (bit 0 detected: s > kappa * median and a
+// local maximum; bit 1 local maximum), ratio = s / median (may be null), count of detections.
+// Scratch s [F][A].  win in [2, 32].
+bool        detect_supported(int win);
+cudaError_t detect(const double2* R, int F, int A, int L, const uint8_t* dc, int conv_f, int win, double kappa,
+                   double* s, uint8_t* flags, float* ratio, int* count, cudaStream_t st);
+
 // Persistent launch over a device list of work items (taken with an atomic counter that
 // the caller zeroes before the launch); `grid` (even) CTAs in two-CTA clusters, one per SM.
 cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, int* err,

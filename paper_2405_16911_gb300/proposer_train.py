@@ -17,7 +17,8 @@ ln(A L F / P_fa) / (ln L + 0.5772) = 3.8 would give P_fa = 1e-3 per signal (A = 
 L = 64, F = 2).  Neighbouring lags of these oversampled signals are strongly correlated,
 so the maximum has a lighter median and a heavier tail than that: on the mix, 0.7 of the
 1.7 detections per signal at 3.8 lie far from every line the generator puts in.
-calibrate_kappa() therefore sets kappa from the ratio s/nu itself, at the local maxima
+The rule runs in the library (cyc_detect, include/cyc.h).  calibrate_kappa() sets kappa
+from the ratio s/nu itself, at the local maxima
 three or more grid bins away from every such line (k/sps, k/(2 sps), and 2 f0 + k/(2 sps)):
 an exponential tail fitted above its 99th percentile, solved for P_fa = 1e-3 per signal.
 On 512 held-out signals that gives 8.36, and KAPPA = 8.4.  A proposal hits a detection
@@ -73,22 +74,7 @@ WIN = 16
 KAPPA = 8.4
 
 
-def cfar_ratio(R: np.ndarray):
-    """(s/nu [F][A], local-maximum mask [F][A]) of a full-grid estimate R [F][A][L]."""
-    s2 = (np.abs(R) ** 2).max(axis=-1)
-    s2[0, len(GRID) // 2] = 0.0                     # the conventional a = 0 line is always there
-    A = s2.shape[1]
-    offs = np.array([d for d in range(-WIN, WIN + 1) if abs(d) > 1])
-    idx = (np.arange(A)[:, None] + offs[None, :]) % A
-    nu = np.median(s2[:, idx], axis=2)
-    lm = (s2 >= np.roll(s2, 1, axis=1)) & (s2 >= np.roll(s2, -1, axis=1))
-    return s2 / np.maximum(nu, 1e-300), lm
-
-
-def detect(R: np.ndarray, n_eff: int = 0, kappa: float = KAPPA) -> np.ndarray:
-    """Labels [2][512] from a full-grid estimate R [2][512][64] (see module doc)."""
-    ratio, lm = cfar_ratio(R)
-    return ((ratio > kappa) & lm).astype(np.float32)
+WIN = 16
 
 
 def line_bins(p: dict, guard: int = 3) -> np.ndarray:
@@ -115,20 +101,20 @@ def calibrate_kappa(ratios, maxima, params, p_fa: float = P_FA) -> float:
 
 
 def label(pkg, xs_dev, n: int, precision: str = "bf16x3", ratios: bool = False):
-    """Full-grid estimates of n signals already on the device -> labels [n][2][512]
-    (and, with ratios=True, the CFAR ratios and local-maximum masks as well)."""
+    """Full-grid estimates of n signals already on the device -> labels [n][2][512], the
+    library's cyc_detect on each estimate (and, with ratios=True, the CFAR ratios and
+    local-maximum masks as well)."""
     labels = np.zeros((n, 2, 512), dtype=np.float32)
     rs, ms = [], []
     with pkg.Stream(LAGS, GRID, pkg.CYC_BOTH, precision=precision, max_chunk=NS) as s:
         for i in range(n):
             s.reset()
             s.push(xs_dev[i])
-            R, n_eff = s.read()
-            r, m = cfar_ratio(R)
-            labels[i] = ((r > KAPPA) & m).astype(np.float32)
+            flags, ratio, _ = s.detect(KAPPA, WIN)
+            labels[i] = (flags & 1).astype(np.float32)
             if ratios:
-                rs.append(r.astype(np.float32))
-                ms.append(m)
+                rs.append(ratio.copy())
+                ms.append((flags & 2) != 0)
     return (labels, rs, ms) if ratios else labels
 
 

@@ -67,12 +67,15 @@ def test_forward_and_gradients_match_oracle(cyc, signals):
         g, loss = cyc.cyc_net_gradients(net, f, torch.from_numpy(labels).cuda(), 2, 5.0)
         lref, gref = on.batch_loss_and_grads(ps, list(feats), list(labels), pos_weight=5.0)
         assert abs(loss - lref) / lref < 1e-2
+        # element by element, each tensor against a tolerance scaled by its largest entry
+        # (FP16 activations and weights; a wrong gradient at a few positions, e.g. at the
+        # circular wrap of a convolution, is an error of the order of those entries)
         go = oracle_params(g)
         for li, ((gW, gb), (rW, rb)) in enumerate(zip(go, gref)):
-            rel = np.linalg.norm(gW - rW) / (np.linalg.norm(rW) + 1e-30)
-            assert rel < 2e-2, (li, rel)
-            relb = np.linalg.norm(gb - rb) / (np.linalg.norm(rb) + 1e-30)
-            assert relb < 2e-2, (li, relb)
+            errW = np.max(np.abs(gW - rW)) / np.max(np.abs(rW))
+            errb = np.max(np.abs(gb - rb)) / np.max(np.abs(rb))
+            assert errW < 3e-2, (li, errW)
+            assert errb < 3e-2, (li, errb)
     finally:
         cyc.cyc_net_destroy(net)
 

@@ -103,3 +103,49 @@ def test_lag_product_channel_shows_a_conventional_line():
     assert F[c4, k] > F[c4, k - 5] + 2.0 and F[c4, k] > F[c4, k + 5] + 2.0
     assert abs(F[2, k] - np.median(F[2])) < 1e-6     # |x|^2 = 1: no line at 1/8
     assert np.allclose(F.mean(axis=1), 0.0, atol=1e-9) and np.allclose(F.std(axis=1), 1.0, atol=1e-9)
+
+
+def test_welch_hann_tone_closed_form():
+    """A bin-centred tone A exp(j 2 pi k0 n / N) under the Hann window w = 1/2 - 1/2 cos(2 pi n / N):
+    the windowed DFT is A N (1/2 at k0, -1/4 at k0 +- 1, 0 elsewhere), so the periodogram has
+    exactly three non-zero bins A^2 N^2 (1/16, 1/4, 1/16) -- ratios 1:4:1 -- and every segment
+    is the same, so the 16-segment mean equals one of them.  x^2 is the tone 2 k0 with A^2, and
+    a lag product x[n+d] conj(x[n]) = A^2 exp(j 2 pi k0 d / N) is a constant: its three bins
+    are at 0 and +-1.  (A rectangular window would give one bin; a wrong segment count or
+    scaling another level.)"""
+    N, k0, amp = on.NFFT, 37, 0.75
+    x = amp * np.exp(2j * np.pi * k0 * np.arange(on.NEED) / N)
+    P = on.welch(x)
+    for c, (k, a2) in enumerate([(k0, amp ** 2), (2 * k0, amp ** 4)] + [(0, amp ** 4)] * len(on.LAG_CHANNELS)):
+        expect = np.zeros(N)
+        expect[k % N] = a2 * N * N / 4
+        expect[(k + 1) % N] = expect[(k - 1) % N] = a2 * N * N / 16
+        assert np.allclose(P[c], expect, rtol=1e-9, atol=1e-9 * a2 * N * N), c
+
+
+def test_welch_averages_the_segments():
+    """Segments with different amplitudes: the Welch estimate is the mean of their periodograms
+    (sum of the squared amplitudes over the 16 segments, divided by 16)."""
+    N, k0 = on.NFFT, 100
+    amps = 1.0 + 0.25 * np.arange(on.NSEG)
+    n = np.arange(on.NEED)
+    a = np.concatenate([np.repeat(amps, N), np.full(on.NEED - on.NSEG * N, amps[-1])])
+    x = a * np.exp(2j * np.pi * k0 * n / N)
+    P = on.welch(x)
+    assert abs(P[0, k0] - np.mean(amps ** 2) * N * N / 4) < 1e-9 * P[0, k0]
+
+
+def test_features_are_the_standardised_log_of_the_shifted_welch_spectrum():
+    """features = per channel (L - mean L) / std L with L = log10(Welch + 1e-12), frequency bins
+    shifted so that bin j is -1/2 + j/N: checked through properties that pin each step -- the
+    shift (a tone's peak bin), the standardisation (zero mean, unit spread), and the log
+    (a scaled signal gives the same features for x, whose spectrum has no floor)."""
+    import synth
+    x = synth.white(on.NEED, seed=11)
+    F = on.features(x)
+    G = on.features(3.0 * x)
+    assert np.allclose(F.mean(axis=1), 0.0, atol=1e-9) and np.allclose(F.std(axis=1), 1.0, atol=1e-9)
+    assert np.allclose(F[0], G[0], atol=1e-9)                     # log10(9 P) - mean: the 9 cancels
+    P = on.welch(x)
+    L = np.log10(np.roll(P, on.NFFT // 2, axis=1) + 1e-12)
+    assert np.allclose(np.corrcoef(F[0], L[0])[0, 1], 1.0, atol=1e-12)

@@ -1,7 +1,10 @@
-"""The proposer's label rule (local constant-false-alarm detection) on synthetic estimates."""
+"""The proposer's label rule (the constant-false-alarm detection of oracle.detect, which
+cyc_detect implements in the library) on synthetic estimates of the label grid."""
 import numpy as np
 
-from paper_2405_16911_gb300 import proposer_train as pt
+from oracle import detect as od
+
+GRID = -0.5 + np.arange(512) / 512.0
 
 
 def noise(rng, scale=1.0):
@@ -14,7 +17,7 @@ def test_few_false_alarms_on_noise_even_when_its_level_varies_with_a():
     fa = 0
     for _ in range(100):
         R = noise(rng) * np.sqrt(bumps)[None, :, None]
-        fa += pt.detect(R, 65536).sum()
+        fa += od.cfar(R, GRID)[0].sum()
     assert fa / 100 < 0.05
 
 
@@ -24,7 +27,7 @@ def test_planted_lines_are_detected_and_the_a0_line_is_not():
     R[0, 256, :] += 5.0                           # conventional a = 0: always present, never a label
     R[0, 320, 10] += 0.2                          # a = 1/8 at lag 10
     R[1, 100, 0] += 0.3
-    lab = pt.detect(R, 65536)
-    assert lab[0, 320] == 1 and lab[1, 100] == 1
-    assert lab[0, 256] == 0
+    lab = od.cfar(R, GRID)[0]
+    assert lab[0, 320] and lab[1, 100]
+    assert not lab[0, 256]
     assert lab.sum() <= 3
