@@ -8,12 +8,18 @@
 // and column tables and the FP32 partial sums) in one file-scope device array of fixed
 // size, and folds the partials straight into the caller's output buffer in FP64.
 //
-// The array is created when the library is loaded on a device and stays resident on every
-// GPU that loads the library until the process exits (kScratchBytes, about 8.1 MiB).
-// Every call shares it and it keeps the previous call's contents; everything a call reads
-// from it is written by that same call first.  Two calls whose GPU work overlaps (calls on
-// different CUDA streams) race on the array and give wrong results; calls on one stream
-// are ordered and safe.
+// The array belongs to this file's module.  CUDA loads modules lazily by default, so the
+// array (kScratchBytes, about 8.1 MiB) and the kernels are brought onto a device by the
+// first call on that device, which also looks up the array's device address; from then on
+// the array stays resident until the process exits.  A caller whose host application
+// reserves the device memory must therefore make one call (any valid size) before that, or
+// run with CUDA_MODULE_LOADING=EAGER so that the module loads with the context.  The tables
+// a call needs are written into the array by kernels that carry them as launch parameters,
+// so a call only queues work and never waits for the stream.
+// Every call shares the array and it keeps the previous call's contents; everything a call
+// reads from it is written by that same call first.  Two calls whose GPU work overlaps
+// (calls on different CUDA streams) race on the array and give wrong results; calls on one
+// stream are ordered and safe.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -81,6 +87,22 @@ __global__ void static_fold_kernel(const float2* __restrict__ part, int nsplit, 
     out[e] = make_double2((o.x + sr) * scale, (o.y + si) * scale);
 }
 
+// A slice of the tables, passed by value as the launch's parameters (a few KB), copied into
+// the scratch array: no host-to-device copy from pageable memory, which could make the
+// call wait for the stream.
+constexpr int kTableBytes = 3968;
+struct TableSlice {
+    unsigned char* dst;
+    uint32_t       nbytes;
+    uint32_t       pad;
+    unsigned char  data[kTableBytes];
+};
+
+__global__ void table_kernel(TableSlice t)
+{
+    for (uint32_t i = threadIdx.x; i < t.nbytes; i += blockDim.x) t.dst[i] = t.data[i];
+}
+
 uint64_t phase_step(double a)
 {
     uint64_t phi = 0;
@@ -88,6 +110,8 @@ uint64_t phase_step(double a)
     return phi;
 }
 
+// Device or managed memory of device `dev` (managed memory reports the device it was
+// allocated on).
 bool on_device(const void* p, int dev)
 {
     cudaPointerAttributes at;
@@ -95,7 +119,7 @@ bool on_device(const void* p, int dev)
         cudaGetLastError();
         return false;
     }
-    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -136,6 +160,8 @@ extern "C" int cyc_estimate_static(const void* x, int64_t T, const int32_t* lags
     }
     if (!on_device(x, dev) || !on_device(out, dev))
         return sfail(CYC_EINVAL, "cyc_estimate_static: x and out must be memory of the current device %d", dev);
+    if (((uintptr_t)x & 7) != 0 || ((uintptr_t)out & 15) != 0)
+        return sfail(CYC_EINVAL, "cyc_estimate_static: x must be 8-byte and out 16-byte aligned");
 
     // ---- once per device: the device address of the scratch array ----
     unsigned char* base;
@@ -152,10 +178,13 @@ extern "C" int cyc_estimate_static(const void* x, int64_t T, const int32_t* lags
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
-    // ---- tables: built on the stack, copied into the scratch array in stream order ----
-    uint64_t phi[kMaxAlphas];
-    int32_t col_lag[kMaxCols];
-    int8_t col_conj[kMaxCols];
+    // ---- tables: built on the stack, written into the scratch array in stream order by
+    // kernels that carry them as launch parameters ----
+    const int ncols = nlags * F;
+    unsigned char tab[kOffConj + kMaxCols];
+    uint64_t* phi = (uint64_t*)(tab + kOffPhi);
+    int32_t* col_lag = (int32_t*)(tab + kOffLag);
+    int8_t* col_conj = (int8_t*)(tab + kOffConj);
     for (int i = 0; i < nalphas; ++i) phi[i] = phase_step(alphas[i]);
     const int forms[2] = {conj_flag & CYC_CONV ? CYC_CONV : CYC_CONJ, CYC_CONJ};
     for (int l = 0; l < nlags; ++l)
@@ -163,12 +192,21 @@ extern "C" int cyc_estimate_static(const void* x, int64_t T, const int32_t* lags
             col_lag[l * F + f] = lags[l];
             col_conj[l * F + f] = forms[f] == CYC_CONJ ? 1 : 0;
         }
-    const int ncols = nlags * F;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(base + kOffPhi, phi, nalphas * sizeof(uint64_t), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + kOffLag, col_lag, ncols * sizeof(int32_t), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(base + kOffConj, col_conj, ncols * sizeof(int8_t), cudaMemcpyHostToDevice, st)))
-        return sfail(CYC_ECUDA, "cyc_estimate_static: table copy failed: %s", cudaGetErrorString(e));
+    const size_t spans[3][2] = {{kOffPhi, (size_t)nalphas * sizeof(uint64_t)},
+                                {kOffLag, (size_t)ncols * sizeof(int32_t)},
+                                {kOffConj, (size_t)ncols}};
+    for (const auto& sp : spans)
+        for (size_t o = 0; o < sp[1]; o += kTableBytes) {
+            TableSlice t;
+            t.dst = base + sp[0] + o;
+            t.nbytes = (uint32_t)(sp[1] - o < (size_t)kTableBytes ? sp[1] - o : (size_t)kTableBytes);
+            t.pad = 0;
+            memcpy(t.data, tab + sp[0] + o, t.nbytes);
+            table_kernel<<<1, 256, 0, st>>>(t);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return sfail(CYC_ECUDA, "cyc_estimate_static: table launch failed: %s", cudaGetErrorString(e));
+        }
 
     int num_sms = 1;
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);

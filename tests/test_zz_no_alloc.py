@@ -4,10 +4,11 @@ Some callers cannot allocate device memory when they need an estimate (a real-ti
 callback that must not call cudaMalloc, a plug-in whose host application owns the device
 memory pool); cyc_estimate_static serves them from a fixed device array inside the
 library.  Its result must equal what cyc_create / cyc_push / cyc_read give on the same
-samples, within the FP32 path's tolerance (1e-5 relative to R^0(0)), on two calls in a
-row that use different sizes, so that nothing left in the shared array leaks from the
-first call into the second.  This file sorts last so that a stop at its first failure
-has already run every other test.
+samples, and the FP64 oracle's, within the FP32 path's tolerance (1e-5 relative to
+R^0(0)), on two calls in a row that use different sizes, so that nothing left in the
+shared array leaks from the first call into the second; and at the array's limit of 2^20
+partial sums, where one FP32 partial per entry takes a whole pass of 2^20 samples.  This
+file sorts last so that a stop at its first failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -52,6 +53,42 @@ def test_static_matches_streaming_on_two_calls(cyc):
         r00 = oracle.r00(x, int(lags.max()))
         err = float(np.max(np.abs(Rs - Rr)) / r00)
         assert err < 1e-5, (i, err)
+        Ro, no = oracle.estimate(x, lags, alphas, forms, n0=n0)
+        assert no == ns
+        err_o = float(np.max(np.abs(Rs - Ro)) / r00)
+        assert err_o < 1e-5, (i, err_o)
+
+
+def test_static_at_the_partial_limit_against_the_oracle(cyc):
+    """4096 cycle frequencies x 128 lags x 2 forms = 2^20 partial sums: one FP32 partial per
+    entry over each pass of 2^20 samples.  Sampled entries against the FP64 oracle,
+    including the all-positive mean-power entry a = 0, m = 0."""
+    T = (1 << 20) + 300
+    x = (synth.white(T, seed=230) * 1.3 + 0.4).astype(np.complex64)
+    lags = np.arange(128)
+    alphas = -0.5 + np.arange(4096) / 4096.0
+    Rs, ns = static(cyc, x, lags, alphas, 3, 0)
+    assert ns == T - 127
+    r00 = oracle.r00(x, 127)
+    rng = np.random.default_rng(231)
+    picks = [(0, 2048, 0), (1, 2048, 0), (0, 0, 127)] + [(int(rng.integers(2)), int(rng.integers(4096)),
+                                                           int(rng.integers(128))) for _ in range(13)]
+    for f, ai, m in picks:
+        ref = oracle.entries(x, 127, [f + 1], [alphas[ai]], [m])[0][0]
+        err = abs(Rs[f, ai, m] - ref) / r00
+        assert err < 1e-5, (f, ai, m, err)
+
+
+def test_static_rejects_misaligned_buffers(cyc):
+    import torch
+    x = torch.zeros(2 * 1001, dtype=torch.float32, device="cuda")
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(cyc.CycError) as e:           # x one float in: 4-byte aligned
+        cyc.cyc_estimate_static(x.data_ptr() + 4, 1000, [0, 1], [0.1], 1, 0, out)
+    assert e.value.code == cyc.CYC_EINVAL
+    with pytest.raises(cyc.CycError) as e:           # out one double in: 8-byte aligned
+        cyc.cyc_estimate_static(x, 1000, [0, 1], [0.1], 1, 0, out.data_ptr() + 8)
+    assert e.value.code == cyc.CYC_EINVAL
 
 
 def test_static_rejects_sizes_beyond_its_array(cyc):
