@@ -218,7 +218,8 @@ CYC_API int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk,
 
 /*
  * cyc_read: wait for the stream's work, then write R = sums / N_eff (layout above) to
- * `out`, which may be host or device memory of at least F * nalphas * nlags * 16 bytes.
+ * `out`, which may be host or device memory of at least F * nalphas * nlags * 16 bytes
+ * (device memory 16-byte aligned: CYC_EINVAL otherwise).
  * *n_eff (optional) receives N_eff.  CYC_ENODATA when N_eff == 0 (out untouched).
  */
 CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);
@@ -261,6 +262,20 @@ CYC_API int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, in
  */
 CYC_API int cyc_profile(cyc_stream* s, int enable);
 CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels);
+
+/*
+ * cyc_set_wait_budget: how long (SM clock cycles) each bounded wait inside the stream's
+ * tensor-core projection kernel waits for a producer, a copy or the tensor core before it
+ * gives up; 0 restores the default of 2e9 (about a second at 2 GHz).  A wait that gives up
+ * makes every other wait of the kernel give up at once, the kernel winds down (in-flight
+ * copies and tensor-core work are waited for), and the next cyc_sync / cyc_read reports
+ * CYC_ETIMEDOUT; the sums are then unreliable (cyc_reset).  Applies to launches queued
+ * after the call; the FP32 paths have no waits.  cycles in [0, 2^40].
+ * Test hook: the environment variable CYC_TEST_WITHHOLD_ARRIVAL=1 at stream creation makes
+ * the tensor-core kernel of that stream leave one producer arrival out, so that a wait
+ * runs out -- the only way to exercise this path without a fault; never set it otherwise.
+ */
+CYC_API int cyc_set_wait_budget(cyc_stream* s, int64_t cycles);
 
 /*
  * cyc_phase_increment: the fixed-point form in which a stream holds cycle frequency a:
@@ -401,23 +416,31 @@ CYC_API int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int
  * allocate (device allocation can synchronise the whole device and take unbounded time),
  * or a plug-in whose host application has already reserved the device memory in its
  * own pool.
- *   x        device memory of the current device: T interleaved complex64 samples
- *   lags, alphas, conj_flag, n0   as in cyc_params (host arrays, read before return)
- *   out      device memory of the current device, F * nalphas * nlags * 16 bytes: R as
- *            interleaved FP64 [form][alpha][lag] (same layout and value as cyc_read)
+ *   x        device (or managed) memory of the current device, 8-byte aligned: T interleaved
+ *            complex64 samples
+ *   lags     non-negative lags (the signed lags of cyc_params are not accepted here:
+ *            CYC_EINVAL); alphas, conj_flag, n0 as in cyc_params (host arrays, read before
+ *            return)
+ *   out      device (or managed) memory of the current device, 16-byte aligned,
+ *            F * nalphas * nlags * 16 bytes: R as interleaved FP64 [form][alpha][lag] (same
+ *            layout and value as cyc_read)
  *   n_eff    optional, receives T - max(lags) (or 0)
  *   cuda_stream   cudaStream_t the work is queued on (NULL = legacy default stream); the
- *            call returns once the work is queued, synchronise that stream before
- *            reading `out`.
+ *            call returns once the work is queued -- the tables travel as kernel launch
+ *            parameters, so no copy from host memory makes it wait for the stream --;
+ *            synchronise that stream before reading `out`.
  * It runs the FP32 projection with its scratch -- the cycle-frequency and column tables
  * and the FP32 partial sums -- in one fixed file-scope device array of about 8.1 MiB,
- * which every GPU that loads the library holds until the process exits.  Limits:
- * nalphas <= 4096, nlags * F <= 2048 and nalphas * nlags * F <= 2^20; larger requests
- * fail with CYC_EINVAL and queue nothing.  Duplicate cycle frequencies are computed
- * separately.  The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call shares the array:
- * calls whose GPU work can overlap (different CUDA streams) race and give wrong results;
- * calls on one stream are ordered and safe.  CYC_ENODATA when T <= max(lags).
+ * which every GPU that loads it holds until the process exits.  CUDA loads the library's
+ * device code lazily by default, so the array is brought onto a device, and its device
+ * address looked up, by the first call on that device: a caller whose host application
+ * later reserves the device memory, or that captures work into a CUDA graph, must make
+ * one call (of any valid size) beforehand, or run with CUDA_MODULE_LOADING=EAGER.
+ * Limits: nalphas <= 4096, nlags * F <= 2048 and nalphas * nlags * F <= 2^20; larger
+ * requests fail with CYC_EINVAL and queue nothing.  Duplicate cycle frequencies are
+ * computed separately.  Every call shares the array: calls whose GPU work can overlap
+ * (different CUDA streams) race and give wrong results; calls on one stream are ordered
+ * and safe.  CYC_ENODATA when T <= max(lags).
  */
 CYC_API int cyc_estimate_static(const void* x, int64_t T, const int32_t* lags, int nlags,
                                 const double* alphas, int nalphas, int conj_flag, int64_t n0,

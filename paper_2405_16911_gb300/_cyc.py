@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "cyc_read_windows": ([P, P, I64, P, P], I),
         "cyc_read_spectrum": ([P, I32, I32, P], I),
         "cyc_detect": ([P, ctypes.c_double, I32, P, P, P], I),
+        "cyc_set_wait_budget": ([P, I64], I),
         "cyc_push": ([P, P, I64, I], I),
         "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
@@ -350,6 +351,11 @@ def cyc_estimate_static(x, T: int, lags, alphas, conj_flag: int, n0: int, out, c
     _check(lib.cyc_estimate_static(xa, int(T), lags.ctypes.data, lags.size, alphas.ctypes.data, alphas.size,
                                    int(conj_flag), int(n0), oa, ctypes.byref(neff), cuda_stream or None))
     return neff.value
+
+
+def cyc_set_wait_budget(h: int, cycles: int) -> None:
+    """SM cycles each bounded wait of the stream's tensor-core kernel waits (0: default)."""
+    _check(load().cyc_set_wait_budget(h, int(cycles)))
 
 
 def cyc_phase_increment(a: float) -> int:
@@ -630,6 +636,9 @@ class Stream:
 
     def detect(self, kappa: float = 8.4, win: int = 16, flags=None, ratio=None):
         return cyc_detect(self.h, kappa, win, flags, ratio)
+
+    def set_wait_budget(self, cycles: int):
+        cyc_set_wait_budget(self.h, cycles)
 
     def sync(self):
         cyc_sync(self.h)

@@ -393,11 +393,14 @@ bool is_device_ptr(const void* p, int device, bool* wrong_device)
         return false;
     }
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
-        if (at.type == cudaMemoryTypeDevice && at.device != device) *wrong_device = true;
+        if (at.device != device) *wrong_device = true;
         return true;
     }
     return false;
 }
+
+// Device outputs are written as double2 (16-byte stores).
+bool misaligned16(const void* p) { return ((uintptr_t)p & 15) != 0; }
 
 }  // namespace
 
@@ -642,6 +645,7 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     bool wrong = false;
     bool dev = is_device_ptr(out, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_read: out is memory of another device");
+    if (dev && misaligned16(out)) return fail(CYC_EINVAL, "cyc_read: device out must be 16-byte aligned");
     double2* dst = dev ? (double2*)out : s->d_out;
     if (s->full)
         CK(full_read(s->sums, s->Au, s->ncols, s->F, s->L, 1.0 / (double)s->n_eff, dst, s->st));
@@ -664,6 +668,7 @@ int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
     bool wrong = false;
     const bool dev = is_device_ptr(out, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_read_spectrum: out is memory of another device");
+    if (dev && misaligned16(out)) return fail(CYC_EINVAL, "cyc_read_spectrum: device out must be 16-byte aligned");
     if (!s->d_lags) {
         CK(cudaMalloc(&s->d_lags, (size_t)s->L * sizeof(int32_t)));
         CK(cudaMemcpy(s->d_lags, s->lags.data(), (size_t)s->L * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -707,6 +712,7 @@ int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* 
     if (wrong) return fail(CYC_EINVAL, "cyc_detect: flags is memory of another device");
     const bool rdev = ratio && is_device_ptr(ratio, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_detect: ratio is memory of another device");
+    if (rdev && ((uintptr_t)ratio & 3) != 0) return fail(CYC_EINVAL, "cyc_detect: device ratio must be 4-byte aligned");
     const size_t nfa = (size_t)s->F * s->A;
     if (!s->dt_s) {
         CK(cudaMalloc(&s->dt_s, nfa * sizeof(double)));
@@ -751,6 +757,7 @@ int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin,
     bool wrong = false;
     const bool dev = is_device_ptr(out, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_read_windows: out is memory of another device");
+    if (dev && misaligned16(out)) return fail(CYC_EINVAL, "cyc_read_windows: device out must be 16-byte aligned");
     const int64_t per = (int64_t)s->F * s->A * s->L;
     const uint64_t base = (uint64_t)s->n0 + (uint64_t)s->Mneg;
     const double inv_n = 1.0 / (double)s->win_len;
@@ -879,6 +886,14 @@ int cyc_phase_increment(double a, uint64_t* phi)
 {
     if (!phi || !isfinite(a)) return fail(CYC_EINVAL, "cyc_phase_increment: a must be finite, phi non-NULL");
     *phi = alpha_to_phi(a);
+    return CYC_OK;
+}
+
+int cyc_set_wait_budget(cyc_stream* s, int64_t cycles)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_set_wait_budget: handle is NULL");
+    if (cycles < 0 || cycles > ((int64_t)1 << 40)) return fail(CYC_EINVAL, "cyc_set_wait_budget: cycles must be in [0, 2^40]");
+    s->wait_budget = cycles;
     return CYC_OK;
 }
 

@@ -715,6 +715,7 @@ int cyc_server_read(cyc_server* srv, int sid, double* out, int64_t* n_eff)
     bool dev = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
                (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
     cudaGetLastError();
+    if (dev && ((uintptr_t)out & 15) != 0) return sfail(CYC_EINVAL, "cyc_server_read: device out must be 16-byte aligned");
     double2* dst = dev ? (double2*)out : s.d_out;
     // the sums were last written by a batch on the compute stream
     SCK(read_sums(s.sums, s.d_amap, s.F, s.A, s.L, s.ncols, 1.0 / (double)want, dst, srv->cst));
