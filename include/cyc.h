@@ -207,7 +207,9 @@ CYC_API int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags,
  * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read
  * in stream order -- keep it unchanged until the next cyc_read / cyc_sync.
  * on_device == 0: host memory; pageable memory is consumed before return, page-locked
- * memory is read in stream order like device memory.  nsamples == 0 is a no-op.
+ * memory is read in stream order like device memory -- on a copy stream of the handle's own,
+ * so that the copy of one push overlaps the projection of the previous one (the projection
+ * waits for its copy).  nsamples == 0 is a no-op.
  */
 CYC_API int cyc_push(cyc_stream* s, const void* chunk, int64_t nsamples, int on_device);
 

@@ -164,6 +164,11 @@ struct cyc_stream {
     double2* d_out = nullptr;
     int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
     int* h_err = nullptr;       // page-locked copy, read after a stream synchronisation
+    // host pushes: chunks are copied on a stream of their own, so that the copy of one pass
+    // overlaps the projection of the previous one (created at the first host push)
+    cudaStream_t xst = nullptr;
+    cudaEvent_t ev_copied = nullptr;        // the current pass's chunk has landed
+    cudaEvent_t ev_read[2] = {nullptr, nullptr};   // the last pass that viewed stage[b] is done
     // profiling
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -181,6 +186,10 @@ struct cyc_stream {
     void free_all()
     {
         free_events();
+        if (xst) { cudaStreamSynchronize(xst); cudaStreamDestroy(xst); xst = nullptr; }
+        if (ev_copied) { cudaEventDestroy(ev_copied); ev_copied = nullptr; }
+        for (auto& e : ev_read)
+            if (e) { cudaEventDestroy(e); e = nullptr; }
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
                       part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S,
                       dt_s, dt_flags, dt_ratio, dt_dc, dt_count};
@@ -575,17 +584,29 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
     }
     const float2* src = (const float2*)xchunk;
     const float2* ysrc = (const float2*)ychunk;
+    if (!on_device && !s->xst) {
+        CK(cudaStreamCreateWithFlags(&s->xst, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&s->ev_copied, cudaEventDisableTiming));
+        for (auto& e : s->ev_read) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     int64_t left = nsamples;
     // a windowed pass holds at most kWinSplits hop-aligned partials
     const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(kWinSplits - 1) * s->hop) : s->max_chunk;
     while (left > 0) {
         int64_t c = left < pass ? left : pass;
         float2* view = s->stage[s->cur];
-        // a1: the view is [carried tail (held samples) | new samples], for both inputs
-        CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, s->st));
+        // a1: the view is [carried tail (held samples) | new samples], for both inputs.  A host
+        // chunk lands through the copy stream once the pass that last viewed this buffer is
+        // done; the tail [0, held) comes from the previous pass on the compute stream.
+        cudaStream_t cs = on_device ? s->st : s->xst;
+        if (!on_device) CK(cudaStreamWaitEvent(cs, s->ev_read[s->cur], 0));
+        CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
         if (s->cross)
-            CK(cudaMemcpyAsync(s->stage_y[s->cur] + s->held, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault,
-                               s->st));
+            CK(cudaMemcpyAsync(s->stage_y[s->cur] + s->held, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
+        if (!on_device) {
+            CK(cudaEventRecord(s->ev_copied, cs));
+            CK(cudaStreamWaitEvent(s->st, s->ev_copied, 0));
+        }
         int64_t nview = s->held + c;
         int64_t nc = nview - s->M;
         if (nc > 0) {
@@ -605,6 +626,7 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
                 CK(cudaMemcpyAsync(s->stage_y[s->cur ^ 1], s->stage_y[s->cur] + nview - keep,
                                    (size_t)keep * sizeof(float2), cudaMemcpyDeviceToDevice, s->st));
         }
+        if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
         s->cur ^= 1;
         s->held = keep;
         src += c;
