@@ -70,70 +70,70 @@ struct Layout {
 const Layout LAY;
 
 // ------------------------------------------------------------------------ features (FFT)
-// One CTA per (signal, channel): 16 radix-2 FFTs of 4096 points in shared memory,
-// periodograms accumulated, then log10, shift and standardisation.
-__global__ void __launch_bounds__(512) features_kernel(const float2* __restrict__ x, int64_t T, __half* __restrict__ out)
+// The windowed DFT of one segment of one channel into d (shared memory, natural order):
+// d[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), radix-2 decimation in time over tw.
+__device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, float2* d, const float2* tw)
 {
-    extern __shared__ float fsm[];
-    float2* d = reinterpret_cast<float2*>(fsm);          // 4096 complex
-    float2* tw = d + NFFT;                                // 2048 twiddles
-    float* acc = reinterpret_cast<float*>(tw + NFFT / 2); // 4096
-    __shared__ float red[2][16];
-    const int sig = blockIdx.x / NIN, ch = blockIdx.x % NIN, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const int lag = ch >= 2 ? c_lagch[ch - 2] : 0;
-    const float2* xs = x + (size_t)sig * T;
-    for (int k = tid; k < NFFT / 2; k += blockDim.x) {
+    __syncthreads();
+    for (int k = tid; k < NFFT; k += blockDim.x) {
+        float2 v = xs[(size_t)seg * NFFT + k];
+        float2 y;
+        if (ch == 0) {
+            y = v;
+        } else if (ch == 1) {
+            y = make_float2(v.x * v.x - v.y * v.y, 2.f * v.x * v.y);
+        } else {
+            const float2 u = xs[(size_t)seg * NFFT + k + lag];      // x[n+d] conj(x[n])
+            y = make_float2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);
+        }
+        float s, c;
+        sincospif(2.0f * k / NFFT, &s, &c);
+        float w = 0.5f - 0.5f * c;                    // Hann
+        d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
+    }
+    for (int half = 1; half < NFFT; half <<= 1) {
+        __syncthreads();
+        const int tstep = NFFT / (2 * half);
+        for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
+            const int grp = bf / half, pos = bf % half;
+            const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+            const float2 w = tw[pos * tstep];
+            const float2 a = d[i0], b = d[i1];
+            const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+            d[i0] = make_float2(a.x + bw.x, a.y + bw.y);
+            d[i1] = make_float2(a.x - bw.x, a.y - bw.y);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void twiddles(float2* tw)
+{
+    for (int k = threadIdx.x; k < NFFT / 2; k += blockDim.x) {
         float s, c;
         sincospif(-2.0f * k / NFFT, &s, &c);              // exp(-j 2 pi k / N)
         tw[k] = make_float2(c, s);
     }
-    for (int k = tid; k < NFFT; k += blockDim.x) acc[k] = 0.f;
-    for (int seg = 0; seg < NSEG; ++seg) {
-        __syncthreads();
-        for (int k = tid; k < NFFT; k += blockDim.x) {
-            float2 v = xs[(size_t)seg * NFFT + k];
-            float2 y;
-            if (ch == 0) {
-                y = v;
-            } else if (ch == 1) {
-                y = make_float2(v.x * v.x - v.y * v.y, 2.f * v.x * v.y);
-            } else {
-                const float2 u = xs[(size_t)seg * NFFT + k + lag];      // x[n+d] conj(x[n])
-                y = make_float2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);
-            }
-            float s, c;
-            sincospif(2.0f * k / NFFT, &s, &c);
-            float w = 0.5f - 0.5f * c;                    // Hann
-            d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
-        }
-        for (int half = 1; half < NFFT; half <<= 1) {
-            __syncthreads();
-            const int tstep = NFFT / (2 * half);
-            for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
-                const int grp = bf / half, pos = bf % half;
-                const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-                const float2 w = tw[pos * tstep];
-                const float2 a = d[i0], b = d[i1];
-                const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
-                d[i0] = make_float2(a.x + bw.x, a.y + bw.y);
-                d[i1] = make_float2(a.x - bw.x, a.y - bw.y);
-            }
-        }
-        __syncthreads();
-        for (int k = tid; k < NFFT; k += blockDim.x) acc[k] += d[k].x * d[k].x + d[k].y * d[k].y;
-    }
-    __syncthreads();
-    // log10 and the shift: output bin j <- FFT bin (j + N/2) mod N
+}
+
+// acc (the segments' summed periodogram, natural bin order) -> log10 of the mean, shifted so
+// that output bin j is FFT bin (j + N/2) mod N, standardised, FP16.  v: NFFT floats of scratch.
+__device__ void finish_channel(const float* acc, float* v, __half* o)
+{
+    __shared__ float red[2][16];
+    const int tid = threadIdx.x;
     float s1 = 0.f, s2 = 0.f;
     for (int j = tid; j < NFFT; j += blockDim.x) {
-        float v = log10f(acc[(j + NFFT / 2) & (NFFT - 1)] / NSEG + 1e-12f);
-        d[j].x = v;
-        s1 += v;
-        s2 += v * v;
+        float t = log10f(acc[(j + NFFT / 2) & (NFFT - 1)] / NSEG + 1e-12f);
+        v[j] = t;
+        s1 += t;
+        s2 += t * t;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     }
     if ((tid & 31) == 0) {
         red[0][tid >> 5] = s1;
@@ -147,19 +147,71 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
     }
     const float mu = t1 / NFFT;
     const float sd = fmaxf(sqrtf(fmaxf(t2 / NFFT - mu * mu, 0.f)), 1e-6f);
-    __half* o = out + ((size_t)sig * NIN + ch) * NFFT;
-    for (int j = tid; j < NFFT; j += blockDim.x) o[j] = __float2half_rn((d[j].x - mu) / sd);
+    for (int j = tid; j < NFFT; j += blockDim.x) o[j] = __float2half_rn((v[j] - mu) / sd);
+}
+
+// One CTA per (signal, channel): the 16 segments one after the other (many signals at once).
+__global__ void __launch_bounds__(512) features_kernel(const float2* __restrict__ x, int64_t T, __half* __restrict__ out)
+{
+    extern __shared__ float fsm[];
+    float2* d = reinterpret_cast<float2*>(fsm);          // 4096 complex
+    float2* tw = d + NFFT;                                // 2048 twiddles
+    float* acc = reinterpret_cast<float*>(tw + NFFT / 2); // 4096
+    const int sig = blockIdx.x / NIN, ch = blockIdx.x % NIN, tid = threadIdx.x;
+    const float2* xs = x + (size_t)sig * T;
+    twiddles(tw);
+    for (int k = tid; k < NFFT; k += blockDim.x) acc[k] = 0.f;
+    for (int seg = 0; seg < NSEG; ++seg) {
+        segment_dft(xs, ch, seg, d, tw);
+        for (int k = tid; k < NFFT; k += blockDim.x) acc[k] += d[k].x * d[k].x + d[k].y * d[k].y;
+    }
+    __syncthreads();
+    finish_channel(acc, reinterpret_cast<float*>(d), out + ((size_t)sig * NIN + ch) * NFFT);
+}
+
+// One signal, latency first: one CTA per (channel, segment) writes its periodogram to
+// pg [NIN][NSEG][NFFT]; features_finish_kernel then sums the segments in order (the same
+// sums, in the same order, as features_kernel) and finishes each channel.
+__global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restrict__ x, float* __restrict__ pg)
+{
+    extern __shared__ float fsm[];
+    float2* d = reinterpret_cast<float2*>(fsm);
+    float2* tw = d + NFFT;
+    const int ch = blockIdx.x / NSEG, seg = blockIdx.x % NSEG;
+    twiddles(tw);
+    segment_dft(x, ch, seg, d, tw);
+    float* o = pg + ((size_t)ch * NSEG + seg) * NFFT;
+    for (int k = threadIdx.x; k < NFFT; k += blockDim.x) o[k] = d[k].x * d[k].x + d[k].y * d[k].y;
+}
+
+__global__ void __launch_bounds__(512) features_finish_kernel(const float* __restrict__ pg, __half* __restrict__ out)
+{
+    __shared__ float acc[NFFT];
+    __shared__ float v[NFFT];
+    const int ch = blockIdx.x;
+    for (int k = threadIdx.x; k < NFFT; k += blockDim.x) {
+        float q[NSEG];
+#pragma unroll
+        for (int seg = 0; seg < NSEG; ++seg) q[seg] = pg[((size_t)ch * NSEG + seg) * NFFT + k];
+        float a = 0.f;
+#pragma unroll
+        for (int seg = 0; seg < NSEG; ++seg) a += q[seg];
+        acc[k] = a;
+    }
+    __syncthreads();
+    finish_channel(acc, v, out + (size_t)ch * NFFT);
 }
 
 // ------------------------------------------------------------------------ convolution
 // y[b][o][i] = bias[o] + sum_c sum_k W[o][c][k] x[b][c][(i + k - 4) mod N]  (+ ReLU, mask)
-// Block: 32 outputs channels x 128 positions of one sample; 256 threads, 4 x 4 each.
-template <typename TIn, typename TOut>
+// Block: 32 output channels x 32 MP positions of one sample; 256 threads, 4 x MP outputs each
+// (MP = 4 for training batches; MP = 1 for a single signal, four times as many CTAs).
+template <typename TIn, typename TOut, int MP>
 __global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, int cin, int cout,
                                                    const __half* __restrict__ w, const float* __restrict__ bias,
                                                    int relu, const __half* __restrict__ mask, TOut* __restrict__ y)
 {
-    constexpr int TI = 128, TCO = 32;
+    constexpr int TI = 32 * MP, TCO = 32;
     extern __shared__ float csm[];
     float* xs = csm;                          // [cin][TI + 8]
     float* ws = csm + cin * (TI + 8);         // [TCO][cin][9]
@@ -176,24 +228,24 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, in
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    float acc[4][4];
+    float acc[4][MP];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) acc[a][m] = 0.f;
+        for (int m = 0; m < MP; ++m) acc[a][m] = 0.f;
     for (int c = 0; c < cin; ++c) {
         const float* xr = xs + c * (TI + 8);
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
-            float wv[4], xv[4];
+            float wv[4], xv[MP];
 #pragma unroll
             for (int a = 0; a < 4; ++a) wv[a] = ws[((warp + 8 * a) * cin + c) * KW + k];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) xv[m] = xr[lane + 32 * m + k];
+            for (int m = 0; m < MP; ++m) xv[m] = xr[lane + 32 * m + k];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int m = 0; m < 4; ++m) acc[a][m] = fmaf(wv[a], xv[m], acc[a][m]);
+                for (int m = 0; m < MP; ++m) acc[a][m] = fmaf(wv[a], xv[m], acc[a][m]);
         }
     }
 #pragma unroll
@@ -202,7 +254,7 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, in
         if (o >= cout) continue;
         const float bv = bias ? bias[o] : 0.f;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < MP; ++m) {
             const int i = i0 + lane + 32 * m;
             float v = acc[a][m] + bv;
             if (relu) v = fmaxf(v, 0.f);
@@ -211,6 +263,38 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, in
             y[idx] = (TOut)v;
         }
     }
+}
+
+// The output layer (cout = 2) for few signals: one thread per position computes both outputs.
+__global__ void __launch_bounds__(256) conv_out2_kernel(const __half* __restrict__ x, int cin,
+                                                        const __half* __restrict__ w, const float* __restrict__ bias,
+                                                        float* __restrict__ y)
+{
+    constexpr int TI = 256;
+    extern __shared__ float csm[];
+    float* xs = csm;                          // [cin][TI + 8]
+    float* ws = csm + cin * (TI + 8);         // [2][cin][9]
+    const int b = blockIdx.z, i0 = blockIdx.x * TI, tid = threadIdx.x;
+    const __half* xb = x + (size_t)b * cin * NFFT;
+    for (int e = tid; e < cin * (TI + 8); e += 256) {
+        const int c = e / (TI + 8), j = e % (TI + 8);
+        xs[e] = __half2float(xb[(size_t)c * NFFT + ((i0 + j - 4 + NFFT) & (NFFT - 1))]);
+    }
+    for (int e = tid; e < 2 * cin * KW; e += 256) ws[e] = __half2float(w[e]);
+    __syncthreads();
+    float a0 = 0.f, a1 = 0.f;
+    for (int c = 0; c < cin; ++c) {
+        const float* xr = xs + c * (TI + 8) + tid;
+        const float* w0 = ws + c * KW;
+        const float* w1 = ws + (cin + c) * KW;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            a0 = fmaf(w0[k], xr[k], a0);
+            a1 = fmaf(w1[k], xr[k], a1);
+        }
+    }
+    y[((size_t)b * 2 + 0) * NFFT + i0 + tid] = a0 + bias[0];
+    y[((size_t)b * 2 + 1) * NFFT + i0 + tid] = a1 + bias[1];
 }
 
 // dW[o][c][k] += sum_b sum_i dz[b][o][i] h[b][c][(i + k - 4) mod N];  db[o] += sum dz[b][o][i]
@@ -320,40 +404,35 @@ __global__ void to_half_kernel(const float* __restrict__ p, int n, __half* __res
     if (e < n) h[e] = __float2half_rn(p[e]);
 }
 
-// Top-K per form by logit (iterated block argmax).  Confidence of a form: 1 - sigmoid of
-// the best bin left out, i.e. how sure the net is that no line was left behind.
+// Top-K per form by logit: a bitonic sort of the 512 (logit, bin) pairs in shared memory,
+// larger logit first and the lower bin first among equal logits.  Confidence of a form:
+// 1 - sigmoid of the best bin left out, i.e. how sure the net is that no line was left behind.
 __global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
                                                    float* __restrict__ conf)
 {
     __shared__ float val[NBIN];
-    __shared__ float bv[16];
-    __shared__ int bi[16];
-    const int f = blockIdx.x, tid = threadIdx.x;
-    val[tid] = logits[f * NBIN + tid];
-    for (int r = 0; r <= k; ++r) {
-        __syncthreads();
-        float v = val[tid];
-        int id = tid;
-        for (int o = 16; o > 0; o >>= 1) {
-            float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            int i2 = __shfl_xor_sync(0xffffffffu, id, o);
-            if (v2 > v || (v2 == v && i2 < id)) { v = v2; id = i2; }
-        }
-        if ((tid & 31) == 0) { bv[tid >> 5] = v; bi[tid >> 5] = id; }
-        __syncthreads();
-        if (tid == 0) {
-            float bb = bv[0];
-            int ii = bi[0];
-            for (int w = 1; w < 16; ++w)
-                if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
-            if (r < k) {
-                idx[f * k + r] = ii;
-                val[ii] = -INFINITY;
-            } else {
-                conf[f] = k < NBIN ? 1.f - 1.f / (1.f + expf(-bb)) : 1.f;
+    __shared__ int bin[NBIN];
+    const int f = blockIdx.x, t = threadIdx.x;
+    val[t] = logits[f * NBIN + t];
+    bin[t] = t;
+    for (int size = 2; size <= NBIN; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            const int j = t ^ stride;
+            if (j > t) {
+                const float va = val[t], vb = val[j];
+                const int ia = bin[t], ib = bin[j];
+                const bool a_first = va > vb || (va == vb && ia < ib);
+                if (a_first != ((t & size) == 0)) {
+                    val[t] = vb; val[j] = va;
+                    bin[t] = ib; bin[j] = ia;
+                }
             }
         }
     }
+    __syncthreads();
+    if (t < k) idx[f * k + t] = bin[t];
+    if (t == 0) conf[f] = k < NBIN ? 1.f - 1.f / (1.f + expf(-val[k])) : 1.f;
 }
 
 }  // namespace
@@ -378,8 +457,10 @@ struct cyc_net {
     __half* feats = nullptr;  // [1][NIN][4096] for cyc_propose
     float2* xbuf = nullptr;   // staging for a host signal
     int64_t xcap = 0;
-    int* topi = nullptr;
+    int* topi = nullptr;      // [2][NBIN] proposals, then (at 2 NBIN) the two confidences as floats
     float* conf = nullptr;
+    float* pg = nullptr;      // [NIN][NSEG][NFFT] one signal's segment periodograms (cyc_propose)
+    int* h_res = nullptr;     // page-locked copy of topi and conf
 
     void free_acts()
     {
@@ -408,24 +489,35 @@ int ensure_batch(cyc_net* n, int B)
     return CYC_OK;
 }
 
-size_t conv_smem(int cin) { return (size_t)cin * (128 + 8) * 4 + (size_t)32 * cin * KW * 4; }
+size_t conv_smem(int cin, int ti) { return (size_t)cin * (ti + 8) * 4 + (size_t)32 * cin * KW * 4; }
 
-template <typename TI, typename TO>
-cudaError_t conv(const TI* x, int cin, int cout, const __half* w, const float* bias, int relu, const __half* mask,
-                 TO* y, int B, cudaStream_t st)
+// Batches of at most kSmallBatch signals take the narrow tiles (latency of one proposal).
+constexpr int kSmallBatch = 2;
+
+template <typename TI, typename TO, int MP>
+cudaError_t conv_mp(const TI* x, int cin, int cout, const __half* w, const float* bias, int relu, const __half* mask,
+                    TO* y, int B, cudaStream_t st)
 {
     static bool set[64] = {false};                        // the attribute is per device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)conv_smem(64));
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<TI, TO, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)conv_smem(64, 32 * MP));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) set[dev] = true;
     }
-    dim3 grid(NFFT / 128, (cout + 31) / 32, B);
-    conv_kernel<TI, TO><<<grid, 256, conv_smem(cin), st>>>(x, cin, cout, w, bias, relu, mask, y);
+    dim3 grid(NFFT / (32 * MP), (cout + 31) / 32, B);
+    conv_kernel<TI, TO, MP><<<grid, 256, conv_smem(cin, 32 * MP), st>>>(x, cin, cout, w, bias, relu, mask, y);
     return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t conv(const TI* x, int cin, int cout, const __half* w, const float* bias, int relu, const __half* mask,
+                 TO* y, int B, cudaStream_t st)
+{
+    if (B <= kSmallBatch) return conv_mp<TI, TO, 1>(x, cin, cout, w, bias, relu, mask, y, B, st);
+    return conv_mp<TI, TO, 4>(x, cin, cout, w, bias, relu, mask, y, B, st);
 }
 
 // forward of B feature sets; leaves h[1..3], z4 and (pooled) logits in the net's buffers
@@ -438,7 +530,22 @@ int net_forward(cyc_net* n, const __half* feats, int B, cudaStream_t st)
         PCK((conv<__half, __half>(in, CHS[l], CHS[l + 1], n->ph + LAY.w[l], n->p + LAY.b[l], 1, nullptr, n->h[l + 1], B, st)));
         in = n->h[l + 1];
     }
-    PCK((conv<__half, float>(in, CHS[NL - 1], CHS[NL], n->ph + LAY.w[NL - 1], n->p + LAY.b[NL - 1], 0, nullptr, n->z4, B, st)));
+    if (B <= kSmallBatch) {
+        const size_t sm = (size_t)CHS[NL - 1] * (256 + 8) * 4 + (size_t)2 * CHS[NL - 1] * KW * 4;
+        static bool set[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !set[dev]) {
+            PCK(cudaFuncSetAttribute(conv_out2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            if (dev >= 0 && dev < 64) set[dev] = true;
+        }
+        conv_out2_kernel<<<dim3(NFFT / 256, 1, B), 256, sm, st>>>(in, CHS[NL - 1], n->ph + LAY.w[NL - 1],
+                                                               n->p + LAY.b[NL - 1], n->z4);
+        PCK(cudaGetLastError());
+    } else {
+        PCK((conv<__half, float>(in, CHS[NL - 1], CHS[NL], n->ph + LAY.w[NL - 1], n->p + LAY.b[NL - 1], 0, nullptr,
+                                 n->z4, B, st)));
+    }
     return CYC_OK;
 }
 
@@ -520,8 +627,10 @@ int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out
     chk(cudaMalloc(&n->wt, 64 * 64 * KW * sizeof(__half)));
     chk(cudaMalloc(&n->loss, sizeof(float)));
     chk(cudaMalloc(&n->feats, NIN * NFFT * sizeof(__half)));
-    chk(cudaMalloc(&n->topi, 2 * NBIN * sizeof(int)));
-    chk(cudaMalloc(&n->conf, 2 * sizeof(float)));
+    chk(cudaMalloc(&n->topi, (2 * NBIN + 2) * sizeof(int)));
+    n->conf = reinterpret_cast<float*>(n->topi + 2 * NBIN);
+    chk(cudaMalloc(&n->pg, (size_t)NIN * NSEG * NFFT * sizeof(float)));
+    chk(cudaMallocHost(&n->h_res, (2 * NBIN + 2) * sizeof(int)));
     if (rc == CYC_OK) {
         chk(cudaMemcpy(n->p, host.data(), LAY.total * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
@@ -542,9 +651,10 @@ int cyc_net_destroy(cyc_net* n)
     if (!n) return CYC_OK;
     cudaSetDevice(n->device);
     n->free_acts();
-    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->conf};
+    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->pg};
     for (void* q : ps)
         if (q) cudaFree(q);
+    if (n->h_res) cudaFreeHost(n->h_res);
     delete n;
     return CYC_OK;
 }
@@ -652,17 +762,32 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
         PCK(cudaMemcpy(n->xbuf, x, use * sizeof(float2), cudaMemcpyHostToDevice));
         xd = n->xbuf;
     }
-    int rc = cyc_features(xd, use, 1, n->feats);
-    if (rc) return rc;
-    rc = net_forward(n, n->feats, 1, 0);
+    // features of one signal: a CTA per (channel, segment), then one per channel
+    {
+        static bool set[64] = {false};
+        const int smem = NFFT * 8 + NFFT / 2 * 8;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !set[dev]) {
+            PCK(cudaFuncSetAttribute(periodogram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            if (dev >= 0 && dev < 64) set[dev] = true;
+        }
+        periodogram_kernel<<<NIN * NSEG, 512, smem>>>(xd, n->pg);
+        features_finish_kernel<<<NIN, 512>>>(n->pg, n->feats);
+        PCK(cudaGetLastError());
+    }
+    int rc = net_forward(n, n->feats, 1, 0);
     if (rc) return rc;
     pool_loss_kernel<<<(2 * NBIN + 255) / 256, 256>>>(n->z4, nullptr, 1, 1.f, n->logits, nullptr, nullptr);
     topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf);
     PCK(cudaGetLastError());
-    std::vector<int> idx(2 * k);
+    // one synchronisation: the proposals [2][k] and the confidences (stored after them)
+    PCK(cudaMemcpyAsync(n->h_res, n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost, 0));
+    PCK(cudaMemcpyAsync(n->h_res + 2 * NBIN, n->conf, 2 * sizeof(float), cudaMemcpyDeviceToHost, 0));
+    PCK(cudaStreamSynchronize(0));
+    const int* idx = n->h_res;
     float cf[2];
-    PCK(cudaMemcpy(idx.data(), n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost));
-    PCK(cudaMemcpy(cf, n->conf, sizeof cf, cudaMemcpyDeviceToHost));
+    memcpy(cf, n->h_res + 2 * NBIN, sizeof cf);
     for (int r = 0; r < k; ++r) {
         alphas_conv[r] = -0.5 + idx[r] / (double)NBIN;
         alphas_conj[r] = -0.5 + idx[k + r] / (double)NBIN;

@@ -116,3 +116,24 @@ def test_trained_proposer_recall_and_gain(cyc):
     assert r["detections"] >= 100, r
     assert r["recall"] >= 0.99, r
     assert r["work_ratio"] > 4.0, r
+
+
+def test_propose_path_equals_the_batch_path(cyc, signals):
+    """cyc_propose computes one signal's features with a CTA per (channel, segment); its
+    proposals must be the top-k of the logits that the batch path (cyc_features, one CTA per
+    channel, then cyc_net_forward) gives for the same signal."""
+    import torch
+    net = cyc.cyc_net_create(None, 21)
+    try:
+        f = gpu_features(cyc, signals[:1])
+        logits = torch.empty((1, 2, 512), dtype=torch.float32, device="cuda")
+        cyc.cyc_net_forward(net, f, 1, logits)
+        lg = logits.cpu().numpy()[0]
+        xd = torch.from_numpy(signals[0].view(np.float32).copy()).cuda()
+        ac, aj, conf, fb = cyc.cyc_propose(net, xd, NS, k=16, tau=0.0)
+        for form, al in ((0, ac), (1, aj)):
+            got = set(np.round((np.asarray(al) + 0.5) * 512).astype(int).tolist())
+            order = np.argsort(-lg[form], kind="stable")
+            assert got == set(order[:16].tolist()), form
+    finally:
+        cyc.cyc_net_destroy(net)
