@@ -634,15 +634,21 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- our arm
 
-def time_device_steps(pkg, x_dev, lags, alphas, precision, steps, warmup, world, profile):
+def time_device_steps(pkg, x_dev, lags, alphas, precision, steps, warmup, world, profile, n0=0, merge=False):
+    """Steps over the device-resident samples x_dev (pushes of CHUNK samples, the last one
+    possibly shorter); merge=True: the ranks hold time shards of one stream (start index
+    n0), merged by one in-place all-reduce of the running sums before the read."""
     import torch
+    from paper_2405_16911_gb300 import shard
     out = torch.empty((NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
-    nchunks = x_dev.numel() // (2 * CHUNK)
-    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK) as s:
+    nsamp = x_dev.numel() // 2
+    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK, n0=n0) as s:
         def step():
             s.reset()
-            for c in range(nchunks):
-                s.push(x_dev[2 * c * CHUNK:2 * (c + 1) * CHUNK])
+            for c0 in range(0, nsamp, CHUNK):
+                s.push(x_dev[2 * c0:2 * min(c0 + CHUNK, nsamp)])
+            if merge:
+                shard.allreduce_stream(s)
             s.read(out)
         for _ in range(warmup):
             step()
@@ -702,16 +708,24 @@ def run_ours(args):
             raise
         precision = "fp32"
 
-    w = workloads.config1(T=args.samples, replica=rank)
+    sharded = args.shard and world > 1
+    w = workloads.config1(T=args.samples, replica=0 if sharded else rank)
     x, lags, alphas = w["x"], w["lags"], w["alphas"]
-    x_dev = torch.from_numpy(x.view(np.float32)).cuda()
+    n0 = 0
+    if sharded:
+        # one stream of T samples cut into time shards, one per rank (strong scaling)
+        from paper_2405_16911_gb300 import shard
+        s0, s1, n0, _ = shard.time_shards(x.size, NLAGS - 1, world)[rank]
+        x_dev = torch.from_numpy(np.ascontiguousarray(x[s0:s1]).view(np.float32)).cuda()
+    else:
+        x_dev = torch.from_numpy(x.view(np.float32)).cuda()
 
     sampler = ClockSampler(uuid)
     ms, R, proj_ms, proj_launches, kernels = time_device_steps(
-        pkg, x_dev, lags, alphas, precision, args.steps, args.warmup, world, True)
+        pkg, x_dev, lags, alphas, precision, args.steps, args.warmup, world, True, n0=n0, merge=sharded)
     clocks = sampler.stop()
     ms = max_over_ranks(ms, world)
-    cmac = cmac_per_step() * world
+    cmac = cmac_per_step() * (1 if sharded else world)
     value = cmac / (ms * 1e-3) / 1e9
 
     # roofline of the projection kernel (the dominant kernel of the step)
@@ -722,7 +736,7 @@ def run_ours(args):
             peaks = json.load(f)
     except OSError:
         pass
-    cmac_launch = cmac_per_step() * args.steps / max(proj_launches, 1)
+    cmac_launch = cmac_per_step() / (world if sharded else 1) * args.steps / max(proj_launches, 1)
     avg_launch_s = proj_ms * 1e-3 / max(proj_launches, 1)
     if precision == "fp32":
         clk = float(peaks.get("sm_max_mhz", 2070.0))
@@ -750,10 +764,11 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "fp16": "f16"}[precision],
         "data": "synthetic", "config": workload_config(precision),
-        "msamples_per_s": ARGS_SAMPLES[0] * world / (ms * 1e-3) / 1e6,
+        "msamples_per_s": ARGS_SAMPLES[0] * (1 if sharded else world) / (ms * 1e-3) / 1e6,
         "precision": {"fp32": "fp32 CUDA-core projection", "bf16x3": "bf16 hi/lo split, 3 products, fp32 accumulate",
                       "fp16": "fp16 single pass, fp32 accumulate"}[precision] + "; fp64 running sums",
         "gpu_launches": kernels, "roofline": roof, "clocks": clocks,
@@ -837,6 +852,9 @@ def main():
     ap.add_argument("--no-windows", action="store_true", help="skip the windowed-output leg")
     ap.add_argument("--no-full", action="store_true", help="skip the Full-mode leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1 ranks: cut one config-1 stream into N time shards and merge them with one "
+                         "all-reduce of the running sums (strong scaling) instead of N independent replicas")
     ap.add_argument("--samples", type=int, default=T_SAMPLES,
                     help="stream length per step (multiple of 2^16); smaller values only for profiling")
     args = ap.parse_args()

@@ -266,6 +266,27 @@ CYC_API int cyc_profile(cyc_stream* s, int enable);
 CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels);
 
 /*
+ * cyc_sums / cyc_set_n_eff: the stream's raw running sums for merging time shards of one
+ * stream across GPUs (one process per GPU).  Because the phase uses the absolute sample
+ * index, shard r of a stream -- a handle with the same lags, alphas, forms and precision,
+ * start index n0 + a_r, fed samples [a_r, b_r + M) of the stream -- holds exactly the sums
+ * of the committed terms [a_r, b_r); the whole stream's sums are their SUM and its N_eff
+ * the SUM of the counts.
+ *   cyc_sums      waits for the stream's work and returns the device address of its FP64
+ *                 running sums (*nvalues complex values, interleaved re, im; an internal
+ *                 layout that is the same for handles created with the same parameters) and
+ *                 its N_eff.  The array stays the handle's; a caller may add into it in place
+ *                 (e.g. a SUM all-reduce across the ranks' handles) while no push is queued.
+ *   cyc_set_n_eff sets the count cyc_read (and cyc_read_spectrum, cyc_detect) divides by:
+ *                 after merging, the total of the ranks' counts.  The handle then describes
+ *                 the merged stream for reading; pushing more samples into it afterwards does
+ *                 not continue that stream (cyc_reset first).
+ * CYC_ENOTSUP for windowed streams.
+ */
+CYC_API int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff);
+CYC_API int cyc_set_n_eff(cyc_stream* s, int64_t n_eff);
+
+/*
  * cyc_set_wait_budget: how long (SM clock cycles) each bounded wait inside the stream's
  * tensor-core projection kernel waits for a producer, a copy or the tensor core before it
  * gives up; 0 restores the default of 2e9 (about a second at 2 GHz).  A wait that gives up

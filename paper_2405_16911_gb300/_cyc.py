@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
         "cyc_read_spectrum": ([P, I32, I32, P], I),
         "cyc_detect": ([P, ctypes.c_double, I32, P, P, P], I),
         "cyc_set_wait_budget": ([P, I64], I),
+        "cyc_sums": ([P, P, P, P], I),
+        "cyc_set_n_eff": ([P, I64], I),
         "cyc_push": ([P, P, I64, I], I),
         "cyc_push_xy": ([P, P, P, I64, I], I),
         "cyc_read": ([P, P, P], I),
@@ -356,6 +358,28 @@ def cyc_estimate_static(x, T: int, lags, alphas, conj_flag: int, n0: int, out, c
 def cyc_set_wait_budget(h: int, cycles: int) -> None:
     """SM cycles each bounded wait of the stream's tensor-core kernel waits (0: default)."""
     _check(load().cyc_set_wait_budget(h, int(cycles)))
+
+
+class _DeviceArray:
+    """A device buffer of the library, exposed to torch through __cuda_array_interface__."""
+
+    def __init__(self, addr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (addr, False), "version": 3}
+
+
+def cyc_sums(h: int):
+    """(torch float64 tensor viewing the stream's device running sums, n_eff); adding into
+    the tensor in place adds into the stream's sums (see include/cyc.h)."""
+    import torch
+    p = ctypes.c_void_p(0)
+    nv = ctypes.c_int64(0)
+    ne = ctypes.c_int64(0)
+    _check(load().cyc_sums(h, ctypes.byref(p), ctypes.byref(nv), ctypes.byref(ne)))
+    return torch.as_tensor(_DeviceArray(p.value, 2 * nv.value), device="cuda"), int(ne.value)
+
+
+def cyc_set_n_eff(h: int, n_eff: int) -> None:
+    _check(load().cyc_set_n_eff(h, int(n_eff)))
 
 
 def cyc_phase_increment(a: float) -> int:
@@ -639,6 +663,12 @@ class Stream:
 
     def set_wait_budget(self, cycles: int):
         cyc_set_wait_budget(self.h, cycles)
+
+    def sums(self):
+        return cyc_sums(self.h)
+
+    def set_n_eff(self, n_eff: int):
+        cyc_set_n_eff(self.h, n_eff)
 
     def sync(self):
         cyc_sync(self.h)

@@ -102,6 +102,26 @@ struct BlobHeader {
 
 void cyc::record_error(const char* msg) { g_err = msg; }
 
+namespace {
+thread_local int g_alloc_fail_at = 0, g_alloc_count = 0;
+}
+
+void cyc::test_alloc_arm()
+{
+    const char* ev = getenv("CYC_TEST_FAIL_ALLOC");
+    g_alloc_fail_at = ev ? atoi(ev) : 0;
+    g_alloc_count = 0;
+}
+
+cudaError_t cyc::dev_malloc(void** p, size_t bytes)
+{
+    if (g_alloc_fail_at > 0 && ++g_alloc_count == g_alloc_fail_at) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 struct cyc_stream {
     int device = 0;
     cudaStream_t st = nullptr;
@@ -239,18 +259,18 @@ int alloc_state(cyc_stream* s)
 {
     size_t stage_n = (size_t)(s->M + s->max_chunk + kStagePad);
     for (int b = 0; b < 2; ++b) {
-        CK(cudaMalloc(&s->stage[b], stage_n * sizeof(float2)));
+        CK(dev_malloc((void**)&s->stage[b], stage_n * sizeof(float2)));
         CK(cudaMemset(s->stage[b], 0, stage_n * sizeof(float2)));
         if (s->cross) {
-            CK(cudaMalloc(&s->stage_y[b], stage_n * sizeof(float2)));
+            CK(dev_malloc((void**)&s->stage_y[b], stage_n * sizeof(float2)));
             CK(cudaMemset(s->stage_y[b], 0, stage_n * sizeof(float2)));
         }
     }
-    CK(cudaMalloc(&s->sums, (size_t)s->Au * s->ncols * sizeof(double2)));
+    CK(dev_malloc((void**)&s->sums, (size_t)s->Au * s->ncols * sizeof(double2)));
     CK(cudaMemset(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2)));
-    CK(cudaMalloc(&s->d_phi, s->Au * sizeof(uint64_t)));
+    CK(dev_malloc((void**)&s->d_phi, s->Au * sizeof(uint64_t)));
     CK(cudaMemcpy(s->d_phi, s->phi_u.data(), s->Au * sizeof(uint64_t), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&s->d_amap, s->A * sizeof(int32_t)));
+    CK(dev_malloc((void**)&s->d_amap, s->A * sizeof(int32_t)));
     CK(cudaMemcpy(s->d_amap, s->amap.data(), s->A * sizeof(int32_t), cudaMemcpyHostToDevice));
     std::vector<int32_t> cl(s->ncols);
     std::vector<int8_t> cc(s->ncols);
@@ -260,9 +280,9 @@ int alloc_state(cyc_stream* s)
             cl[l * s->F + f] = s->lags[l] + s->Mneg;        // shifted lag m + M^- >= 0
             cc[l * s->F + f] = s->forms[f] == CYC_CONJ ? 1 : 0;
         }
-    CK(cudaMalloc(&s->d_col_lag, s->ncols * sizeof(int32_t)));
+    CK(dev_malloc((void**)&s->d_col_lag, s->ncols * sizeof(int32_t)));
     CK(cudaMemcpy(s->d_col_lag, cl.data(), s->ncols * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&s->d_col_conj, s->ncols * sizeof(int8_t)));
+    CK(dev_malloc((void**)&s->d_col_conj, s->ncols * sizeof(int8_t)));
     CK(cudaMemcpy(s->d_col_conj, cc.data(), s->ncols * sizeof(int8_t), cudaMemcpyHostToDevice));
     if (s->precision != CYC_P_FP32)
         s->part_elems = tc_max_partials(s->units.U, s->Au, s->ncols, s->num_sms);
@@ -272,18 +292,18 @@ int alloc_state(cyc_stream* s)
         s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
     if (s->win && s->part_elems < (size_t)kWinSplits * s->Au * s->ncols)
         s->part_elems = (size_t)kWinSplits * s->Au * s->ncols;
-    CK(cudaMalloc(&s->part, s->part_elems * sizeof(float2)));
+    CK(dev_malloc((void**)&s->part, s->part_elems * sizeof(float2)));
     if (s->win) {
         const size_t nuc = (size_t)s->Au * s->ncols;
-        CK(cudaMalloc(&s->w_ring, (size_t)s->win_w * nuc * sizeof(float2)));
-        CK(cudaMalloc(&s->w_sum, nuc * sizeof(float4)));
-        CK(cudaMalloc(&s->w_pend, nuc * sizeof(float4)));
-        CK(cudaMalloc(&s->w_out, (size_t)s->win_cap * nuc * sizeof(float2)));
+        CK(dev_malloc((void**)&s->w_ring, (size_t)s->win_w * nuc * sizeof(float2)));
+        CK(dev_malloc((void**)&s->w_sum, nuc * sizeof(float4)));
+        CK(dev_malloc((void**)&s->w_pend, nuc * sizeof(float4)));
+        CK(dev_malloc((void**)&s->w_out, (size_t)s->win_cap * nuc * sizeof(float2)));
         CK(cudaMemset(s->w_sum, 0, nuc * sizeof(float4)));
         CK(cudaMemset(s->w_pend, 0, nuc * sizeof(float4)));
     }
-    CK(cudaMalloc(&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
-    CK(cudaMalloc(&s->d_err, sizeof(int)));
+    CK(dev_malloc((void**)&s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2)));
+    CK(dev_malloc((void**)&s->d_err, sizeof(int)));
     CK(cudaMemset(s->d_err, 0, sizeof(int)));
     CK(cudaMallocHost(&s->h_err, sizeof(int)));
     *s->h_err = 0;
@@ -522,6 +542,7 @@ static int create_impl(const cyc_params* p, bool cross, int64_t win_len, int64_t
         const char* ev = getenv("CYC_TEST_WITHHOLD_ARRIVAL");
         s->withhold = (ev && ev[0] == '1') ? 1 : 0;
     }
+    test_alloc_arm();
     rc = alloc_state(s);
     if (rc) {
         s->free_all();
@@ -692,7 +713,7 @@ int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
     if (wrong) return fail(CYC_EINVAL, "cyc_read_spectrum: out is memory of another device");
     if (dev && misaligned16(out)) return fail(CYC_EINVAL, "cyc_read_spectrum: device out must be 16-byte aligned");
     if (!s->d_lags) {
-        CK(cudaMalloc(&s->d_lags, (size_t)s->L * sizeof(int32_t)));
+        CK(dev_malloc((void**)&s->d_lags, (size_t)s->L * sizeof(int32_t)));
         CK(cudaMemcpy(s->d_lags, s->lags.data(), (size_t)s->L * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     if (Q > s->sp_Q) {
@@ -737,11 +758,11 @@ int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* 
     if (rdev && ((uintptr_t)ratio & 3) != 0) return fail(CYC_EINVAL, "cyc_detect: device ratio must be 4-byte aligned");
     const size_t nfa = (size_t)s->F * s->A;
     if (!s->dt_s) {
-        CK(cudaMalloc(&s->dt_s, nfa * sizeof(double)));
-        CK(cudaMalloc(&s->dt_flags, nfa));
-        CK(cudaMalloc(&s->dt_ratio, nfa * sizeof(float)));
-        CK(cudaMalloc(&s->dt_count, sizeof(int)));
-        CK(cudaMalloc(&s->dt_dc, (size_t)s->A));
+        CK(dev_malloc((void**)&s->dt_s, nfa * sizeof(double)));
+        CK(dev_malloc((void**)&s->dt_flags, nfa));
+        CK(dev_malloc((void**)&s->dt_ratio, nfa * sizeof(float)));
+        CK(dev_malloc((void**)&s->dt_count, sizeof(int)));
+        CK(dev_malloc((void**)&s->dt_dc, (size_t)s->A));
         std::vector<uint8_t> dc(s->A);
         for (int i = 0; i < s->A; ++i) dc[i] = (!s->cross && alpha_to_phi(s->alphas[i]) == 0) ? 1 : 0;
         CK(cudaMemcpy(s->dt_dc, dc.data(), (size_t)s->A, cudaMemcpyHostToDevice));
@@ -908,6 +929,27 @@ int cyc_phase_increment(double a, uint64_t* phi)
 {
     if (!phi || !isfinite(a)) return fail(CYC_EINVAL, "cyc_phase_increment: a must be finite, phi non-NULL");
     *phi = alpha_to_phi(a);
+    return CYC_OK;
+}
+
+int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff)
+{
+    if (!s || !sums) return fail(CYC_EINVAL, "cyc_sums: NULL argument");
+    if (s->win) return fail(CYC_ENOTSUP, "cyc_sums: windowed streams keep their windows apart from the sums");
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->st));
+    *sums = (double*)s->sums;
+    if (nvalues) *nvalues = (int64_t)s->Au * s->ncols;
+    if (n_eff) *n_eff = s->n_eff;
+    return CYC_OK;
+}
+
+int cyc_set_n_eff(cyc_stream* s, int64_t n_eff)
+{
+    if (!s) return fail(CYC_EINVAL, "cyc_set_n_eff: handle is NULL");
+    if (n_eff < 0) return fail(CYC_EINVAL, "cyc_set_n_eff: n_eff < 0");
+    if (s->win) return fail(CYC_ENOTSUP, "cyc_set_n_eff: not for windowed streams");
+    s->n_eff = n_eff;
     return CYC_OK;
 }
 

@@ -235,6 +235,13 @@ cudaError_t detect(const double2* R, int F, int A, int L, const uint8_t* dc, int
 cudaError_t tc_launch_items(const TcItem* items, const int* nitems, int* counter, int grid, int precision, int* err,
                             long long budget, cudaStream_t st);
 
+// Device allocation of the stream and server set-up paths.  Test hook: with the environment
+// variable CYC_TEST_FAIL_ALLOC=k at the start of a cyc_create_* or cyc_server_open call, the
+// k-th allocation of that call fails as if the device were out of memory (nothing is
+// allocated), so that the tests can check that a failed admission leaves nothing behind.
+void        test_alloc_arm();       // reads the hook at the start of a set-up call
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // Sets the calling thread's message returned by cyc_last_error() (cyc_api.cu).
 void record_error(const char* msg);
 

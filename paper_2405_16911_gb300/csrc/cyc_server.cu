@@ -586,6 +586,7 @@ int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const doubl
                          nalphas * sizeof(int32_t) + ncols * 5 + (size_t)F * nalphas * nlags * sizeof(double2);
     DevGuard g(srv->p.device);
     std::lock_guard<std::mutex> lk(srv->admin);
+    test_alloc_arm();
     int slot = -1;
     for (int i = 0; i < (int)srv->streams.size(); ++i)
         if (!srv->streams[i]->open && !srv->streams[i]->closing.load()) {
@@ -606,13 +607,13 @@ int cyc_server_open(cyc_server* srv, const int32_t* lags, int nlags, const doubl
                      cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&s.ring, cap * sizeof(float2))) != cudaSuccess) return fail_free(e, "ring");
-    if ((e = cudaMalloc(&s.sums, (size_t)Au * ncols * sizeof(double2))) != cudaSuccess) return fail_free(e, "sums");
-    if ((e = cudaMalloc(&s.d_phi, Au * sizeof(uint64_t))) != cudaSuccess) return fail_free(e, "tables");
-    if ((e = cudaMalloc(&s.d_amap, nalphas * sizeof(int32_t))) != cudaSuccess) return fail_free(e, "tables");
-    if ((e = cudaMalloc(&s.d_col_lag, ncols * sizeof(int32_t))) != cudaSuccess) return fail_free(e, "tables");
-    if ((e = cudaMalloc(&s.d_col_conj, ncols * sizeof(int8_t))) != cudaSuccess) return fail_free(e, "tables");
-    if ((e = cudaMalloc(&s.d_out, (size_t)F * nalphas * nlags * sizeof(double2))) != cudaSuccess)
+    if ((e = dev_malloc((void**)&s.ring, cap * sizeof(float2))) != cudaSuccess) return fail_free(e, "ring");
+    if ((e = dev_malloc((void**)&s.sums, (size_t)Au * ncols * sizeof(double2))) != cudaSuccess) return fail_free(e, "sums");
+    if ((e = dev_malloc((void**)&s.d_phi, Au * sizeof(uint64_t))) != cudaSuccess) return fail_free(e, "tables");
+    if ((e = dev_malloc((void**)&s.d_amap, nalphas * sizeof(int32_t))) != cudaSuccess) return fail_free(e, "tables");
+    if ((e = dev_malloc((void**)&s.d_col_lag, ncols * sizeof(int32_t))) != cudaSuccess) return fail_free(e, "tables");
+    if ((e = dev_malloc((void**)&s.d_col_conj, ncols * sizeof(int8_t))) != cudaSuccess) return fail_free(e, "tables");
+    if ((e = dev_malloc((void**)&s.d_out, (size_t)F * nalphas * nlags * sizeof(double2))) != cudaSuccess)
         return fail_free(e, "read buffer");
     if ((e = cudaMemset(s.sums, 0, (size_t)Au * ncols * sizeof(double2))) != cudaSuccess ||
         (e = cudaMemcpy(s.d_phi, phi_u.data(), Au * sizeof(uint64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||

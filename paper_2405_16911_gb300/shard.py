@@ -7,14 +7,16 @@ estimate R_r (over N_r = b_r - a_r terms) and the others combine exactly by
 
     R = sum_r N_r R_r / sum_r N_r
 
-which is one SUM reduction of F*A*L complex FP64 values (and the counts) at read time.
-Independent streams (serving) need no exchange at all.
+which is one SUM reduction of F*A*L complex FP64 values (and the counts) at read time:
+allreduce_stream() adds the ranks' libcyc running sums in place on the device (NCCL) and
+sets the merged count, so that the library's own read divides by it.  Independent streams
+(serving) need no exchange at all.
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["time_shards", "merge", "allreduce_merge"]
+__all__ = ["time_shards", "merge", "allreduce_merge", "allreduce_stream"]
 
 
 def time_shards(T: int, M: int, world: int):
@@ -65,3 +67,19 @@ def allreduce_merge(R_local, n_local: int, group=None):
         return None, 0
     Rm = out[:-1].view(np.complex128).reshape(R.shape) / n
     return Rm, n
+
+
+def allreduce_stream(stream, group=None) -> int:
+    """Merge the time shards held by every rank's libcyc stream (same parameters, start index
+    of its shard): one in-place SUM all-reduce of the stream's FP64 device sums and one of the
+    counts; afterwards stream.read() returns the whole stream's estimate.  Returns N_eff."""
+    import torch
+    import torch.distributed as dist
+    sums, n = stream.sums()
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+    cnt = torch.tensor([n], dtype=torch.int64, device=sums.device)
+    dist.all_reduce(cnt, op=dist.ReduceOp.SUM, group=group)
+    total = int(cnt.item())                 # waits for both reductions (one NCCL stream, in order)
+    torch.cuda.synchronize()
+    stream.set_n_eff(total)
+    return total
