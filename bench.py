@@ -543,18 +543,18 @@ def full_big_pushes(pkg, x_dev, out, T, CB, reps):
 
 def full_leg(pkg, x_dev, reps=2):
     """The paper's Full mode on the config-1 workload: every cycle frequency -1/2 + k/1024 (the
-    config-1 grid itself), lags 0..127, both forms, the whole stream in 2^16-sample pushes, one
-    read at the end.  The lag products (FP32) are folded modulo 1024 in float-float and one
-    FP64 DFT per column runs at the read: a different algorithm from the projection, bound by
-    the latency of the fold's sample reads rather than by the tensor pipe.  Reported: device
-    time, samples/s, the direct estimator's complex MACs per second for the same output, the
-    error on the stored oracle entries, and the same stream pushed in 2^20-sample chunks
-    (fewer per-push copies and launches for the same work)."""
+    config-1 grid itself), lags 0..127, both forms, the whole stream in 2^16-sample device
+    pushes, one read at the end.  The lag products (FP32) are folded modulo 1024 in float-float
+    (one launch folds up to 16 pending pushes, read in place) and one FP64 DFT per column runs
+    at the read: a different algorithm from the projection, bound by shared-memory traffic
+    rather than by the tensor pipe.  Reported: device time, samples/s, the direct estimator's
+    complex MACs per second for the same output, the error on the stored oracle entries, and
+    the same stream pushed in 2^20-sample chunks with max_chunk 2^20."""
     import torch
     C = CHUNK
     T = x_dev.numel() // 2
     out = torch.empty((NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
-    with pkg.Stream(np.arange(NLAGS), None, pkg.CYC_BOTH, max_chunk=C, full=NALPHAS) as s:
+    with pkg.Stream(np.arange(NLAGS), None, pkg.CYC_BOTH, full=NALPHAS) as s:
         def run():
             s.reset()
             for c in range(T // C):

@@ -152,10 +152,16 @@ CYC_API int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop,
  * phase depends on n only through n mod A, so a push folds its lag products modulo A
  * (float-float sums of FP32 runs, about 48 significant bits) and cyc_read takes one A-point
  * DFT per column: O(samples x columns) work per push instead of O(samples x columns x A).
+ * Pushes are folded in batches: 8-byte aligned device chunks are read where they are and
+ * folded, up to 16 chunks and max_chunk samples at a time, in one launch (when the next push
+ * would not fit, and before any call that reads or replaces the stream's state: cyc_read,
+ * cyc_sync, cyc_save, cyc_load, cyc_reset, cyc_info, ...).  As for every stream, a device
+ * chunk must stay unchanged until the next cyc_read / cyc_sync.
  *   A          power of two in [2, 4096]
  *   precision  must be CYC_P_FP32 (FP32 lag products, float-float folding, FP64 DFT); else CYC_EINVAL
  *   cross      0: one input (cyc_push); 1: two inputs (cyc_push_xy)
- * cyc_save / cyc_load, cyc_reset work as for any stream; windows are not available.
+ * cyc_save / cyc_load, cyc_reset work as for any stream; cyc_sums returns CYC_ENOTSUP (the
+ * folds are float-float, not FP64 sums); windows are not available.
  */
 CYC_API int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_stream** out);
 
@@ -281,7 +287,7 @@ CYC_API int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launc
  *                 after merging, the total of the ranks' counts.  The handle then describes
  *                 the merged stream for reading; pushing more samples into it afterwards does
  *                 not continue that stream (cyc_reset first).
- * CYC_ENOTSUP for windowed streams.
+ * CYC_ENOTSUP for windowed streams and for Full-mode streams (cyc_create_full).
  */
 CYC_API int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff);
 CYC_API int cyc_set_n_eff(cyc_stream* s, int64_t n_eff);

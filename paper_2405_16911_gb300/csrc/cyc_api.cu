@@ -138,6 +138,16 @@ struct cyc_stream {
     bool cross = false;             // two inputs (cyc_create_xy / cyc_push_xy)
     // uniform grid a_k = -1/2 + k/A (cyc_create_full): sums holds the lag products folded mod A
     bool full = false;
+    int32_t* d_fsl = nullptr;       // Full mode: shifted lags in ascending order
+    int32_t* d_fperm = nullptr;     // Full mode: the lag index of each sorted position
+    int fxl = 0;                    // Full mode: x samples per staged row of the fold
+    bool fcons = false;             // Full mode: each 16-lag tile of sorted lags is consecutive
+    // Full mode: pushes not folded yet (one launch folds them all): x, y and length; host
+    // chunks and misaligned device chunks are copied into stage[cur] after the tail first
+    struct Pend { const float2* x; const float2* y; int64_t c; };
+    std::vector<Pend> fpend;
+    int64_t fpend_total = 0;
+    bool fpend_host = false;        // a host copy on the copy stream feeds the pending fold
     // windowed output (cyc_create_window): window k covers committed n in [k hop, k hop + N)
     bool win = false;
     int64_t win_len = 0, hop = 0, win_cap = 0;
@@ -212,7 +222,7 @@ struct cyc_stream {
             if (e) { cudaEventDestroy(e); e = nullptr; }
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
                       part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S,
-                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count};
+                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count, d_fsl, d_fperm};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
@@ -225,6 +235,7 @@ struct cyc_stream {
         sp_E = sp_S = nullptr;
         sp_Q = 0;
         dt_s = nullptr; dt_flags = nullptr; dt_ratio = nullptr; dt_dc = nullptr; dt_count = nullptr;
+        d_fsl = d_fperm = nullptr;
     }
 };
 
@@ -284,6 +295,18 @@ int alloc_state(cyc_stream* s)
     CK(cudaMemcpy(s->d_col_lag, cl.data(), s->ncols * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(dev_malloc((void**)&s->d_col_conj, s->ncols * sizeof(int8_t)));
     CK(cudaMemcpy(s->d_col_conj, cc.data(), s->ncols * sizeof(int8_t), cudaMemcpyHostToDevice));
+    if (s->full) {                    // the fold takes the lags in ascending order, 16 per tile
+        std::vector<int32_t> perm(s->L), sl(s->L);
+        for (int l = 0; l < s->L; ++l) perm[l] = l;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t u, int32_t v) { return s->lags[u] < s->lags[v]; });
+        for (int p = 0; p < s->L; ++p) sl[p] = s->lags[perm[p]] + s->Mneg;
+        s->fxl = full_row_samples(sl.data(), s->L);
+        s->fcons = full_lags_consecutive(sl.data(), s->L);
+        CK(dev_malloc((void**)&s->d_fsl, s->L * sizeof(int32_t)));
+        CK(cudaMemcpy(s->d_fsl, sl.data(), s->L * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(dev_malloc((void**)&s->d_fperm, s->L * sizeof(int32_t)));
+        CK(cudaMemcpy(s->d_fperm, perm.data(), s->L * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     if (s->precision != CYC_P_FP32)
         s->part_elems = tc_max_partials(s->units.U, s->Au, s->ncols, s->num_sms);
     else if (small_supported(s->Au))
@@ -359,8 +382,7 @@ int project(cyc_stream* s, int64_t nc)
         }
         CK(cudaEventRecord(ev.first, s->st));
     }
-    CK(s->full                    ? full_fold(a, s->Au, s->sums, s->st)
-       : s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->st)
+    CK(s->precision != CYC_P_FP32 ? tc_launch(a, s->precision, s->st)
        : small                    ? small_launch(a, s->st)
                                   : fp32_launch(a, s->st));
     if (s->prof) {
@@ -368,9 +390,7 @@ int project(cyc_stream* s, int64_t nc)
         s->ev_pending.push_back(ev);
     }
     s->prof_launches++;
-    if (s->full) {
-        // (the fold replaced the projection above)
-    } else if (s->win) {
+    if (s->win) {
         HopArgs h;
         h.part = s->part;
         h.nsplit = pl.nsplit;
@@ -395,6 +415,129 @@ int project(cyc_stream* s, int64_t nc)
     }
     s->kernel_launches += 2;
     return CYC_OK;
+}
+
+// Fold the pending pushes of a Full-mode stream in one launch: the view is the carried tail
+// stage[cur][0, held) followed by the pending chunks; the same launch writes the view's last
+// `keep` samples to stage[cur ^ 1] as the next tail.
+int full_flush(cyc_stream* s)
+{
+    if (s->fpend.empty()) return CYC_OK;
+    const int64_t c = s->fpend_total;
+    const int64_t held_f = s->T < s->M ? s->T : s->M;       // the tail the running sums view
+    int64_t nc = held_f + c - s->M;
+    if (nc < 0) nc = 0;
+    const int64_t T2 = s->T + c;
+    const int64_t keep = T2 < s->M ? T2 : s->M;
+    FoldArgs f;
+    f.nsrc = 1 + (int)s->fpend.size();
+    f.start[0] = 0;
+    f.sx[0] = s->stage[s->cur];
+    f.sy[0] = s->cross ? s->stage_y[s->cur] : f.sx[0];
+    int64_t pos = s->held;
+    for (size_t k = 0; k < s->fpend.size(); ++k) {
+        f.start[k + 1] = (int32_t)pos;
+        f.sx[k + 1] = s->fpend[k].x;
+        f.sy[k + 1] = s->cross ? s->fpend[k].y : s->fpend[k].x;
+        pos += s->fpend[k].c;
+    }
+    f.start[f.nsrc] = (int32_t)pos;
+    f.off = s->held - held_f;
+    f.nc = nc;
+    f.D = s->Mneg;
+    f.A = s->Au;
+    f.base_mod = (uint32_t)(((uint64_t)s->n0 + (uint64_t)s->n_eff + (uint64_t)s->Mneg) & (uint64_t)(s->Au - 1));
+    f.sl = s->d_fsl;
+    f.perm = s->d_fperm;
+    f.L = s->L;
+    f.F = s->F;
+    for (int k = 0; k < s->F; ++k) {
+        if (s->forms[k] == CYC_CONV) f.fV = k;
+        if (s->forms[k] == CYC_CONJ) f.fJ = k;
+    }
+    f.xl = s->fxl;
+    f.consecutive = s->fcons;
+    f.fold = reinterpret_cast<float4*>(s->sums);
+    f.nx = s->stage[s->cur ^ 1];
+    f.ny = s->cross ? s->stage_y[s->cur ^ 1] : nullptr;
+    f.keep = keep;
+    s->fpend.clear();
+    s->fpend_total = 0;
+    if (s->fpend_host) {
+        CK(cudaStreamWaitEvent(s->st, s->ev_copied, 0));
+        s->fpend_host = false;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (s->prof && nc > 0) {
+        if (!s->ev_free.empty()) {
+            ev = s->ev_free.back();
+            s->ev_free.pop_back();
+        } else {
+            CK(cudaEventCreate(&ev.first));
+            CK(cudaEventCreate(&ev.second));
+        }
+        CK(cudaEventRecord(ev.first, s->st));
+    }
+    CK(full_fold(f, s->st));
+    if (ev.first) {
+        CK(cudaEventRecord(ev.second, s->st));
+        s->ev_pending.push_back(ev);
+        s->prof_launches++;
+    }
+    if (nc > 0 || keep > 0) s->kernel_launches += 1;
+    if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
+    s->n_eff += nc;
+    s->T = T2;
+    s->cur ^= 1;
+    s->held = keep;
+    return CYC_OK;
+}
+
+// Queue a Full-mode push: 8-byte aligned device chunks are read where they are; host chunks
+// and misaligned device chunks are copied into stage[cur] behind the tail and the chunks
+// already queued (host chunks on the copy stream).  The pending chunks are folded in one
+// launch when the next would not fit (16 chunks, max_chunk samples) and before anything
+// reads the stream's state.
+int full_push(cyc_stream* s, const float2* src, const float2* ysrc, int64_t nsamples, bool on_device)
+{
+    int64_t left = nsamples;
+    while (left > 0) {
+        int64_t c = left < s->max_chunk ? left : s->max_chunk;
+        if ((int)s->fpend.size() + 1 >= kFoldSrc || s->fpend_total + c > s->max_chunk) {
+            int rc = full_flush(s);
+            if (rc) return rc;
+        }
+        const bool direct = on_device && ((uintptr_t)src & 7) == 0 && (!s->cross || ((uintptr_t)ysrc & 7) == 0);
+        if (direct) {
+            s->fpend.push_back({src, ysrc, c});
+        } else {
+            float2* dx = s->stage[s->cur] + s->held + s->fpend_total;
+            float2* dy = s->cross ? s->stage_y[s->cur] + s->held + s->fpend_total : nullptr;
+            cudaStream_t cs = on_device ? s->st : s->xst;
+            if (!on_device) CK(cudaStreamWaitEvent(cs, s->ev_read[s->cur], 0));
+            CK(cudaMemcpyAsync(dx, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
+            if (s->cross) CK(cudaMemcpyAsync(dy, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
+            if (!on_device) {
+                CK(cudaEventRecord(s->ev_copied, cs));
+                s->fpend_host = true;
+            }
+            s->fpend.push_back({dx, dy, c});
+        }
+        s->fpend_total += c;
+        src += c;
+        if (ysrc) ysrc += c;
+        left -= c;
+    }
+    return CYC_OK;
+}
+
+// Fold a Full-mode stream's pending pushes before anything reads or replaces its state.
+int settle(cyc_stream* s)
+{
+    if (!s->full || s->fpend.empty()) return CYC_OK;
+    DeviceGuard g(s->device);
+    if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
+    return full_flush(s);
 }
 
 // After a stream synchronisation: did a kernel's bounded wait give up?
@@ -610,6 +753,7 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
         CK(cudaEventCreateWithFlags(&s->ev_copied, cudaEventDisableTiming));
         for (auto& e : s->ev_read) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    if (s->full) return full_push(s, src, ysrc, nsamples, on_device != 0);
     int64_t left = nsamples;
     // a windowed pass holds at most kWinSplits hop-aligned partials
     const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(kWinSplits - 1) * s->hop) : s->max_chunk;
@@ -628,17 +772,15 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
             CK(cudaEventRecord(s->ev_copied, cs));
             CK(cudaStreamWaitEvent(s->st, s->ev_copied, 0));
         }
-        int64_t nview = s->held + c;
+        const int64_t nview = s->held + c;
         int64_t nc = nview - s->M;
+        if (nc < 0) nc = 0;
+        const int64_t T2 = s->T + c;
+        const int64_t keep = T2 < s->M ? T2 : s->M;
         if (nc > 0) {
             int rc = project(s, nc);
             if (rc) return rc;
-        } else {
-            nc = 0;
         }
-        s->n_eff += nc;
-        s->T += c;
-        int64_t keep = s->T < s->M ? s->T : s->M;
         // the last `keep` samples of the view become the next view's head
         if (keep > 0) {
             CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
@@ -647,6 +789,8 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
                 CK(cudaMemcpyAsync(s->stage_y[s->cur ^ 1], s->stage_y[s->cur] + nview - keep,
                                    (size_t)keep * sizeof(float2), cudaMemcpyDeviceToDevice, s->st));
         }
+        s->n_eff += nc;
+        s->T = T2;
         if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
         s->cur ^= 1;
         s->held = keep;
@@ -674,6 +818,7 @@ int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk, int64_t
 int cyc_sync(cyc_stream* s)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_sync: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     DeviceGuard g(s->device);
     return sync_and_check(s);
 }
@@ -681,6 +826,7 @@ int cyc_sync(cyc_stream* s)
 int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_read: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (n_eff) *n_eff = s->n_eff;
     if (s->n_eff == 0) return fail(CYC_ENODATA, "cyc_read: N_eff is 0 (fewer than max(lags) + 1 samples)");
     if (!out) return fail(CYC_EINVAL, "cyc_read: out is NULL");
@@ -703,6 +849,7 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
 int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_read_spectrum: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (Q < 1 || Q > (1 << 16)) return fail(CYC_EINVAL, "cyc_read_spectrum: Q must be in [1, 65536]");
     if (taper != 0 && taper != 1) return fail(CYC_EINVAL, "cyc_read_spectrum: taper must be 0 or 1");
     if (s->n_eff == 0) return fail(CYC_ENODATA, "cyc_read_spectrum: N_eff is 0");
@@ -744,6 +891,7 @@ int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
 int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* ratio, int32_t* ndetected)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_detect: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (ndetected) *ndetected = 0;
     if (!flags) return fail(CYC_EINVAL, "cyc_detect: flags is NULL");
     if (!(kappa > 0.0) || !isfinite(kappa)) return fail(CYC_EINVAL, "cyc_detect: kappa must be positive and finite");
@@ -789,6 +937,7 @@ int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags, float* 
 int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_read_windows: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (!s->win) return fail(CYC_EINVAL, "cyc_read_windows: not a windowed stream (cyc_create_window)");
     if (nwin) *nwin = 0;
     if (first_k) *first_k = s->win_read;
@@ -825,6 +974,7 @@ int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin,
 int cyc_reset(cyc_stream* s)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_reset: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     DeviceGuard g(s->device);
     CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
     if (s->win) {
@@ -851,6 +1001,7 @@ int cyc_destroy(cyc_stream* s)
 int cyc_save(cyc_stream* s, void* buf, size_t* len)
 {
     if (!s || !len) return fail(CYC_EINVAL, "cyc_save: NULL argument");
+    if (int rc0 = settle(s)) return rc0;
     if (s->win) return fail(CYC_ENOTSUP, "cyc_save: windowed streams keep no blob");
     size_t sums_b = (size_t)s->Au * s->ncols * sizeof(double2);
     const size_t held_b = (size_t)s->held * sizeof(float2) * (s->cross ? 2 : 1);
@@ -883,6 +1034,7 @@ int cyc_save(cyc_stream* s, void* buf, size_t* len)
 int cyc_load(cyc_stream* s, const void* buf, size_t len)
 {
     if (!s || !buf) return fail(CYC_EINVAL, "cyc_load: NULL argument");
+    if (int rc0 = settle(s)) return rc0;
     if (s->win) return fail(CYC_ENOTSUP, "cyc_load: windowed streams keep no blob");
     BlobHeader h;
     if (len < sizeof h) return fail(CYC_EINVAL, "cyc_load: blob too short");
@@ -918,6 +1070,7 @@ int cyc_load(cyc_stream* s, const void* buf, size_t len)
 int cyc_info(cyc_stream* s, int* forms, int* nunique, int64_t* total, int64_t* n_eff)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_info: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (forms) *forms = s->F;
     if (nunique) *nunique = s->Au;
     if (total) *total = s->T;
@@ -936,6 +1089,7 @@ int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff)
 {
     if (!s || !sums) return fail(CYC_EINVAL, "cyc_sums: NULL argument");
     if (s->win) return fail(CYC_ENOTSUP, "cyc_sums: windowed streams keep their windows apart from the sums");
+    if (s->full) return fail(CYC_ENOTSUP, "cyc_sums: Full-mode streams keep float-float folds, not FP64 sums");
     DeviceGuard g(s->device);
     CK(cudaStreamSynchronize(s->st));
     *sums = (double*)s->sums;
@@ -947,6 +1101,7 @@ int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff)
 int cyc_set_n_eff(cyc_stream* s, int64_t n_eff)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_set_n_eff: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     if (n_eff < 0) return fail(CYC_EINVAL, "cyc_set_n_eff: n_eff < 0");
     if (s->win) return fail(CYC_ENOTSUP, "cyc_set_n_eff: not for windowed streams");
     s->n_eff = n_eff;
@@ -971,6 +1126,7 @@ int cyc_profile(cyc_stream* s, int enable)
 int cyc_profile_read(cyc_stream* s, double* proj_ms, int64_t* proj_launches, int64_t* kernels)
 {
     if (!s) return fail(CYC_EINVAL, "cyc_profile_read: handle is NULL");
+    if (int rc0 = settle(s)) return rc0;
     DeviceGuard g(s->device);
     CK(cudaStreamSynchronize(s->st));
     for (auto& e : s->ev_pending) {

@@ -209,10 +209,41 @@ int         tc_pair_units();    // units per work item (128)
 int         tc_tile_rows();     // rows of an item's partial tile (2 outputs per unit: 256)
 int         tc_tile_cols();     // columns per work item (128)
 // The uniform grid a_k = -1/2 + k/A (full_mode.cu): fold a pass's lag products modulo A into
-// F ([A][ncols], FP64, accumulated), and at read time the A-point DFT of every column into
-// out[f][k][l] / N.  A a power of two in [2, 4096].
+// the fold ([ncols][A] float-float, accumulated), and at read time the A-point DFT of every
+// column into out[f][k][l] / N.  A a power of two in [2, 4096].
+//
+// One pass of a Full-mode stream.  Its view is the carried tail followed by one or more
+// chunks, each in a buffer of its own (a chunk may be the caller's device memory, 8-byte
+// aligned): source s covers view samples [start[s], start[s + 1]).  Fold sample v is view
+// sample off + v.  Term i < nc adds x[v + m] c_f(y[v + D]) (v = i, m the shifted lag) to
+// residue (i + base_mod) mod A.  The same launch copies the view's last `keep` samples to nx
+// (and ny for two inputs) for the next pass.  The view stays below 2^30 samples.
+constexpr int kFoldSrc = 17;         // the tail and up to 16 chunks
+struct FoldArgs {
+    int nsrc = 0;
+    int32_t start[kFoldSrc + 1] = {};
+    const float2* sx[kFoldSrc] = {};
+    const float2* sy[kFoldSrc] = {}; // == sx for one input
+    int64_t off = 0;
+    int64_t nc = 0;
+    int D = 0;                       // M^-
+    int A = 0;
+    uint32_t base_mod = 0;
+    const int32_t* sl = nullptr;     // [L] shifted lags m + M^-, ascending
+    const int32_t* perm = nullptr;   // [L] the lag index of each sorted position
+    int L = 0, F = 0;
+    int fV = -1, fJ = -1;            // form index of x conj(y) and of x y (-1: not kept)
+    int xl = 0;                      // full_row_samples(sl, L)
+    bool consecutive = false;        // full_lags_consecutive(sl, L)
+    float4* fold = nullptr;          // [L F][A]
+    float2* nx = nullptr;
+    float2* ny = nullptr;            // null for one input
+    int64_t keep = 0;
+};
 bool        full_supported(int A);
-cudaError_t full_fold(const ProjArgs& a, int A, double2* F, cudaStream_t st);
+int         full_row_samples(const int32_t* sorted_shifted_lags, int L);   // x samples per staged row
+bool        full_lags_consecutive(const int32_t* sorted_shifted_lags, int L);  // each 16-lag tile m, m + 1, ...
+cudaError_t full_fold(const FoldArgs& f, cudaStream_t st);
 cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double inv_n, double2* out, cudaStream_t st);
 
 // Cyclic spectrum (spectrum.cu): S[rows][Q] = R[rows][L] x E[L][Q] in FP64, E[l][q] =

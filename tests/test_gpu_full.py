@@ -130,3 +130,47 @@ def test_full_grid_device_host_and_offset_chunks_agree(cyc):
     Ro, no = oracle.estimate_xy(x, y, lags, grid(A))
     assert n0 == no
     assert np.max(np.abs(R0 - Ro)) / oracle.r00_xy(x, y, 5, 11) < 1e-5
+
+
+def test_full_grid_many_pushes_fold_in_batches(cyc):
+    """Device pushes are folded several at a time (up to 16 chunks or max_chunk samples per
+    launch): 40 ragged device pushes with a read in between, a stream whose max_chunk forces
+    folds by size, and one interleaving host and device chunks -- all equal to the oracle;
+    the interleaved run folds the same batches as the first and equals it bit for bit."""
+    import torch
+    T, A = 30011, 256
+    x = synth.white(T, seed=177).astype(np.complex64)
+    lags = np.arange(0, 33)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    rng = np.random.default_rng(178)
+    cuts = np.sort(rng.choice(np.arange(1, T), 39, replace=False))
+    chunks = np.diff(np.concatenate([[0], cuts, [T]]))
+    Ro, no = oracle.estimate(x, lags, grid(A))
+    r00 = oracle.r00(x, 32)
+    res = []
+    for max_chunk in (0, 4096):
+        with cyc.Stream(lags, None, 3, full=A, max_chunk=max_chunk) as s:
+            pos = 0
+            for k, c in enumerate(chunks):
+                s.push(xt[2 * pos:2 * (pos + c)])
+                pos += c
+                if k == 20:                          # a read in the middle folds what is pending
+                    Rm, nm = s.read()
+                    Rp, npre = oracle.estimate(x[:pos], lags, grid(A))
+                    assert nm == npre and np.max(np.abs(Rm - Rp)) / r00 < 1e-5
+            R, n = s.read()
+        assert n == no and np.max(np.abs(R - Ro)) / r00 < 1e-5, max_chunk
+        res.append(R)
+    with cyc.Stream(lags, None, 3, full=A) as s:
+        pos = 0
+        for k, c in enumerate(chunks):
+            if k % 3 == 1:
+                s.push(x[pos:pos + c])               # host memory
+            else:
+                s.push(xt[2 * pos:2 * (pos + c)])
+            pos += c
+            if k == 20:
+                s.read()
+        R, n = s.read()
+    assert n == no and np.max(np.abs(R - Ro)) / r00 < 1e-5
+    assert np.array_equal(res[0], R)
