@@ -166,10 +166,35 @@ CYC_API int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop,
 CYC_API int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_stream** out);
 
 /*
+ * cyc_create_full_window: the paper's Full mode per window (Sec. 4: with win_len = A, one
+ * A-point FFT per lag over each window; each window's output holds nlags * A values per form).
+ * Window k covers the A reference samples n = k * hop + M^- .. k * hop + M^- + A - 1 (sample
+ * indices from the first pushed sample) and, for every lag m and form f, gives
+ *   W_k[f][kk][l] = (1/A) sum_{n'=0}^{A-1} x[n0 + n' + m_l] c_f(y[n0 + n']) exp(-j 2 pi a_kk n'),
+ *   a_kk = -1/2 + kk/A,  n0 = k * hop + M^-,
+ * i.e. Eq. (impl-corr) at that window with the window-local phase, on the whole grid.  A
+ * window is complete once its last x sample has been pushed; completed windows wait in a
+ * device ring of `capacity` windows (FP32, F * A * nlags * 8 bytes each) for
+ * cyc_read_windows ([nwin][F][A][nlags] complex FP64).  A push that would complete more
+ * windows than the ring has room for fails with CYC_EAGAIN before doing anything.  Pushes
+ * are folded in batches as for cyc_create_full, and the stream keeps its running estimate
+ * (cyc_read) as well.
+ *   A          power of two in [2, 4096] (the window length and the FFT size)
+ *   hop        1 .. 2^30 samples between window starts (hop = 1: a window per sample, the
+ *              block's own output rate)
+ *   capacity   1 .. 2^20 windows (the ring at most 64 GB)
+ *   precision  must be CYC_P_FP32 (FP32 lag products and FFT); else CYC_EINVAL
+ * cyc_save / cyc_load / cyc_sums return CYC_ENOTSUP.
+ */
+CYC_API int cyc_create_full_window(const cyc_params* p, int32_t A, int64_t hop, int64_t capacity, int cross,
+                                   cyc_stream** out);
+
+/*
  * cyc_read_windows: move up to max_win completed windows, oldest first, out of the ring into
  * out ([nwin][F][nalphas][nlags] complex FP64, host or device memory of the stream's device,
  * synchronous).  *nwin receives how many were written (0 when none are complete), *first_k
- * the index k of the first of them.  CYC_EINVAL on a stream not made by cyc_create_window.
+ * the index k of the first of them.  CYC_EINVAL on a stream not made by cyc_create_window or
+ * cyc_create_full_window.
  */
 CYC_API int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin, int64_t* first_k);
 

@@ -5,7 +5,7 @@ its thin binding.  There is no fallback: without the built library or a GPU, cal
 """
 from ._cyc import *  # noqa: F401,F403
 from ._cyc import (CycError, Stream, load, declared_functions, LIB_PATH, HEADER,  # noqa: F401
-                   cyc_create, cyc_create_ex, cyc_create_xy, cyc_create_window, cyc_create_full, cyc_push, cyc_push_xy, cyc_read,
+                   cyc_create, cyc_create_ex, cyc_create_xy, cyc_create_window, cyc_create_full, cyc_create_full_window, cyc_push, cyc_push_xy, cyc_read,
                    cyc_read_windows, cyc_read_spectrum, cyc_detect, cyc_set_wait_budget, cyc_sums, cyc_set_n_eff, cyc_sync, cyc_reset, cyc_destroy,
                    cyc_save, cyc_load, cyc_info, cyc_phase_increment, cyc_estimate_static, cyc_profile, cyc_profile_read, cyc_strerror,
                    cyc_last_error)

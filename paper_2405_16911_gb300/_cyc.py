@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "cyc_create_xy": ([P, P], I),
         "cyc_create_window": ([P, I64, I64, I64, I, P], I),
         "cyc_create_full": ([P, I32, I, P], I),
+        "cyc_create_full_window": ([P, I32, I64, I64, I, P], I),
         "cyc_read_windows": ([P, P, I64, P, P], I),
         "cyc_read_spectrum": ([P, I32, I32, P], I),
         "cyc_detect": ([P, ctypes.c_double, I32, P, P, P], I),
@@ -232,6 +233,20 @@ def cyc_create_full(lags, A: int, conj_flag: int = CYC_BOTH, n0: int = 0, max_ch
                    cuda_stream or None, device)
     h = ctypes.c_void_p()
     _check(lib.cyc_create_full(ctypes.byref(p), int(A), 1 if cross else 0, ctypes.byref(h)))
+    _shapes[h.value] = (_nforms(conj_flag), int(A), lags.size)
+    return h.value
+
+
+def cyc_create_full_window(lags, A: int, hop: int, capacity: int, conj_flag: int = CYC_BOTH, n0: int = 0,
+                           max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False) -> int:
+    """Full mode per window: every A samples' window (every hop) on the grid -1/2 + k/A."""
+    lib = load()
+    lags = np.ascontiguousarray(np.asarray(lags, dtype=np.int32))
+    p = cyc_params(lags.ctypes.data, lags.size, None, 0, conj_flag, CYC_P_FP32, int(n0), int(max_chunk),
+                   cuda_stream or None, device)
+    h = ctypes.c_void_p()
+    _check(lib.cyc_create_full_window(ctypes.byref(p), int(A), int(hop), int(capacity), 1 if cross else 0,
+                                      ctypes.byref(h)))
     _shapes[h.value] = (_nforms(conj_flag), int(A), lags.size)
     return h.value
 
@@ -629,11 +644,19 @@ class Stream:
     def __init__(self, lags, alphas, conj_flag: int = CYC_BOTH, precision=CYC_P_FP32, n0: int = 0,
                  max_chunk: int = 0, cuda_stream: int = 0, device: int = 0, cross: bool = False, window=None,
                  full: int = 0):
-        """full=A: the uniform grid -1/2 + k/A by folding (alphas must be None)."""
+        """full=A: the uniform grid -1/2 + k/A by folding (alphas must be None); with
+        window=(A, hop, capacity) as well, Full mode per window (cyc_create_full_window)."""
         if full:
             if alphas is not None:
                 raise ValueError("full mode generates its own cycle frequencies; pass alphas=None")
-            self.h = cyc_create_full(lags, full, conj_flag, n0, max_chunk, cuda_stream, device, cross)
+            if window is not None:
+                win_len, hop, capacity = window
+                if win_len != full:
+                    raise ValueError("a Full-mode window is A samples long")
+                self.h = cyc_create_full_window(lags, full, hop, capacity, conj_flag, n0, max_chunk, cuda_stream,
+                                                device, cross)
+            else:
+                self.h = cyc_create_full(lags, full, conj_flag, n0, max_chunk, cuda_stream, device, cross)
         else:
             self.h = cyc_create_ex(lags, alphas, conj_flag, precision, n0, max_chunk, cuda_stream, device, cross,
                                    window)

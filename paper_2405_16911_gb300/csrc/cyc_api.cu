@@ -148,6 +148,8 @@ struct cyc_stream {
     std::vector<Pend> fpend;
     int64_t fpend_total = 0;
     bool fpend_host = false;        // a host copy on the copy stream feeds the pending fold
+    float2* d_ftw = nullptr;        // windowed Full mode: FFT twiddles exp(-j 2 pi j / A), j < A / 2
+    int64_t carry = 0;              // samples carried from pass to pass (M; A + M - 1 for Full windows)
     // windowed output (cyc_create_window): window k covers committed n in [k hop, k hop + N)
     bool win = false;
     int64_t win_len = 0, hop = 0, win_cap = 0;
@@ -222,7 +224,7 @@ struct cyc_stream {
             if (e) { cudaEventDestroy(e); e = nullptr; }
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
                       part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S,
-                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count, d_fsl, d_fperm};
+                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count, d_fsl, d_fperm, d_ftw};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
@@ -236,6 +238,7 @@ struct cyc_stream {
         sp_Q = 0;
         dt_s = nullptr; dt_flags = nullptr; dt_ratio = nullptr; dt_dc = nullptr; dt_count = nullptr;
         d_fsl = d_fperm = nullptr;
+        d_ftw = nullptr;
     }
 };
 
@@ -268,7 +271,8 @@ int check_params(const cyc_params* p)
 
 int alloc_state(cyc_stream* s)
 {
-    size_t stage_n = (size_t)(s->M + s->max_chunk + kStagePad);
+    s->carry = s->full && s->win ? (int64_t)s->A + s->M - 1 : s->M;
+    size_t stage_n = (size_t)(s->carry + s->max_chunk + kStagePad);
     for (int b = 0; b < 2; ++b) {
         CK(dev_malloc((void**)&s->stage[b], stage_n * sizeof(float2)));
         CK(cudaMemset(s->stage[b], 0, stage_n * sizeof(float2)));
@@ -313,10 +317,19 @@ int alloc_state(cyc_stream* s)
         s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
     else
         s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
-    if (s->win && s->part_elems < (size_t)kWinSplits * s->Au * s->ncols)
+    if (s->win && !s->full && s->part_elems < (size_t)kWinSplits * s->Au * s->ncols)
         s->part_elems = (size_t)kWinSplits * s->Au * s->ncols;
     CK(dev_malloc((void**)&s->part, s->part_elems * sizeof(float2)));
-    if (s->win) {
+    if (s->win && s->full) {          // Full-mode windows: the ring of spectra and the twiddles
+        CK(dev_malloc((void**)&s->w_out, (size_t)s->win_cap * s->ncols * s->A * sizeof(float2)));
+        std::vector<float2> tw(s->A / 2);
+        for (int j = 0; j < s->A / 2; ++j) {
+            const double ang = -2.0 * M_PI * (double)j / (double)s->A;
+            tw[j] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+        CK(dev_malloc((void**)&s->d_ftw, tw.size() * sizeof(float2)));
+        CK(cudaMemcpy(s->d_ftw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    } else if (s->win) {
         const size_t nuc = (size_t)s->Au * s->ncols;
         CK(dev_malloc((void**)&s->w_ring, (size_t)s->win_w * nuc * sizeof(float2)));
         CK(dev_malloc((void**)&s->w_sum, nuc * sizeof(float4)));
@@ -417,6 +430,12 @@ int project(cyc_stream* s, int64_t nc)
     return CYC_OK;
 }
 
+// Windows complete after T samples: window k needs samples up to k hop + win_len + M - 1.
+int64_t windows_made(const cyc_stream* s, int64_t T)
+{
+    return T - s->M >= s->win_len ? (T - s->M - s->win_len) / s->hop + 1 : 0;
+}
+
 // Fold the pending pushes of a Full-mode stream in one launch: the view is the carried tail
 // stage[cur][0, held) followed by the pending chunks; the same launch writes the view's last
 // `keep` samples to stage[cur ^ 1] as the next tail.
@@ -428,7 +447,7 @@ int full_flush(cyc_stream* s)
     int64_t nc = held_f + c - s->M;
     if (nc < 0) nc = 0;
     const int64_t T2 = s->T + c;
-    const int64_t keep = T2 < s->M ? T2 : s->M;
+    const int64_t keep = T2 < s->carry ? T2 : s->carry;
     FoldArgs f;
     f.nsrc = 1 + (int)s->fpend.size();
     f.start[0] = 0;
@@ -485,6 +504,25 @@ int full_flush(cyc_stream* s)
         s->prof_launches++;
     }
     if (nc > 0 || keep > 0) s->kernel_launches += 1;
+    if (s->win) {                     // Full-mode windows completed by this pass, from the same view
+        const int64_t made2 = windows_made(s, T2);
+        if (made2 > s->win_made) {
+            FullWinArgs w;
+            w.k0 = s->win_made;
+            w.hop = s->hop;
+            w.vbase0 = w.k0 * s->hop - (s->T - s->held);        // view sample of window k0's first y
+            w.cap = s->win_cap;
+            w.N = s->A;
+            while ((1 << w.logN) < w.N) ++w.logN;
+            w.ncols = s->ncols;
+            w.col_lag = s->d_col_lag;
+            w.tw = s->d_ftw;
+            w.ring = s->w_out;
+            CK(full_windows(f, w, (int)(made2 - s->win_made), s->st));
+            s->kernel_launches += 1;
+            s->win_made = made2;
+        }
+    }
     if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
     s->n_eff += nc;
     s->T = T2;
@@ -714,6 +752,26 @@ int cyc_create_full(const cyc_params* p, int32_t A, int cross, cyc_stream** out)
     return create_impl(&q, cross != 0, 0, 0, 0, out, true);
 }
 
+int cyc_create_full_window(const cyc_params* p, int32_t A, int64_t hop, int64_t capacity, int cross,
+                           cyc_stream** out)
+{
+    if (out) *out = nullptr;
+    if (!p) return fail(CYC_EINVAL, "cyc_create_full_window: params is NULL");
+    if (!full_supported(A)) return fail(CYC_EINVAL, "cyc_create_full_window: A must be a power of two in [2, 4096]");
+    if (p->precision != CYC_P_FP32) return fail(CYC_EINVAL, "cyc_create_full_window: FP32 only");
+    if (hop < 1 || hop > ((int64_t)1 << 30)) return fail(CYC_EINVAL, "cyc_create_full_window: hop must be in [1, 2^30]");
+    if (capacity < 1 || capacity > (1 << 20))
+        return fail(CYC_EINVAL, "cyc_create_full_window: capacity must be in [1, 2^20]");
+    if ((double)capacity * A * p->nlags * ((p->conj_flag & 1) + ((p->conj_flag >> 1) & 1)) * 8.0 > 64e9)
+        return fail(CYC_EINVAL, "cyc_create_full_window: the ring would exceed 64 GB");
+    std::vector<double> grid(A);
+    for (int k = 0; k < A; ++k) grid[k] = -0.5 + (double)k / (double)A;          // exact in binary
+    cyc_params q = *p;
+    q.alphas = grid.data();
+    q.nalphas = A;
+    return create_impl(&q, cross != 0, A, hop, capacity, out, true);
+}
+
 int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop, int64_t capacity, int cross,
                       cyc_stream** out)
 {
@@ -730,9 +788,7 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
     if (nsamples < 0) return fail(CYC_EINVAL, "%s: nsamples < 0", who);
     if (nsamples == 0) return CYC_OK;
     if (s->win) {                     // room for every window this push completes?
-        const int64_t T2 = s->T + nsamples;
-        const int64_t hops2 = (T2 > s->M ? T2 - s->M : 0) / s->hop;
-        const int64_t made2 = hops2 >= s->win_w ? hops2 - s->win_w + 1 : 0;
+        const int64_t made2 = windows_made(s, s->T + s->fpend_total + nsamples);
         if (made2 - s->win_read > s->win_cap)
             return fail(CYC_EAGAIN, "%s: the push would complete %lld windows with room for %lld; read windows first",
                         who, (long long)(made2 - s->win_made), (long long)(s->win_cap - (s->win_made - s->win_read)));
@@ -953,7 +1009,19 @@ int cyc_read_windows(cyc_stream* s, double* out, int64_t max_win, int64_t* nwin,
     const int64_t per = (int64_t)s->F * s->A * s->L;
     const uint64_t base = (uint64_t)s->n0 + (uint64_t)s->Mneg;
     const double inv_n = 1.0 / (double)s->win_len;
-    if (dev) {
+    if (s->full) {                    // Full-mode windows: spectra in the ring, transposed to [F][A][L]
+        if (dev) {
+            CK(full_read_windows(s->w_out, s->win_cap, s->win_read, n, s->A, s->F, s->L, (double2*)out, s->st));
+            s->kernel_launches += 1;
+        } else {
+            for (int64_t i = 0; i < n; ++i) {
+                CK(full_read_windows(s->w_out, s->win_cap, s->win_read + i, 1, s->A, s->F, s->L, s->d_out, s->st));
+                CK(cudaMemcpyAsync((double2*)out + i * per, s->d_out, (size_t)per * sizeof(double2),
+                                   cudaMemcpyDeviceToHost, s->st));
+            }
+            s->kernel_launches += n;
+        }
+    } else if (dev) {
         CK(read_windows(s->w_out, s->win_cap, s->win_read, n, s->d_amap, s->d_phi, s->F, s->A, s->L, s->Au, s->ncols,
                         base, s->hop, inv_n, (double2*)out, s->st));
         s->kernel_launches += 1;
@@ -977,11 +1045,11 @@ int cyc_reset(cyc_stream* s)
     if (int rc0 = settle(s)) return rc0;
     DeviceGuard g(s->device);
     CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
-    if (s->win) {
+    if (s->win && !s->full) {
         CK(cudaMemsetAsync(s->w_sum, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));
         CK(cudaMemsetAsync(s->w_pend, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));
-        s->hops = s->win_made = s->win_read = 0;
     }
+    if (s->win) s->hops = s->win_made = s->win_read = 0;
     s->T = s->n_eff = s->held = 0;
     return CYC_OK;
 }

@@ -240,6 +240,20 @@ struct FoldArgs {
     float2* ny = nullptr;            // null for one input
     int64_t keep = 0;
 };
+// Windowed Full mode: windows k0 .. k0 + nwin - 1, window k0 + w reading view samples
+// vbase0 + w hop + n (n < N, plus the lags); each lag's N-point FFT per form, divided by N,
+// goes to ring slot (k mod cap) as [ncols][N] FP32.
+struct FullWinArgs {
+    int64_t k0 = 0, hop = 0, vbase0 = 0, cap = 0;
+    int N = 0, logN = 0, ncols = 0;
+    const int32_t* col_lag = nullptr;    // [ncols] shifted lag of column l F + f
+    const float2* tw = nullptr;          // [N / 2] exp(-j 2 pi j / N), FP32
+    float2* ring = nullptr;              // [cap][ncols][N]
+};
+cudaError_t full_windows(const FoldArgs& a, const FullWinArgs& w, int nwin, cudaStream_t st);
+// out [n][F][N][L] FP64 from ring slots k0 .. k0 + n - 1
+cudaError_t full_read_windows(const float2* ring, int64_t cap, int64_t k0, int64_t n, int N, int F, int L,
+                              double2* out, cudaStream_t st);
 bool        full_supported(int A);
 int         full_row_samples(const int32_t* sorted_shifted_lags, int L);   // x samples per staged row
 bool        full_lags_consecutive(const int32_t* sorted_shifted_lags, int L);  // each 16-lag tile m, m + 1, ...

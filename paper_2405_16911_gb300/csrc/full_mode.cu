@@ -375,6 +375,96 @@ __global__ void __launch_bounds__(FT, 1) fold_kernel(FoldArgs a)
     }
 }
 
+// Windowed Full mode.  Block (l, w): window k = k0 + w of lag l, whose reference samples
+// are view samples base + n, n < N (base = vbase0 + w hop), for both forms: the products
+// P(n) = x[base + n + m] c_f(y[base + n + D]) (m the shifted lag) times (-1)^n go in
+// bit-reversed order into shared memory, an in-place radix-2 FFT (FP32, twiddles from a
+// table) gives sum_n P(n) exp(-j 2 pi (-1/2 + kk/N) n), and the spectrum divided by N goes to
+// ring slot (k mod cap) as [column][kk].
+__global__ void __launch_bounds__(256) window_fft_kernel(FoldArgs a, FullWinArgs w)
+{
+    extern __shared__ __align__(16) float2 fw[];             // [2][N] then the twiddles [N / 2]
+    __shared__ SrcTab tab;
+    if (threadIdx.x == 0) tab.n = a.nsrc;
+    if (threadIdx.x <= kFoldSrc) tab.start[threadIdx.x] = a.start[threadIdx.x];
+    if (threadIdx.x < kFoldSrc) {
+        tab.x[threadIdx.x] = a.sx[threadIdx.x];
+        tab.y[threadIdx.x] = a.sy[threadIdx.x];
+    }
+    const int N = w.N, l = blockIdx.x;
+    float2* V = fw;
+    float2* J = fw + N;
+    float2* tw = fw + 2 * N;
+    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) tw[j] = w.tw[j];
+    __syncthreads();
+    const int m = w.col_lag[l * a.F];                         // shifted lag of lag index l
+    const int base = (int)(w.vbase0 + (int64_t)blockIdx.y * w.hop);
+    int cx = 0, cy = 0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int vx = base + n + m, vy = base + n + a.D;
+        cx = src_from(tab, vx, cx);
+        cy = src_from(tab, vy, cy);
+        const float2 xm = tab.x[cx][vx - tab.start[cx]];
+        const float2 y = tab.y[cy][vy - tab.start[cy]];
+        const float sg = (n & 1) ? -1.f : 1.f;
+        const float ar = xm.x * y.x, bi = xm.y * y.y, cr = xm.y * y.x, di = xm.x * y.y;
+        const unsigned r = __brev((unsigned)n) >> (32 - w.logN);
+        V[r] = make_float2(sg * (ar + bi), sg * (cr - di));    // x conj(y)
+        J[r] = make_float2(sg * (ar - bi), sg * (cr + di));    // x y
+    }
+    __syncthreads();
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len >> 1, step = N / len;
+        for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+            const int j = t & (half - 1);
+            const int i0 = (t - j) * 2 + j, i1 = i0 + half;
+            const float2 z = tw[j * step];                      // exp(-j 2 pi j / len)
+            float2 b = V[i1], u = V[i0];
+            float2 q = make_float2(b.x * z.x - b.y * z.y, b.x * z.y + b.y * z.x);
+            V[i0] = make_float2(u.x + q.x, u.y + q.y);
+            V[i1] = make_float2(u.x - q.x, u.y - q.y);
+            b = J[i1];
+            u = J[i0];
+            q = make_float2(b.x * z.x - b.y * z.y, b.x * z.y + b.y * z.x);
+            J[i0] = make_float2(u.x + q.x, u.y + q.y);
+            J[i1] = make_float2(u.x - q.x, u.y - q.y);
+        }
+        __syncthreads();
+    }
+    const int64_t slot = (w.k0 + blockIdx.y) % w.cap;
+    const float inv = 1.f / (float)N;                          // a power of two: exact
+    float2* rV = a.fV >= 0 ? w.ring + ((size_t)slot * w.ncols + l * a.F + a.fV) * N : nullptr;
+    float2* rJ = a.fJ >= 0 ? w.ring + ((size_t)slot * w.ncols + l * a.F + a.fJ) * N : nullptr;
+    for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
+        if (rV) rV[kk] = make_float2(V[kk].x * inv, V[kk].y * inv);
+        if (rJ) rJ[kk] = make_float2(J[kk].x * inv, J[kk].y * inv);
+    }
+}
+
+// out[i][f][kk][l] (FP64) = ring slot ((k0 + i) mod cap) [l F + f][kk]: 32 x 32 tiles of (kk,
+// l) transposed through shared memory.  Grid (ceil(N / 32) x ceil(L / 32), F, n).
+__global__ void window_read_kernel(const float2* __restrict__ ring, int64_t cap, int64_t k0, int N, int F, int L,
+                                   double2* __restrict__ out)
+{
+    __shared__ float2 t[32][33];
+    const int ntl = (L + 31) / 32;
+    const int kt = blockIdx.x / ntl, lt = blockIdx.x % ntl, f = blockIdx.y, i = blockIdx.z;
+    const int64_t slot = (k0 + i) % cap;
+    const int ncols = F * L;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {       // r: lag within the tile
+        const int l = lt * 32 + r, kk = kt * 32 + threadIdx.x;
+        t[r][threadIdx.x] = l < L && kk < N ? ring[((size_t)slot * ncols + l * F + f) * N + kk] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {       // r: kk within the tile
+        const int kk = kt * 32 + r, l = lt * 32 + threadIdx.x;
+        if (l < L && kk < N) {
+            const float2 v = t[threadIdx.x][r];
+            out[(((size_t)i * F + f) * N + kk) * L + l] = make_double2(v.x, v.y);
+        }
+    }
+}
+
 // Block c: out[f][k][l] = (1/N) sum_r (-1)^r F_c[r] exp(-j 2 pi k r / A) for column
 // c = l F + f, by an in-place radix-2 FFT in shared memory (FP64).
 __global__ void dft_read_kernel(const float4* __restrict__ F, int A, int logA, int ncols, int nF, int L,
@@ -468,6 +558,33 @@ cudaError_t full_fold(const FoldArgs& f, cudaStream_t st)
     return mode == 0 ? launch_fold<0>(f, grid, smem, st)
          : mode == 1 ? launch_fold<1>(f, grid, smem, st)
                      : launch_fold<2>(f, grid, smem, st);
+}
+
+cudaError_t full_windows(const FoldArgs& a, const FullWinArgs& w, int nwin, cudaStream_t st)
+{
+    if (nwin <= 0) return cudaSuccess;
+    if (a.nsrc < 1 || a.nsrc > kFoldSrc || w.N < 2 || w.N > 4096) return cudaErrorInvalidValue;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(window_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(4096 * 5 / 2 * sizeof(float2)));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const size_t smem = (size_t)w.N * 5 / 2 * sizeof(float2);
+    window_fft_kernel<<<dim3(a.L, nwin), 256, smem, st>>>(a, w);
+    return cudaGetLastError();
+}
+
+cudaError_t full_read_windows(const float2* ring, int64_t cap, int64_t k0, int64_t n, int N, int F, int L,
+                              double2* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(((N + 31) / 32) * ((L + 31) / 32), F, (unsigned)n);
+    window_read_kernel<<<grid, dim3(32, 8), 0, st>>>(ring, cap, k0, N, F, L, out);
+    return cudaGetLastError();
 }
 
 cudaError_t full_read(const double2* F, int A, int ncols, int nF, int L, double inv_n, double2* out, cudaStream_t st)

@@ -174,3 +174,82 @@ def test_full_grid_many_pushes_fold_in_batches(cyc):
         R, n = s.read()
     assert n == no and np.max(np.abs(R - Ro)) / r00 < 1e-5
     assert np.array_equal(res[0], R)
+
+
+@pytest.mark.parametrize("A,hop,cross", [(64, 64, False), (256, 100, True), (32, 1, False), (1024, 512, False)])
+def test_full_windows_against_the_oracle(cyc, A, hop, cross):
+    """Full mode per window (cyc_create_full_window): window k's A-point spectrum per lag and
+    form, window-local phase, element by element against the oracle's windowed estimate on
+    the grid -1/2 + kk/A (FP32 tolerance 1e-5 of R^0(0)); the ring read in pieces between
+    ragged pushes of device and host chunks; the start index does not move a window's phase;
+    the running estimate is kept beside the windows."""
+    import torch
+    T = {64: 5000, 256: 6001, 32: 700, 1024: 6000}[A]
+    x = synth.white(T, seed=180).astype(np.complex64)
+    y = synth.white(T, seed=181).astype(np.complex64) if cross else None
+    lags = np.arange(-4, 7) if cross else np.arange(0, 9)
+    Ro = oracle.windows(x, y, lags, grid(A), A, hop)
+    r00 = oracle.r00_xy(x, y, int(max(0, -lags.min())), int(lags.max()))
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    yt = torch.from_numpy(y.view(np.float32).copy()).cuda() if cross else None
+    rng = np.random.default_rng(182)
+    cuts = np.sort(rng.choice(np.arange(1, T), 11, replace=False))
+    chunks = np.diff(np.concatenate([[0], cuts, [T]]))
+    for n0 in (0, (1 << 33) + 5):
+        got = []
+        cap = Ro.shape[0] + 1
+        with cyc.Stream(lags, None, 3, n0=n0, cross=cross, full=A, window=(A, hop, cap)) as s:
+            pos = 0
+            for k, c in enumerate(chunks):
+                sl = slice(2 * pos, 2 * (pos + c))
+                if k % 4 == 3:
+                    s.push(x[pos:pos + c], y=y[pos:pos + c] if cross else None)     # host chunk
+                else:
+                    s.push(xt[sl], y=yt[sl] if cross else None)
+                pos += c
+                if k % 3 == 0:
+                    W, k0 = s.read_windows(cap)
+                    assert k0 == sum(len(g) for g in got)
+                    got.append(W.copy())
+            W, k0 = s.read_windows(cap)
+            got.append(W.copy())
+            R, n = s.read()
+        W = np.concatenate(got)
+        assert W.shape == Ro.shape, (W.shape, Ro.shape)
+        err = float(np.max(np.abs(W - Ro)) / r00)
+        assert err < 1e-5, (n0, err)
+        Rs, ns = (oracle.estimate_xy(x, y, lags, grid(A), n0=n0) if cross else
+                  oracle.estimate(x, lags, grid(A), n0=n0))
+        assert n == ns and np.max(np.abs(R - Rs)) / r00 < 1e-5
+
+
+def test_full_windows_ring_limit_and_arguments(cyc):
+    """A push that would complete more windows than the ring holds fails with CYC_EAGAIN and
+    changes nothing; reading frees the room; bad arguments fail with CYC_EINVAL."""
+    import torch
+    A, hop, cap = 64, 32, 4
+    T = 64 + 32 * 10 + 8
+    x = synth.white(T, seed=183).astype(np.complex64)
+    lags = np.array([0, 1, 8])
+    Ro = oracle.windows(x, None, lags, grid(A), A, hop)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    with cyc.Stream(lags, None, 3, full=A, window=(A, hop, cap)) as s:
+        s.push(xt[:2 * 180])                                  # windows 0 .. 3 complete: 180 - 8 >= 64 + 32 k
+        with pytest.raises(cyc.CycError) as e:
+            s.push(xt[2 * 180:])                              # would complete 7 more, 11 unread
+        assert e.value.code == cyc.CYC_EAGAIN
+        W1, _ = s.read_windows(cap)
+        s.push(xt[2 * 180:2 * 240])                           # windows 4, 5
+        W2, _ = s.read_windows(cap)
+        s.push(xt[2 * 240:2 * 300])                           # windows 6, 7
+        W3, _ = s.read_windows(cap)
+        s.push(xt[2 * 300:])                                  # windows 8 .. 10
+        W4, _ = s.read_windows(cap)
+    assert [len(w) for w in (W1, W2, W3, W4)] == [4, 2, 2, 3]
+    W = np.concatenate([W1, W2, W3, W4])
+    assert W.shape == Ro.shape
+    assert np.max(np.abs(W - Ro)) / oracle.r00(x, 8) < 1e-5
+    for bad in ((100, 10, 4), (64, 0, 4), (64, 10, 0), (8192, 10, 4)):
+        with pytest.raises(cyc.CycError) as e:
+            cyc.Stream(lags, None, 3, full=bad[0], window=bad)
+        assert e.value.code == cyc.CYC_EINVAL

@@ -68,3 +68,25 @@ def test_one_window_is_the_stream_estimate_with_its_phase_origin_moved():
     assert neff == N
     rot = np.exp(2j * np.pi * np.asarray(alphas) * 3)[None, :, None]   # phase origin M^- = 3
     assert np.max(np.abs(R[0] - Rs * rot)) < 1e-12
+
+
+@pytest.mark.parametrize("N,hop", [(16, 16), (32, 7), (8, 1)])
+def test_full_grid_window_is_the_fft_of_the_lag_products(N, hop):
+    """Full mode per window (Sec. 4: one FFT per lag over each window): on the grid
+    a_kk = -1/2 + kk/N the windowed estimate is (1/N) FFT_N of p(n) (-1)^n, p the window's lag
+    products -- numpy's FFT, independent of the oracle's direct sum."""
+    T = 200
+    x, y = synth.white(T, seed=23), synth.white(T, seed=24)
+    lags = np.array([-3, 0, 2, 5])
+    grid = -0.5 + np.arange(N) / N
+    R = oracle.windows(x, y, lags, grid, N, hop)
+    Mneg, sgn = 3, (-1.0) ** np.arange(N)
+    assert R.shape[0] == (T - (3 + 5 + N)) // hop + 1
+    for k in range(0, R.shape[0], 3):
+        s = k * hop + Mneg
+        for fi, conj in ((0, True), (1, False)):
+            for im, m in enumerate(lags):
+                yy = y[s:s + N]
+                p = x[s + m:s + m + N] * (np.conj(yy) if conj else yy)
+                ref = np.fft.fft(p * sgn) / N
+                assert np.max(np.abs(R[k, fi, :, im] - ref)) < 1e-12
