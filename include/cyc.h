@@ -134,7 +134,9 @@ CYC_API int cyc_create_xy(const cyc_params* p, cyc_stream** out);
  * 1e-7 of each entry beyond the projection's own error); the update that adds a hop and
  * drops the oldest cancels exactly, so long streams carry no drift.
  *   win_len   positive multiple of hop, win_len / hop <= 65536
- *   hop       >= 16 samples between window starts
+ *   hop       >= 1 samples between window starts (hop = 1: a window per sample, the block's
+ *             own output rate); below 16 only with CYC_P_FP32, whose passes then hold as
+ *             many hops as 64 MB of FP32 partials allow
  *   capacity  1 .. 2^20 windows of F * (distinct a) * nlags * 8 bytes each (held in FP32
  *             until read; plus device state of (win_len / hop) * (distinct a) * F * nlags
  *             * 8 bytes for the hop sums and 2 * (distinct a) * F * nlags * 16 bytes)

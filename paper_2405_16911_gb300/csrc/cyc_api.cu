@@ -59,7 +59,8 @@ constexpr int64_t kDefaultChunk = 1 << 20;
 constexpr int64_t kMaxChunk = 1ll << 28;
 constexpr int32_t kMaxLag = 1 << 20;
 constexpr int kStagePad = 256;      // zeroed samples after every staging buffer
-constexpr int kWinSplits = 64;      // hop-aligned partials per pass of a windowed stream
+constexpr int kWinSplits = 64;      // hop-aligned partials per pass of a windowed tensor-core stream
+constexpr size_t kWinPartBytes = 64u << 20;   // FP32 windowed streams: partials of a pass, at most
 constexpr uint32_t kBlobVersion = 3;       // 3: tensor-core streams keep their sums in unit order
 
 // a (cycles/sample) -> round(a * 2^64) mod 2^64, exactly.  a = m * 2^e with m the 53-bit
@@ -154,6 +155,7 @@ struct cyc_stream {
     bool win = false;
     int64_t win_len = 0, hop = 0, win_cap = 0;
     int win_w = 0;                  // hops per window
+    int win_splits = 0;             // hop-aligned partials per pass (one pass covers win_splits - 1 hops)
     int64_t hops = 0;               // hops completed
     int64_t win_made = 0, win_read = 0;
     float2* w_ring = nullptr;       // [win_w][Au][ncols] the last win_w completed hops (FP32)
@@ -317,8 +319,18 @@ int alloc_state(cyc_stream* s)
         s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
     else
         s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
-    if (s->win && !s->full && s->part_elems < (size_t)kWinSplits * s->Au * s->ncols)
-        s->part_elems = (size_t)kWinSplits * s->Au * s->ncols;
+    if (s->win && !s->full) {
+        // FP32 streams: as many hop partials per pass as 64 MB holds (short hops then cost few
+        // launches); tensor-core streams: kWinSplits
+        const size_t nuc = (size_t)s->Au * s->ncols;
+        size_t ws = kWinSplits;
+        if (s->precision == CYC_P_FP32) {
+            ws = kWinPartBytes / (nuc * sizeof(float2));
+            ws = ws < (size_t)kWinSplits ? (size_t)kWinSplits : ws > 65535 ? 65535 : ws;
+        }
+        s->win_splits = (int)ws;
+        if (s->part_elems < ws * nuc) s->part_elems = ws * nuc;
+    }
     CK(dev_malloc((void**)&s->part, s->part_elems * sizeof(float2)));
     if (s->win && s->full) {          // Full-mode windows: the ring of spectra and the twiddles
         CK(dev_malloc((void**)&s->w_out, (size_t)s->win_cap * s->ncols * s->A * sizeof(float2)));
@@ -776,8 +788,10 @@ int cyc_create_window(const cyc_params* p, int64_t win_len, int64_t hop, int64_t
                       cyc_stream** out)
 {
     if (out) *out = nullptr;
-    if (hop < 16 || win_len < hop || win_len % hop != 0 || win_len / hop > (1 << 16))
-        return fail(CYC_EINVAL, "cyc_create_window: need hop >= 16, win_len a multiple of hop, win_len / hop <= 65536");
+    if (hop < 1 || win_len < hop || win_len % hop != 0 || win_len / hop > (1 << 16))
+        return fail(CYC_EINVAL, "cyc_create_window: need hop >= 1, win_len a multiple of hop, win_len / hop <= 65536");
+    if (hop < 16 && p && p->precision != CYC_P_FP32)
+        return fail(CYC_EINVAL, "cyc_create_window: hops below 16 samples need CYC_P_FP32");
     if (capacity < 1 || capacity > (1 << 20)) return fail(CYC_EINVAL, "cyc_create_window: capacity must be in [1, 2^20]");
     return create_impl(p, cross != 0, win_len, hop, capacity, out);
 }
@@ -811,8 +825,8 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
     }
     if (s->full) return full_push(s, src, ysrc, nsamples, on_device != 0);
     int64_t left = nsamples;
-    // a windowed pass holds at most kWinSplits hop-aligned partials
-    const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(kWinSplits - 1) * s->hop) : s->max_chunk;
+    // a windowed pass holds at most win_splits hop-aligned partials
+    const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(s->win_splits - 1) * s->hop) : s->max_chunk;
     while (left > 0) {
         int64_t c = left < pass ? left : pass;
         float2* view = s->stage[s->cur];

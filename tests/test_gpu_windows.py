@@ -158,3 +158,22 @@ def test_windows_long_stream_no_drift(cyc):
         Wo = oracle.windows(x[k * hop:k * hop + N + M], None, lags, alphas, N, hop)[0]
         assert np.max(np.abs(last[i] - Wo)) / nrm < 1e-5, (k, np.max(np.abs(last[i] - Wo)) / nrm)
     assert k_last + last.shape[0] - 1 == (T - M - N) // hop
+
+
+@pytest.mark.parametrize("hop,nalpha,N", [(1, 6, 64), (5, 40, 125), (3, 12, 96)])
+def test_windows_at_short_hops(cyc, hop, nalpha, N):
+    """Hops below 16 samples, down to hop = 1 (an estimate per input sample, the block's own
+    output rate), on the FP32 path (few cycle frequencies: register sums; more: the tiled
+    kernel): every window against the oracle; tensor-core precisions refuse such hops."""
+    T = 3000
+    x = synth.white(T, seed=190).astype(np.complex64)
+    lags = np.array([-2, 0, 1, 4, 7])
+    alphas = np.random.default_rng(191).uniform(-0.5, 0.5, nalpha)
+    W, R, neff = run_windows(cyc, x, None, lags, alphas, N, hop, "fp32", ragged(T, 192), cap=T)
+    Wo = oracle.windows(x, None, lags, alphas, N, hop)
+    check(W, Wo, x, None, lags, TOL["fp32"])
+    Ro, no = oracle.estimate_xy(x, None, lags, alphas)
+    assert neff == no and np.max(np.abs(R - Ro)) / oracle.r00_xy(x, None, 2, 7) < TOL["fp32"]
+    with pytest.raises(cyc.CycError) as e:
+        cyc.Stream(lags, alphas, 3, precision="bf16x3", window=(N, hop, 4))
+    assert e.value.code == cyc.CYC_EINVAL
