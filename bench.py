@@ -337,13 +337,42 @@ def latency_leg(pkg, calls=1000, warm=20):
             call()
             ts.append(time.perf_counter() - t0)
         au = [sc.info()[1], sj.info()[1]]
+        # where a call's time goes: host time to queue reset + push of both forms, the GPU
+        # time of that queued work on each form's CUDA stream (events), the time the two reads
+        # take after it (waiting for the GPU, the read kernel, the D2H copy, the status check),
+        # and a read of an idle stream alone
+        nb = max(calls // 4, 10)
+        issue, gpu, rd, rd_idle = [], [], [], []
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+        for _ in range(nb):
+            t0 = time.perf_counter()
+            for k, s in enumerate((sc, sj)):
+                ev[k][0].record(cs[k])
+                s.reset()
+                s.push(x_dev)
+                ev[k][1].record(cs[k])
+            t1 = time.perf_counter()
+            sc.read(outs[0])
+            sj.read(outs[1])
+            t2 = time.perf_counter()
+            sc.read(outs[0])
+            t3 = time.perf_counter()
+            issue.append(t1 - t0)
+            rd.append(t2 - t1)
+            rd_idle.append(t3 - t2)
+            gpu.append(max(ev[0][0].elapsed_time(ev[0][1]), ev[1][0].elapsed_time(ev[1][1])) * 1e-3)
     ts = np.array(ts) * 1e6
+    med = lambda v: float(np.median(np.array(v) * 1e6))
     cmac = (T - 31) * 32 * sum(au)
     return {"workload": "cfg0 GMSK 65536 samples, lags 0..31, 64 a per form (k/8: %d distinct doubles mod 1; "
                         "0.1 + k/8: %d), CONV+CONJ, fp32" % (au[0], au[1]),
             "calls": calls, "p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99)),
             "mean_us": float(ts.mean()), "gmac_s_at_p50": cmac / (np.percentile(ts, 50) * 1e-6) / 1e9,
-            "call": "reset + push (device chunk) on each form's stream, then read (host) of each"}
+            "call": "reset + push (device chunk) on each form's stream, then read (host) of each",
+            "breakdown_median_us": {"host_issue_reset_push_both": med(issue),
+                                    "gpu_reset_push_per_form_max": med(gpu),
+                                    "reads_both_after_issue": med(rd), "read_idle_stream_one": med(rd_idle),
+                                    "calls": nb}}
 
 
 def precision_leg(pkg, reps=3):
@@ -852,6 +881,8 @@ def main():
     ap.add_argument("--no-windows", action="store_true", help="skip the windowed-output leg")
     ap.add_argument("--no-full", action="store_true", help="skip the Full-mode leg")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
+    ap.add_argument("--latency-only", action="store_true", help="run the config-0 latency leg alone and print it")
+    ap.add_argument("--latency-calls", type=int, default=1000)
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1 ranks: cut one config-1 stream into N time shards and merge them with one "
                          "all-reduce of the running sums (strong scaling) instead of N independent replicas")
@@ -869,6 +900,14 @@ def main():
         torch.cuda.set_device(0)
         pkg.load()
         print(json.dumps(serving_leg(pkg, seconds=args.serving_seconds)))
+        return 0
+    if args.latency_only:
+        import torch
+        import paper_2405_16911_gb300 as pkg
+        torch.cuda.set_device(0)
+        pkg.load()
+        with nvtx_range("latency"):
+            print(json.dumps(latency_leg(pkg, calls=args.latency_calls)))
         return 0
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
