@@ -254,7 +254,9 @@ CYC_API int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk,
 /*
  * cyc_read: wait for the stream's work, then write R = sums / N_eff (layout above) to
  * `out`, which may be host or device memory of at least F * nalphas * nlags * 16 bytes
- * (device memory 16-byte aligned: CYC_EINVAL otherwise).
+ * (device memory 16-byte aligned: CYC_EINVAL otherwise).  A host `out` is filled from a
+ * page-locked buffer of F * nalphas * nlags * 16 bytes (up to 64 MB) that the handle keeps
+ * after its first host read.
  * *n_eff (optional) receives N_eff.  CYC_ENODATA when N_eff == 0 (out untouched).
  */
 CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);

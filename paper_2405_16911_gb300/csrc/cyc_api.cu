@@ -198,6 +198,7 @@ struct cyc_stream {
     double2* d_out = nullptr;
     int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
     int* h_err = nullptr;       // page-locked copy, read after a stream synchronisation
+    void* h_stage = nullptr;    // page-locked landing buffer of cyc_read into host memory (first use)
     // host pushes: chunks are copied on a stream of their own, so that the copy of one pass
     // overlaps the projection of the previous one (created at the first host push)
     cudaStream_t xst = nullptr;
@@ -230,6 +231,8 @@ struct cyc_stream {
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
+        if (h_stage) cudaFreeHost(h_stage);
+        h_stage = nullptr;
         stage[0] = stage[1] = stage_y[0] = stage_y[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
@@ -911,9 +914,19 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     else
         CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st));
     s->kernel_launches++;
-    if (!dev)
-        CK(cudaMemcpyAsync(out, s->d_out, (size_t)s->F * s->A * s->L * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
-    return sync_and_check(s);
+    if (dev) return sync_and_check(s);
+    // host memory: the result lands in a page-locked buffer of the handle's (one copy queued
+    // beside the status word, one synchronisation) and is copied from there; without that
+    // buffer (up to 64 MB, made at the first host read) the copy goes straight to `out`
+    const size_t bytes = (size_t)s->F * s->A * s->L * sizeof(double2);
+    if (!s->h_stage && bytes <= ((size_t)64 << 20) && cudaMallocHost(&s->h_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->h_stage = nullptr;
+    }
+    CK(cudaMemcpyAsync(s->h_stage ? s->h_stage : (void*)out, s->d_out, bytes, cudaMemcpyDeviceToHost, s->st));
+    const int rc = sync_and_check(s);
+    if (rc == CYC_OK && s->h_stage) memcpy(out, s->h_stage, bytes);
+    return rc;
 }
 
 int cyc_read_spectrum(cyc_stream* s, int32_t Q, int32_t taper, double* out)
