@@ -35,6 +35,7 @@ METRIC = "cyclic-corr GMAC/s and Msamples/s, tuned vs plain FP32 at <=1e-4 err; 
 UNIT = "GMAC/s"
 T_SAMPLES = 1 << 26
 CHUNK = 1 << 16
+PASS = 1 << 20                         # the stream's max_chunk: 16 pushes projected per launch
 NLAGS, NALPHAS, NFORMS = 128, 1024, 2
 FLOPS_PER_CMAC = 8                     # one complex multiply-add (the algorithmic unit)
 TC_PASSES = {"bf16x3": 3, "fp16": 1}   # tensor-core products per real product
@@ -45,9 +46,9 @@ TC_EXEC_FLOPS_PER_CMAC_PASS = 4
 TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per projection launch from one ncu capture,
-# valid only for the kernel source it was taken on (sha256 prefix of the .cu file).
+# valid only for the kernel source it was taken on (sha256 prefix of the .cu file) and the
+# samples one launch projects.
 TRAFFIC = {
-    "proj_tc@1c7ae1991702": 610304 + 132096,   # profiles/proj_tc_bf16x3_cfg1_ncu.md
 }
 
 
@@ -55,7 +56,7 @@ def workload_config(precision):
     return {
         "workload": "cfg1 GMSK stream: %d complex64 samples pushed in 2^16-sample chunks, "
                     "lags 0..127, 1024 cycle freqs -0.5+k/1024, CONV+CONJ, FP64 running sums" % ARGS_SAMPLES[0],
-        "samples_per_step": ARGS_SAMPLES[0], "chunk": CHUNK, "lags": NLAGS, "cycle_freqs": NALPHAS,
+        "samples_per_step": ARGS_SAMPLES[0], "chunk": CHUNK, "pass": PASS, "lags": NLAGS, "cycle_freqs": NALPHAS,
         "forms": NFORMS, "projection": precision,
         "l2": "inputs larger than L2 (%d MB stream per step, 129 MB L2)" % (ARGS_SAMPLES[0] * 8 >> 20)
               if ARGS_SAMPLES[0] * 8 > (129 << 20) else
@@ -70,10 +71,10 @@ def cmac_per_step(T=None):
 ARGS_SAMPLES = [T_SAMPLES]
 
 
-def kernel_hash(precision):
+def kernel_hash(precision, samples_per_launch=PASS):
     f = "proj_fp32.cu" if precision == "fp32" else "proj_tc.cu"
     with open(os.path.join(ROOT, "paper_2405_16911_gb300", "csrc", f), "rb") as fh:
-        return f.split(".")[0] + "@" + hashlib.sha256(fh.read()).hexdigest()[:12]
+        return f.split(".")[0] + "@" + hashlib.sha256(fh.read()).hexdigest()[:12] + "@%d" % samples_per_launch
 
 
 def nvtx_range(name):
@@ -671,7 +672,7 @@ def time_device_steps(pkg, x_dev, lags, alphas, precision, steps, warmup, world,
     from paper_2405_16911_gb300 import shard
     out = torch.empty((NFORMS, NALPHAS, NLAGS, 2), dtype=torch.float64, device="cuda")
     nsamp = x_dev.numel() // 2
-    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK, n0=n0) as s:
+    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=PASS, n0=n0) as s:
         def step():
             s.reset()
             for c0 in range(0, nsamp, CHUNK):
@@ -703,7 +704,7 @@ def time_e2e(pkg, x_host_pinned, lags, alphas, precision, steps):
     nchunks = x_host_pinned.numel() // (2 * CHUNK)
     res = np.empty((NFORMS, NALPHAS, NLAGS), dtype=np.complex128)
     base = x_host_pinned.data_ptr()
-    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=CHUNK) as s:
+    with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision=precision, max_chunk=PASS) as s:
         def step():
             s.reset()
             for c in range(nchunks):

@@ -84,8 +84,10 @@ typedef struct cyc_stream cyc_stream;   /* opaque, owned by the library */
  *   conj_flag         CYC_CONV, CYC_CONJ or CYC_BOTH
  *   precision         CYC_P_*
  *   n0                absolute index of the first sample (phase origin, any int64)
- *   max_chunk         largest push handled in one device pass; longer pushes are cut.
- *                     0 selects 1 << 20.  Device staging memory is 2 * (M + max_chunk) * 8 B.
+ *   max_chunk         samples of one device pass: pushes are staged behind each other and
+ *                     projected together once a pass is full (and before any call that reads
+ *                     the stream), longer pushes are cut.  0 selects 1 << 20.  Device staging
+ *                     memory is 2 * (M + max_chunk) * 8 B.
  *   cuda_stream       cudaStream_t the stream's work is ordered on; NULL = the legacy
  *                     default stream of `device`
  *   device            CUDA device ordinal
@@ -237,8 +239,11 @@ CYC_API int cyc_detect(cyc_stream* s, double kappa, int32_t win, uint8_t* flags,
 /*
  * cyc_push: append nsamples samples (interleaved complex64) to the stream and add their
  * contribution to the FP64 running sums (Sec. 4 Eq. (impl-corr), accumulated over the
- * whole stream).  on_device != 0: `chunk` is device memory of the stream's device, read
- * in stream order -- keep it unchanged until the next cyc_read / cyc_sync.
+ * whole stream).  The samples are staged at once; their projection runs when max_chunk
+ * samples are staged (several short pushes share one launch) or when a call reads the
+ * stream (cyc_read, cyc_sync, ...).  on_device != 0: `chunk` is device memory of the
+ * stream's device, read in stream order -- keep it unchanged until the next cyc_read /
+ * cyc_sync.
  * on_device == 0: host memory; pageable memory is consumed before return, page-locked
  * memory is read in stream order like device memory -- on a copy stream of the handle's own,
  * so that the copy of one push overlaps the projection of the previous one (the projection

@@ -584,13 +584,51 @@ int full_push(cyc_stream* s, const float2* src, const float2* ysrc, int64_t nsam
     return CYC_OK;
 }
 
-// Fold a Full-mode stream's pending pushes before anything reads or replaces its state.
+// Project the samples pending in the view of a (Set-mode) stream: one pass over
+// stage[cur][0, held + pending), then the view's last `keep` samples become the next view's
+// head.
+int set_flush(cyc_stream* s)
+{
+    const int64_t c = s->fpend_total;
+    if (c <= 0) return CYC_OK;
+    float2* view = s->stage[s->cur];
+    if (s->fpend_host) {
+        CK(cudaStreamWaitEvent(s->st, s->ev_copied, 0));
+        s->fpend_host = false;
+    }
+    const int64_t nview = s->held + c;
+    int64_t nc = nview - s->M;
+    if (nc < 0) nc = 0;
+    const int64_t T2 = s->T + c;
+    const int64_t keep = T2 < s->M ? T2 : s->M;
+    s->fpend_total = 0;
+    if (nc > 0) {
+        int rc = project(s, nc);
+        if (rc) return rc;
+    }
+    if (keep > 0) {
+        CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
+                           cudaMemcpyDeviceToDevice, s->st));
+        if (s->cross)
+            CK(cudaMemcpyAsync(s->stage_y[s->cur ^ 1], s->stage_y[s->cur] + nview - keep,
+                               (size_t)keep * sizeof(float2), cudaMemcpyDeviceToDevice, s->st));
+    }
+    s->n_eff += nc;
+    s->T = T2;
+    if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
+    s->cur ^= 1;
+    s->held = keep;
+    return CYC_OK;
+}
+
+// Run the pending pushes of a stream (Full mode: fold them; Set mode: project them) before
+// anything reads or replaces its state.
 int settle(cyc_stream* s)
 {
-    if (!s->full || s->fpend.empty()) return CYC_OK;
+    if (s->full ? s->fpend.empty() : s->fpend_total == 0) return CYC_OK;
     DeviceGuard g(s->device);
     if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
-    return full_flush(s);
+    return s->full ? full_flush(s) : set_flush(s);
 }
 
 // After a stream synchronisation: did a kernel's bounded wait give up?
@@ -827,49 +865,33 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
         for (auto& e : s->ev_read) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     if (s->full) return full_push(s, src, ysrc, nsamples, on_device != 0);
-    int64_t left = nsamples;
-    // a windowed pass holds at most win_splits hop-aligned partials
+    // a1: the view is [carried tail (held samples) | pending samples], for both inputs.  Each
+    // push is copied in behind what is pending (a host chunk through the copy stream, once
+    // the pass that last viewed this buffer is done); the projection runs when the view
+    // holds a full pass (max_chunk samples, or win_splits - 1 hops for windowed streams) and
+    // before anything reads the stream, so that short pushes share one launch.
     const int64_t pass = s->win ? std::min<int64_t>(s->max_chunk, (int64_t)(s->win_splits - 1) * s->hop) : s->max_chunk;
+    int64_t left = nsamples;
     while (left > 0) {
-        int64_t c = left < pass ? left : pass;
-        float2* view = s->stage[s->cur];
-        // a1: the view is [carried tail (held samples) | new samples], for both inputs.  A host
-        // chunk lands through the copy stream once the pass that last viewed this buffer is
-        // done; the tail [0, held) comes from the previous pass on the compute stream.
+        const int64_t c = std::min<int64_t>(left, pass - s->fpend_total);
+        const int64_t at = s->held + s->fpend_total;
         cudaStream_t cs = on_device ? s->st : s->xst;
         if (!on_device) CK(cudaStreamWaitEvent(cs, s->ev_read[s->cur], 0));
-        CK(cudaMemcpyAsync(view + s->held, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
+        CK(cudaMemcpyAsync(s->stage[s->cur] + at, src, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
         if (s->cross)
-            CK(cudaMemcpyAsync(s->stage_y[s->cur] + s->held, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
+            CK(cudaMemcpyAsync(s->stage_y[s->cur] + at, ysrc, (size_t)c * sizeof(float2), cudaMemcpyDefault, cs));
         if (!on_device) {
             CK(cudaEventRecord(s->ev_copied, cs));
-            CK(cudaStreamWaitEvent(s->st, s->ev_copied, 0));
+            s->fpend_host = true;
         }
-        const int64_t nview = s->held + c;
-        int64_t nc = nview - s->M;
-        if (nc < 0) nc = 0;
-        const int64_t T2 = s->T + c;
-        const int64_t keep = T2 < s->M ? T2 : s->M;
-        if (nc > 0) {
-            int rc = project(s, nc);
-            if (rc) return rc;
-        }
-        // the last `keep` samples of the view become the next view's head
-        if (keep > 0) {
-            CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
-                               cudaMemcpyDeviceToDevice, s->st));
-            if (s->cross)
-                CK(cudaMemcpyAsync(s->stage_y[s->cur ^ 1], s->stage_y[s->cur] + nview - keep,
-                                   (size_t)keep * sizeof(float2), cudaMemcpyDeviceToDevice, s->st));
-        }
-        s->n_eff += nc;
-        s->T = T2;
-        if (s->xst) CK(cudaEventRecord(s->ev_read[s->cur], s->st));     // this view is free again
-        s->cur ^= 1;
-        s->held = keep;
+        s->fpend_total += c;
         src += c;
         if (ysrc) ysrc += c;
         left -= c;
+        if (s->fpend_total == pass) {
+            int rc = set_flush(s);
+            if (rc) return rc;
+        }
     }
     return CYC_OK;
 }
@@ -1183,6 +1205,7 @@ int cyc_phase_increment(double a, uint64_t* phi)
 int cyc_sums(cyc_stream* s, double** sums, int64_t* nvalues, int64_t* n_eff)
 {
     if (!s || !sums) return fail(CYC_EINVAL, "cyc_sums: NULL argument");
+    if (int rc0 = settle(s)) return rc0;
     if (s->win) return fail(CYC_ENOTSUP, "cyc_sums: windowed streams keep their windows apart from the sums");
     if (s->full) return fail(CYC_ENOTSUP, "cyc_sums: Full-mode streams keep float-float folds, not FP64 sums");
     DeviceGuard g(s->device);
