@@ -49,6 +49,7 @@ TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "fp16": 1e-2}
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu file) and the
 # samples one launch projects.
 TRAFFIC = {
+    "proj_tc@1c7ae1991702@1048576": 8481536 + 3235584,   # profiles/proj_tc_bf16x3_cfg1_ncu.md
 }
 
 
