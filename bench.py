@@ -469,15 +469,16 @@ def proposer_leg(pkg, nsig=64, k=32, pushes=64):
 def cross_leg(pkg, x_dev, T=1 << 24, reps=2):
     """Eq. (impl-corr) in full: two inputs and signed lags at the config-1 shape -- lags
     -64..63 (128, M^- = 64), 1024 cycle frequencies, both forms, BF16x3, 2^16-sample
-    pushes -- with y the config-1 stream delayed by one sample; device time per push next
-    to the one-input stream (lags 0..127) on the same samples."""
+    pushes staged into 2^20-sample passes -- with y the config-1 stream delayed by one
+    sample; device time per push next to the one-input stream (lags 0..127) on the same
+    samples."""
     import torch
     C = CHUNK
     alphas = -0.5 + np.arange(NALPHAS) / NALPHAS
     y_dev = torch.roll(x_dev[:2 * T], 2)
     res = {"workload": "cfg1 shape, two inputs: lags -64..63, 1024 a, CONV+CONJ, bf16x3, %d samples" % T}
     for name, lags, cross in (("cross_signed", np.arange(-64, 64), True), ("one_input", np.arange(128), False)):
-        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C, cross=cross) as s:
+        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=PASS, cross=cross) as s:
             def run():
                 s.reset()
                 for c in range(T // C):
