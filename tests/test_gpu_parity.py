@@ -103,6 +103,37 @@ def test_chunk_split_invariance(cyc, precision):
 
 
 @pytest.mark.parametrize("precision", PRECS)
+def test_staged_passes(cyc, precision):
+    """Pushes are staged behind each other and projected once max_chunk samples are staged
+    or the stream is read: ragged device and host pushes that fill passes of 1000 samples
+    several at a time and cross their boundaries, with reads (each runs what is staged)
+    between them, give the oracle's estimate of everything pushed so far at every read."""
+    import torch
+    x = synth.white(9000, seed=112).astype(np.complex64)
+    lags = np.arange(0, 40, 3)
+    alphas = np.linspace(-0.5, 0.5, 23, endpoint=False)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    splits = [1, 38, 39, 40, 2, 7, 997, 13, 1500, 1, 1, 333, 2999]
+    splits.append(x.size - sum(splits))
+    tol = TOL[precision]
+    with cyc.Stream(lags, alphas, BOTH, precision=precision, max_chunk=1000) as s:
+        pos = 0
+        for k, c in enumerate(splits):
+            if k % 3 == 2:
+                s.push(np.ascontiguousarray(x[pos:pos + c]))
+            else:
+                s.push(xt[2 * pos:2 * (pos + c)])
+            pos += c
+            if k in (3, 6, 9) and pos > 39:
+                R, n = s.read()
+                Ro, no = oracle.estimate(x[:pos], lags, alphas)
+                assert n == no and rel_err(R, Ro, x[:pos], 39) < tol, k
+        R, n = s.read()
+    Ro, no = oracle.estimate(x, lags, alphas)
+    assert n == no and rel_err(R, Ro, x, 39) < tol
+
+
+@pytest.mark.parametrize("precision", PRECS)
 def test_large_start_index(cyc, precision):
     x = synth.white(4000, seed=105).astype(np.complex64)
     lags = np.arange(6)
