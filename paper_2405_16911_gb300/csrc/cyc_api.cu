@@ -862,7 +862,11 @@ static int push_impl(cyc_stream* s, const void* xchunk, const void* ychunk, int6
     if (!on_device && !s->xst) {
         CK(cudaStreamCreateWithFlags(&s->xst, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&s->ev_copied, cudaEventDisableTiming));
-        for (auto& e : s->ev_read) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // both staging buffers are free once the work queued so far is done
+        for (auto& e : s->ev_read) {
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            CK(cudaEventRecord(e, s->st));
+        }
     }
     if (s->full) return full_push(s, src, ysrc, nsamples, on_device != 0);
     // a1: the view is [carried tail (held samples) | pending samples], for both inputs.  Each
