@@ -466,6 +466,28 @@ def proposer_leg(pkg, nsig=64, k=32, pushes=64):
             "breakeven_samples": (t_prop / max(t_full - t_top, 1e-12)) * C if t_full > t_top else None}
 
 
+def propose_timing(pkg, calls=200, nsig=8):
+    """cyc_propose alone on held-out config-4 signals: wall time per call (features, net,
+    top-k, confidence, the synchronisation and the copy of the proposals)."""
+    import torch
+    from paper_2405_16911_gb300 import proposer_train as pt
+    xs = pt.make_signals(nsig, pt.SEED_TEST)
+    xd = torch.from_numpy(xs.view(np.float32)).cuda().view(nsig, pt.NS * 2)
+    net = pkg.cyc_net_create(np.load(pt.WEIGHTS), 0)
+    try:
+        for i in range(3):
+            pkg.cyc_propose(net, xd[i % nsig], pt.NS, k=32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(calls):
+            pkg.cyc_propose(net, xd[i % nsig], pt.NS, k=32)
+        t1 = time.perf_counter()
+    finally:
+        pkg.cyc_net_destroy(net)
+    return {"workload": "cyc_propose on held-out config-4 signals (65552 samples), top-32 per form",
+            "calls": calls, "us_per_call": (t1 - t0) / calls * 1e6}
+
+
 def cross_leg(pkg, x_dev, T=1 << 24, reps=2):
     """Eq. (impl-corr) in full: two inputs and signed lags at the config-1 shape -- lags
     -64..63 (128, M^- = 64), 1024 cycle frequencies, both forms, BF16x3, 2^16-sample
@@ -886,6 +908,8 @@ def main():
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print it")
     ap.add_argument("--latency-only", action="store_true", help="run the config-0 latency leg alone and print it")
     ap.add_argument("--latency-calls", type=int, default=1000)
+    ap.add_argument("--propose-only", action="store_true", help="time cyc_propose alone and print it")
+    ap.add_argument("--propose-calls", type=int, default=200)
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1 ranks: cut one config-1 stream into N time shards and merge them with one "
                          "all-reduce of the running sums (strong scaling) instead of N independent replicas")
@@ -903,6 +927,13 @@ def main():
         torch.cuda.set_device(0)
         pkg.load()
         print(json.dumps(serving_leg(pkg, seconds=args.serving_seconds)))
+        return 0
+    if args.propose_only:
+        import torch
+        import paper_2405_16911_gb300 as pkg
+        torch.cuda.set_device(0)
+        pkg.load()
+        print(json.dumps(propose_timing(pkg, calls=args.propose_calls)))
         return 0
     if args.latency_only:
         import torch
