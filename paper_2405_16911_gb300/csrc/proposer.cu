@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "cyc_impl.h"
+#include "tc_ptx.cuh"
 
 using namespace cyc;
 
@@ -88,17 +89,18 @@ __device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, floa
             const float2 u = xs[(size_t)seg * NFFT + k + lag];      // x[n+d] conj(x[n])
             y = make_float2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);
         }
-        float s, c;
-        sincospif(2.0f * k / NFFT, &s, &c);
-        float w = 0.5f - 0.5f * c;                    // Hann
+        // Hann: 1/2 - 1/2 cos(2 pi k / N), the cosine read from the twiddle table
+        // (cos(2 pi k / N) = -cos(2 pi (k - N/2) / N) in the upper half)
+        const float c = k < NFFT / 2 ? tw[k].x : -tw[k - NFFT / 2].x;
+        float w = 0.5f - 0.5f * c;
         d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
     }
-    for (int half = 1; half < NFFT; half <<= 1) {
+    for (int lh = 0; lh < 12; ++lh) {                 // butterflies of span half = 2^lh
         __syncthreads();
-        const int tstep = NFFT / (2 * half);
+        const int half = 1 << lh, tstep = NFFT >> (lh + 1);
         for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
-            const int grp = bf / half, pos = bf % half;
-            const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+            const int grp = bf >> lh, pos = bf & (half - 1);
+            const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
             const float2 w = tw[pos * tstep];
             const float2 a = d[i0], b = d[i1];
             const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
@@ -265,36 +267,136 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIn* __restrict__ x, in
     }
 }
 
-// The output layer (cout = 2) for few signals: one thread per position computes both outputs.
-__global__ void __launch_bounds__(256) conv_out2_kernel(const __half* __restrict__ x, int cin,
-                                                        const __half* __restrict__ w, const float* __restrict__ bias,
-                                                        float* __restrict__ y)
+// The 64-output-channel layers on the tensor cores (tcgen05, one CTA, kind::f16, FP32 sums in
+// TMEM): y[b][co][p] = act(bias[co] + sum_{t<9} sum_ci w[co][ci][t] x[b][ci][(p + t - 4) mod 4096])
+// is a GEMM over k = (t, ci) with M = positions and N = 64 output channels.  The CTA stages
+// 256 + 8 positions of every input channel transposed, [ci / 8][row][8 channels] (16-byte rows
+// one after another), so the A operand of tap t is the same tile started t rows later; the
+// weights arrive packed as [t][ci / 8][co][8 channels] (pack_conv_kernel) by one bulk copy.
+// Per CTA 9 x (cin16 / 16) MMAs of 128 x 64 x 16 (cin padded to a multiple of 16 with zeros),
+// then 8 warps read the 128 x 64 accumulator (lane = position; warps w and w + 4 take the
+// two halves of the channels of lane quadrant w) and store.
+constexpr int CT_POS = 128, CT_ROWS = CT_POS + 8, CT_T = 256;
+constexpr uint32_t CT_XLBO = CT_ROWS * 16;                 // bytes between 8-channel groups of x
+constexpr long long kConvWaitBudget = 2000000000ll;        // SM cycles per bounded wait
+
+int conv_ch(int cin) { return (cin + 15) / 16 * 2; }        // 8-channel groups, padded to 16 channels
+int conv_nco(int cout) { return cout > 16 ? 64 : 16; }      // MMA N: 64 output channels, or 16 (padded)
+size_t conv_tc_smem(int cin, int nco)
 {
-    constexpr int TI = 256;
-    extern __shared__ float csm[];
-    float* xs = csm;                          // [cin][TI + 8]
-    float* ws = csm + cin * (TI + 8);         // [2][cin][9]
-    const int b = blockIdx.z, i0 = blockIdx.x * TI, tid = threadIdx.x;
-    const __half* xb = x + (size_t)b * cin * NFFT;
-    for (int e = tid; e < cin * (TI + 8); e += 256) {
-        const int c = e / (TI + 8), j = e % (TI + 8);
-        xs[e] = __half2float(xb[(size_t)c * NFFT + ((i0 + j - 4 + NFFT) & (NFFT - 1))]);
+    return (size_t)conv_ch(cin) * CT_XLBO + (size_t)KW * conv_ch(cin) * nco * 16 + 64;
+}
+
+// w [co][ci][t] (FP16) -> [t][ci / 8][co < nco][ci % 8], zero beyond cin and cout
+__global__ void pack_conv_kernel(const __half* __restrict__ w, int cin, int ch, int cout, int nco,
+                                 __half* __restrict__ out)
+{
+    const int total = KW * ch * nco * 8;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int j = e & 7, co = (e >> 3) % nco, tc_ = e / (nco * 8);
+        const int c = tc_ % ch, t = tc_ / ch, ci = c * 8 + j;
+        out[e] = ci < cin && co < cout ? w[((size_t)co * cin + ci) * KW + t] : __float2half(0.f);
     }
-    for (int e = tid; e < 2 * cin * KW; e += 256) ws[e] = __half2float(w[e]);
+}
+
+template <int NCO>
+__device__ __forceinline__ void tmem_ld_half(uint32_t taddr, uint32_t (&r)[NCO / 2])
+{
+    if constexpr (NCO == 64) tc::tmem_ld32(taddr, r);
+    else tc::tmem_ld8(taddr, r);
+}
+
+template <typename TOut, int NCO>
+__global__ void __launch_bounds__(CT_T) conv_tc_kernel(const __half* __restrict__ x, int cin, int ch, int cout,
+                                                         const __half* __restrict__ wpk,
+                                                         const float* __restrict__ bias, int relu,
+                                                         TOut* __restrict__ y, int* err)
+{
+    constexpr int TCOLS = NCO < 32 ? 32 : NCO;                 // TMEM columns allocated (at least 32)
+    extern __shared__ __align__(1024) unsigned char ctsm[];
+    unsigned char* xs = ctsm;                                               // [ch][CT_ROWS][8]
+    unsigned char* ws = ctsm + ch * CT_XLBO;                                // [KW][ch][CT_CO][8]
+    const uint32_t wbytes = (uint32_t)(KW * ch * NCO * 16);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ws + wbytes);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+    int* okf = reinterpret_cast<int*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int p0 = blockIdx.x * CT_POS, b = blockIdx.y;
+    const __half* xb = x + (size_t)b * cin * NFFT;
+    if (warp == 0) tc::tmem_alloc<TCOLS>(slot);
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
-    float a0 = 0.f, a1 = 0.f;
-    for (int c = 0; c < cin; ++c) {
-        const float* xr = xs + c * (TI + 8) + tid;
-        const float* w0 = ws + c * KW;
-        const float* w1 = ws + (cin + c) * KW;
+    if (tid == 0) {
+        tc::mbar_arrive_expect_tx(bar, wbytes);
+        tc::bulk_g2s(ws, wpk, wbytes, bar);
+    }
+    // the input tile: row r is position p0 - 4 + r (circular), 8 channels per 16-byte word
+    for (int e = tid; e < CT_ROWS * ch; e += CT_T) {
+        const int c = e / CT_ROWS, r = e - c * CT_ROWS;
+        const int pos = (p0 - 4 + r) & (NFFT - 1);
+        uint32_t v[4];
 #pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            a0 = fmaf(w0[k], xr[k], a0);
-            a1 = fmaf(w1[k], xr[k], a1);
+        for (int j = 0; j < 4; ++j) {
+            const int c0 = c * 8 + 2 * j;
+            const __half h0 = c0 < cin ? xb[(size_t)c0 * NFFT + pos] : __float2half(0.f);
+            const __half h1 = c0 + 1 < cin ? xb[(size_t)(c0 + 1) * NFFT + pos] : __float2half(0.f);
+            const __half2 hh = __halves2half2(h0, h1);
+            v[j] = *reinterpret_cast<const uint32_t*>(&hh);
+        }
+        *reinterpret_cast<uint4*>(xs + c * CT_XLBO + r * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *slot;
+    if (tid == 0) {
+        int ok = tc::mbar_wait(bar, 0, kConvWaitBudget) ? 1 : 0;       // the weights have landed
+        if (ok) {
+            const uint32_t idesc = tc::idesc_f16(128, NCO, false);
+            const uint32_t xa = tc::smem_u32(xs), wa = tc::smem_u32(ws);
+            uint32_t acc = 0;
+            for (int t = 0; t < KW; ++t)
+                for (int c = 0; c < ch; c += 2) {
+                    const uint64_t ad = tc::smem_desc(xa + c * CT_XLBO + (uint32_t)t * 16, CT_XLBO, 128);
+                    const uint64_t bd = tc::smem_desc(wa + (uint32_t)((t * ch + c) * NCO) * 16, NCO * 16, 128);
+                    tc::mma_f16(tmem, ad, bd, idesc, acc);
+                    acc = 1;
+                }
+            tc::mma_commit(bar);
+        } else {
+            atomicExch(err, 1);
+        }
+        *okf = ok;
+    }
+    __syncthreads();
+    bool ok = *okf != 0;
+    if (ok && !tc::mbar_wait(bar, 1, kConvWaitBudget)) {                 // the accumulators are final
+        atomicExch(err, 1);
+        ok = false;
+    }
+    tc::tc_fence_after();
+    if (ok) {
+        const int q = warp & 3, hf = warp >> 2;
+        const int p = p0 + 32 * q + lane;
+        uint32_t r[NCO / 2];
+        tmem_ld_half<NCO>(tmem + ((uint32_t)(32 * q) << 16) + hf * (NCO / 2), r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < NCO / 2; ++j) {
+            const int co = hf * (NCO / 2) + j;
+            if (co >= cout) break;
+            float v = __uint_as_float(r[j]) + (bias ? bias[co] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            y[((size_t)b * cout + co) * NFFT + p] = (TOut)v;
         }
     }
-    y[((size_t)b * 2 + 0) * NFFT + i0 + tid] = a0 + bias[0];
-    y[((size_t)b * 2 + 1) * NFFT + i0 + tid] = a1 + bias[1];
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc<TCOLS>(tmem);
 }
 
 // dW[o][c][k] += sum_b sum_i dz[b][o][i] h[b][c][(i + k - 4) mod N];  db[o] += sum dz[b][o][i]
@@ -461,6 +563,8 @@ struct cyc_net {
     float* conf = nullptr;
     float* pg = nullptr;      // [NIN][NSEG][NFFT] one signal's segment periodograms (cyc_propose)
     int* h_res = nullptr;     // page-locked copy of topi and conf
+    __half* wpk[NL] = {nullptr, nullptr, nullptr, nullptr};   // conv weights packed for the tensor cores
+    int* derr = nullptr;      // set by a tensor-core conv whose bounded wait gave up (in topi's buffer)
 
     void free_acts()
     {
@@ -520,32 +624,62 @@ cudaError_t conv(const TI* x, int cin, int cout, const __half* w, const float* b
     return conv_mp<TI, TO, 4>(x, cin, cout, w, bias, relu, mask, y, B, st);
 }
 
+// the FP16 weights of the 64-channel layers in the tensor-core kernel's layout (after every
+// change of n->ph)
+cudaError_t pack_weights(cyc_net* n, cudaStream_t st)
+{
+    for (int l = 0; l < NL; ++l)
+        pack_conv_kernel<<<64, 256, 0, st>>>(n->ph + LAY.w[l], CHS[l], conv_ch(CHS[l]), CHS[l + 1],
+                                             conv_nco(CHS[l + 1]), n->wpk[l]);
+    return cudaGetLastError();
+}
+
+// Layer l on the tensor cores: y = relu(conv) in FP16 for the hidden layers, the plain
+// convolution in FP32 for the output layer.
+cudaError_t conv_tc(const cyc_net* n, int l, const __half* x, void* y, int B, cudaStream_t st)
+{
+    static bool set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<__half, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)conv_tc_smem(64, 64));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_tc_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)conv_tc_smem(64, 16));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) set[dev] = true;
+    }
+    const int cin = CHS[l], cout = CHS[l + 1];
+    const dim3 grid(NFFT / CT_POS, B);
+    if (l < NL - 1)
+        conv_tc_kernel<__half, 64><<<grid, CT_T, conv_tc_smem(cin, 64), st>>>(
+            x, cin, conv_ch(cin), cout, n->wpk[l], n->p + LAY.b[l], 1, static_cast<__half*>(y), n->derr);
+    else
+        conv_tc_kernel<float, 16><<<grid, CT_T, conv_tc_smem(cin, 16), st>>>(
+            x, cin, conv_ch(cin), cout, n->wpk[l], n->p + LAY.b[l], 0, static_cast<float*>(y), n->derr);
+    return cudaGetLastError();
+}
+
+// After a synchronisation: did a tensor-core convolution give up waiting?
+int net_status(cyc_net* n, int flag)
+{
+    if (!flag) return CYC_OK;
+    cudaMemset(n->derr, 0, sizeof(int));
+    return pfail(CYC_ETIMEDOUT, "a tensor-core convolution gave up waiting; the outputs are unreliable");
+}
+
 // forward of B feature sets; leaves h[1..3], z4 and (pooled) logits in the net's buffers
 int net_forward(cyc_net* n, const __half* feats, int B, cudaStream_t st)
 {
     int rc = ensure_batch(n, B);
     if (rc) return rc;
     const __half* in = feats;
-    for (int l = 0; l < NL - 1; ++l) {
-        PCK((conv<__half, __half>(in, CHS[l], CHS[l + 1], n->ph + LAY.w[l], n->p + LAY.b[l], 1, nullptr, n->h[l + 1], B, st)));
+    for (int l = 0; l < NL - 1; ++l) {                 // 11 -> 64 -> 64 -> 64
+        PCK(conv_tc(n, l, in, n->h[l + 1], B, st));
         in = n->h[l + 1];
     }
-    if (B <= kSmallBatch) {
-        const size_t sm = (size_t)CHS[NL - 1] * (256 + 8) * 4 + (size_t)2 * CHS[NL - 1] * KW * 4;
-        static bool set[64] = {false};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev < 0 || dev >= 64 || !set[dev]) {
-            PCK(cudaFuncSetAttribute(conv_out2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            if (dev >= 0 && dev < 64) set[dev] = true;
-        }
-        conv_out2_kernel<<<dim3(NFFT / 256, 1, B), 256, sm, st>>>(in, CHS[NL - 1], n->ph + LAY.w[NL - 1],
-                                                               n->p + LAY.b[NL - 1], n->z4);
-        PCK(cudaGetLastError());
-    } else {
-        PCK((conv<__half, float>(in, CHS[NL - 1], CHS[NL], n->ph + LAY.w[NL - 1], n->p + LAY.b[NL - 1], 0, nullptr,
-                                 n->z4, B, st)));
-    }
+    PCK(conv_tc(n, NL - 1, in, n->z4, B, st));       // 64 -> 2, FP32 out
     return CYC_OK;
 }
 
@@ -627,15 +761,20 @@ int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out
     chk(cudaMalloc(&n->wt, 64 * 64 * KW * sizeof(__half)));
     chk(cudaMalloc(&n->loss, sizeof(float)));
     chk(cudaMalloc(&n->feats, NIN * NFFT * sizeof(__half)));
-    chk(cudaMalloc(&n->topi, (2 * NBIN + 2) * sizeof(int)));
+    chk(cudaMalloc(&n->topi, (2 * NBIN + 4) * sizeof(int)));
     n->conf = reinterpret_cast<float*>(n->topi + 2 * NBIN);
+    n->derr = n->topi + 2 * NBIN + 2;
+    for (int l = 0; l < NL; ++l)
+        chk(cudaMalloc(&n->wpk[l], (size_t)KW * conv_ch(CHS[l]) * conv_nco(CHS[l + 1]) * 8 * sizeof(__half)));
     chk(cudaMalloc(&n->pg, (size_t)NIN * NSEG * NFFT * sizeof(float)));
-    chk(cudaMallocHost(&n->h_res, (2 * NBIN + 2) * sizeof(int)));
+    chk(cudaMallocHost(&n->h_res, (2 * NBIN + 4) * sizeof(int)));
     if (rc == CYC_OK) {
         chk(cudaMemcpy(n->p, host.data(), LAY.total * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
         chk(cudaMemset(n->v, 0, LAY.total * sizeof(float)));
+        chk(cudaMemset(n->topi, 0, (2 * NBIN + 4) * sizeof(int)));
         to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+        chk(pack_weights(n, 0));
         chk(cudaDeviceSynchronize());
     }
     if (rc != CYC_OK) {
@@ -651,7 +790,8 @@ int cyc_net_destroy(cyc_net* n)
     if (!n) return CYC_OK;
     cudaSetDevice(n->device);
     n->free_acts();
-    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->pg};
+    void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->pg,
+                  n->wpk[0], n->wpk[1], n->wpk[2], n->wpk[3]};
     for (void* q : ps)
         if (q) cudaFree(q);
     if (n->h_res) cudaFreeHost(n->h_res);
@@ -675,6 +815,7 @@ int cyc_net_set_params(cyc_net* n, const float* params)
     cudaSetDevice(n->device);
     PCK(cudaMemcpy(n->p, params, LAY.total * sizeof(float), cudaMemcpyHostToDevice));
     to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+    PCK(pack_weights(n, 0));
     PCK(cudaDeviceSynchronize());
     n->step = 0;
     PCK(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
@@ -711,7 +852,9 @@ int cyc_net_forward(cyc_net* n, const void* feats, int B, float* logits)
     pool_loss_kernel<<<(ne + 255) / 256, 256>>>(n->z4, nullptr, B, 1.f, logits, nullptr, nullptr);
     PCK(cudaGetLastError());
     PCK(cudaDeviceSynchronize());
-    return CYC_OK;
+    int flag = 0;
+    PCK(cudaMemcpy(&flag, n->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    return net_status(n, flag);
 }
 
 int cyc_net_gradients(cyc_net* n, const void* feats, const float* labels, int B, float pos_weight, float* grads,
@@ -724,6 +867,9 @@ int cyc_net_gradients(cyc_net* n, const void* feats, const float* labels, int B,
     rc = net_backward(n, (const __half*)feats, labels, B, pos_weight, 0);
     if (rc) return rc;
     PCK(cudaDeviceSynchronize());
+    int flag = 0;
+    PCK(cudaMemcpy(&flag, n->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if ((rc = net_status(n, flag))) return rc;
     if (grads) PCK(cudaMemcpy(grads, n->g, LAY.total * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss) PCK(cudaMemcpy(loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost));
     return CYC_OK;
@@ -739,6 +885,7 @@ int cyc_net_train_step(cyc_net* n, const void* feats, const float* labels, int B
     const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
     adam_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, n->g, n->m, n->v, LAY.total, lr, b1, b2, c1, c2, 1e-8f);
     to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
+    PCK(pack_weights(n, 0));
     PCK(cudaGetLastError());
     return CYC_OK;
 }
@@ -783,8 +930,9 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
     PCK(cudaGetLastError());
     // one synchronisation: the proposals [2][k] and the confidences (stored after them)
     PCK(cudaMemcpyAsync(n->h_res, n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost, 0));
-    PCK(cudaMemcpyAsync(n->h_res + 2 * NBIN, n->conf, 2 * sizeof(float), cudaMemcpyDeviceToHost, 0));
+    PCK(cudaMemcpyAsync(n->h_res + 2 * NBIN, n->conf, 2 * sizeof(float) + sizeof(int), cudaMemcpyDeviceToHost, 0));
     PCK(cudaStreamSynchronize(0));
+    if ((rc = net_status(n, n->h_res[2 * NBIN + 2]))) return rc;
     const int* idx = n->h_res;
     float cf[2];
     memcpy(cf, n->h_res + 2 * NBIN, sizeof cf);
