@@ -417,9 +417,10 @@ def precision_leg(pkg, reps=3):
 def proposer_leg(pkg, nsig=64, k=32, pushes=64):
     """Config 4: what the learned proposer buys.  One-off cost of a proposal (features, net,
     top-k, confidence) per held-out 65552-sample signal of the serving mix, and the cost of
-    estimating 2^16 further samples of a stream (lags 0..63, both forms, BF16x3) on the full
-    512-point grid against the proposed cycle frequencies (the 2k proposals of both forms in
-    one stream); with the recall of those proposals against the full-grid detections."""
+    estimating 2^16 further samples of a stream (lags 0..63, both forms, BF16x3, pushes staged
+    into 2^20-sample passes) on the full 512-point grid against the proposed cycle frequencies
+    (the 2k proposals of both forms in one stream); with the recall of those proposals
+    against the full-grid detections."""
     import torch
     from paper_2405_16911_gb300 import proposer_train as pt
     xs = pt.make_signals(nsig, pt.SEED_TEST)
@@ -440,7 +441,7 @@ def proposer_leg(pkg, nsig=64, k=32, pushes=64):
                          .view(np.float32)).cuda()
 
     def per_push(alphas):
-        with pkg.Stream(pt.LAGS, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C) as s:
+        with pkg.Stream(pt.LAGS, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=PASS) as s:
             def run():
                 s.reset()
                 for c in range(pushes):
