@@ -434,8 +434,10 @@ CYC_API int cyc_server_stats(cyc_server* srv, int64_t* batches, int64_t* items, 
  * each channel standardised; FP16 [nsig][11][4096].
  * Net: circular 1-D convolutions, kernel 9, 11 -> 64 -> 64 -> 64 -> 2 channels, ReLU after
  * the first three, mean over groups of 8 bins: logits [B][form][512] (CONV, CONJ).  FP16
- * weights and activations, FP32 sums; parameters as one flat FP32 vector
- * (W1 b1 W2 b2 W3 b3 W4 b4, W[out][in][9]) of cyc_net_nparams() values.
+ * weights and activations, FP32 sums (the forward convolutions on the tensor cores);
+ * parameters as one flat FP32 vector (W1 b1 W2 b2 W3 b3 W4 b4, W[out][in][9]) of
+ * cyc_net_nparams() values.  The forward's bounded device waits report CYC_ETIMEDOUT from
+ * cyc_net_forward, cyc_net_gradients, cyc_net_train_step and cyc_propose.
  * Training minimises the mean binary cross-entropy with logits (positives weighted by
  * pos_weight) against labels [B][form][512] in {0, 1}, with Adam (0.9, 0.999, 1e-8).
  * ====================================================================================== */
