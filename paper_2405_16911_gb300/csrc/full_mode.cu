@@ -555,6 +555,7 @@ cudaError_t full_fold(const FoldArgs& f, cudaStream_t st)
     const size_t smem = (size_t)FQG * FNBUF * FR * rl * sizeof(float2) + kRedBytes;
     if (smem > kFoldSmem) return cudaErrorInvalidValue;
     const dim3 grid(f.A >= FJ ? f.A / FJ : 1, (f.L + FLT - 1) / FLT);
+    if (grid.y > 65535) return cudaErrorInvalidValue;      // more than 2^20 lags
     return mode == 0 ? launch_fold<0>(f, grid, smem, st)
          : mode == 1 ? launch_fold<1>(f, grid, smem, st)
                      : launch_fold<2>(f, grid, smem, st);
@@ -574,7 +575,12 @@ cudaError_t full_windows(const FoldArgs& a, const FullWinArgs& w, int nwin, cuda
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const size_t smem = (size_t)w.N * 5 / 2 * sizeof(float2);
-    window_fft_kernel<<<dim3(a.L, nwin), 256, smem, st>>>(a, w);
+    for (int i0 = 0; i0 < nwin; i0 += 65535) {             // grid.y holds 65535 windows
+        FullWinArgs wi = w;
+        wi.k0 = w.k0 + i0;
+        wi.vbase0 = w.vbase0 + (int64_t)i0 * w.hop;
+        window_fft_kernel<<<dim3(a.L, nwin - i0 < 65535 ? nwin - i0 : 65535), 256, smem, st>>>(a, wi);
+    }
     return cudaGetLastError();
 }
 
@@ -582,8 +588,11 @@ cudaError_t full_read_windows(const float2* ring, int64_t cap, int64_t k0, int64
                               double2* out, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    const dim3 grid(((N + 31) / 32) * ((L + 31) / 32), F, (unsigned)n);
-    window_read_kernel<<<grid, dim3(32, 8), 0, st>>>(ring, cap, k0, N, F, L, out);
+    for (int64_t i0 = 0; i0 < n; i0 += 65535) {             // grid.z holds 65535 windows
+        const int64_t m = n - i0 < 65535 ? n - i0 : 65535;
+        const dim3 grid(((N + 31) / 32) * ((L + 31) / 32), F, (unsigned)m);
+        window_read_kernel<<<grid, dim3(32, 8), 0, st>>>(ring, cap, k0 + i0, N, F, L, out + (size_t)i0 * F * N * L);
+    }
     return cudaGetLastError();
 }
 
