@@ -198,7 +198,10 @@ struct cyc_stream {
     double2* d_out = nullptr;
     int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
     int* h_err = nullptr;       // page-locked copy, read after a stream synchronisation
+    int* h_err_dev = nullptr;   // its address on the device (a read kernel writes it directly)
     void* h_stage = nullptr;    // page-locked landing buffer of cyc_read into host memory (first use)
+    void* h_stage_dev = nullptr;   // its address on the device (nullptr: copied into it instead)
+    int* d_cnt = nullptr;       // register-sum passes: arrival counter per column group
     // host pushes: chunks are copied on a stream of their own, so that the copy of one pass
     // overlaps the projection of the previous one (created at the first host push)
     cudaStream_t xst = nullptr;
@@ -227,12 +230,15 @@ struct cyc_stream {
             if (e) { cudaEventDestroy(e); e = nullptr; }
         void* ps[] = {stage[0], stage[1], stage_y[0], stage_y[1], sums, d_phi, d_amap, d_col_lag, d_col_conj,
                       part, d_out, d_err, w_ring, w_sum, w_pend, w_out, d_lags, sp_E, sp_S,
-                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count, d_fsl, d_fperm, d_ftw};
+                      dt_s, dt_flags, dt_ratio, dt_dc, dt_count, d_fsl, d_fperm, d_ftw, d_cnt};
         for (void* p : ps)
             if (p) cudaFree(p);
         if (h_err) cudaFreeHost(h_err);
         if (h_stage) cudaFreeHost(h_stage);
         h_stage = nullptr;
+        h_stage_dev = nullptr;
+        h_err_dev = nullptr;
+        d_cnt = nullptr;
         stage[0] = stage[1] = stage_y[0] = stage_y[1] = nullptr;
         sums = nullptr; d_phi = nullptr; d_amap = nullptr; d_col_lag = nullptr;
         d_col_conj = nullptr; part = nullptr; d_out = nullptr; d_err = nullptr; h_err = nullptr;
@@ -318,8 +324,12 @@ int alloc_state(cyc_stream* s)
     }
     if (s->precision != CYC_P_FP32)
         s->part_elems = tc_max_partials(s->units.U, s->Au, s->ncols, s->num_sms);
-    else if (small_supported(s->Au))
+    else if (small_supported(s->Au)) {
         s->part_elems = small_max_partials(s->Au, s->ncols, s->num_sms);
+        const int ng = small_groups(s->Au, s->ncols);
+        CK(dev_malloc((void**)&s->d_cnt, ng * sizeof(int)));
+        CK(cudaMemset(s->d_cnt, 0, ng * sizeof(int)));
+    }
     else
         s->part_elems = fp32_max_partials(s->Au, s->ncols, s->num_sms);
     if (s->win && !s->full) {
@@ -358,12 +368,19 @@ int alloc_state(cyc_stream* s)
     CK(cudaMemset(s->d_err, 0, sizeof(int)));
     CK(cudaMallocHost(&s->h_err, sizeof(int)));
     *s->h_err = 0;
+    if (cudaHostGetDevicePointer((void**)&s->h_err_dev, s->h_err, 0) != cudaSuccess) {
+        cudaGetLastError();
+        s->h_err_dev = nullptr;
+    }
     return CYC_OK;
 }
 
-// One device pass over view = stage[cur][0 .. held + c): nc committed terms.
-int project(cyc_stream* s, int64_t nc)
+// One device pass over view = stage[cur][0 .. held + c): nc committed terms.  The view's
+// samples [tail_from, + keep) are the next view's head: *tail_done says whether the pass
+// copied them (the register-sum kernel does) or the caller must.
+int project(cyc_stream* s, int64_t nc, int64_t tail_from, int64_t keep, bool* tail_done)
 {
+    *tail_done = false;
     ProjArgs a;
     a.x = s->stage[s->cur];
     a.nc = nc;
@@ -399,6 +416,19 @@ int project(cyc_stream* s, int64_t nc)
     a.split_len = pl.split_len;
     if ((size_t)pl.nsplit * s->Au * s->ncols > s->part_elems)
         return fail(CYC_ECUDA, "internal: partial buffer too small (%d splits)", pl.nsplit);
+    if (small) {                      // one launch: the FP64 update and the tail copy included
+        if (!s->win) {
+            a.sums = s->sums;
+            a.cnt = s->d_cnt;
+        }
+        if (keep > 0) {
+            a.tail_from = tail_from;
+            a.tail_keep = keep;
+            a.tail_x = s->stage[s->cur ^ 1];
+            a.tail_y = s->cross ? s->stage_y[s->cur ^ 1] : nullptr;
+            *tail_done = true;
+        }
+    }
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (s->prof) {
         if (!s->ev_free.empty()) {
@@ -438,10 +468,12 @@ int project(cyc_stream* s, int64_t nc)
         const int64_t done = (s->n_eff + nc) / s->hop;           // hops complete after this pass
         s->hops = done;
         s->win_made = done >= s->win_w ? done - s->win_w + 1 : 0;
-    } else {
+        s->kernel_launches++;
+    } else if (!a.sums) {
         CK(reduce_partials(s->part, pl.nsplit, s->Au * s->ncols, s->sums, s->st));
+        s->kernel_launches++;
     }
-    s->kernel_launches += 2;
+    s->kernel_launches++;
     return CYC_OK;
 }
 
@@ -602,11 +634,12 @@ int set_flush(cyc_stream* s)
     const int64_t T2 = s->T + c;
     const int64_t keep = T2 < s->M ? T2 : s->M;
     s->fpend_total = 0;
+    bool tail_done = false;
     if (nc > 0) {
-        int rc = project(s, nc);
+        int rc = project(s, nc, nview - keep, keep, &tail_done);
         if (rc) return rc;
     }
-    if (keep > 0) {
+    if (keep > 0 && !tail_done) {
         CK(cudaMemcpyAsync(s->stage[s->cur ^ 1], view + nview - keep, (size_t)keep * sizeof(float2),
                            cudaMemcpyDeviceToDevice, s->st));
         if (s->cross)
@@ -631,12 +664,10 @@ int settle(cyc_stream* s)
     return s->full ? full_flush(s) : set_flush(s);
 }
 
-// After a stream synchronisation: did a kernel's bounded wait give up?
-// Queues the copy of the kernels' status word, synchronises the stream and reports it.
-int sync_and_check(cyc_stream* s)
+// After a stream synchronisation: did a kernel's bounded wait give up?  The status word has
+// landed in h_err; report and clear it.
+int check_status(cyc_stream* s)
 {
-    CK(cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
     const int flag = *s->h_err;
     if (flag) {
         *s->h_err = 0;
@@ -645,6 +676,14 @@ int sync_and_check(cyc_stream* s)
         return fail(CYC_ETIMEDOUT, "a projection kernel gave up waiting (code %d); the sums are unreliable", flag);
     }
     return CYC_OK;
+}
+
+// Queues the copy of the kernels' status word, synchronises the stream and reports it.
+int sync_and_check(cyc_stream* s)
+{
+    CK(cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return check_status(s);
 }
 
 bool is_device_ptr(const void* p, int device, bool* wrong_device)
@@ -934,23 +973,39 @@ int cyc_read(cyc_stream* s, double* out, int64_t* n_eff)
     bool dev = is_device_ptr(out, s->device, &wrong);
     if (wrong) return fail(CYC_EINVAL, "cyc_read: out is memory of another device");
     if (dev && misaligned16(out)) return fail(CYC_EINVAL, "cyc_read: device out must be 16-byte aligned");
-    double2* dst = dev ? (double2*)out : s->d_out;
+    // host memory: the result lands in a page-locked buffer of the handle's (up to 64 MB, made
+    // at the first host read) and is copied from there.  Set-mode streams have the read
+    // kernel write it, and the status word beside it, straight into page-locked memory (one
+    // launch, one synchronisation); Full-mode streams, or without a device address for the
+    // buffer, queue its copy beside the status word's; without the buffer the copy goes
+    // straight to `out`.
+    const size_t bytes = (size_t)s->F * s->A * s->L * sizeof(double2);
+    if (!dev && !s->h_stage && bytes <= ((size_t)64 << 20)) {
+        if (cudaMallocHost(&s->h_stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            s->h_stage = nullptr;
+        } else if (cudaHostGetDevicePointer(&s->h_stage_dev, s->h_stage, 0) != cudaSuccess) {
+            cudaGetLastError();
+            s->h_stage_dev = nullptr;
+        }
+    }
+    const bool direct = !dev && !s->full && s->h_stage_dev && s->h_err_dev;
+    double2* dst = dev ? (double2*)out : direct ? (double2*)s->h_stage_dev : s->d_out;
     if (s->full)
         CK(full_read(s->sums, s->Au, s->ncols, s->F, s->L, 1.0 / (double)s->n_eff, dst, s->st));
     else
-        CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st));
+        CK(read_sums(s->sums, s->d_amap, s->F, s->A, s->L, s->ncols, 1.0 / (double)s->n_eff, dst, s->st,
+                     direct ? s->d_err : nullptr, direct ? s->h_err_dev : nullptr));
     s->kernel_launches++;
     if (dev) return sync_and_check(s);
-    // host memory: the result lands in a page-locked buffer of the handle's (one copy queued
-    // beside the status word, one synchronisation) and is copied from there; without that
-    // buffer (up to 64 MB, made at the first host read) the copy goes straight to `out`
-    const size_t bytes = (size_t)s->F * s->A * s->L * sizeof(double2);
-    if (!s->h_stage && bytes <= ((size_t)64 << 20) && cudaMallocHost(&s->h_stage, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        s->h_stage = nullptr;
+    int rc;
+    if (direct) {
+        CK(cudaStreamSynchronize(s->st));
+        rc = check_status(s);
+    } else {
+        CK(cudaMemcpyAsync(s->h_stage ? s->h_stage : (void*)out, s->d_out, bytes, cudaMemcpyDeviceToHost, s->st));
+        rc = sync_and_check(s);
     }
-    CK(cudaMemcpyAsync(s->h_stage ? s->h_stage : (void*)out, s->d_out, bytes, cudaMemcpyDeviceToHost, s->st));
-    const int rc = sync_and_check(s);
     if (rc == CYC_OK && s->h_stage) memcpy(out, s->h_stage, bytes);
     return rc;
 }

@@ -48,6 +48,15 @@ struct ProjArgs {
     int             np = 0, nself = 0, U = 0;
     long long       budget = 0;     // SM cycles per bounded wait (0: kDefaultWaitBudget)
     int             withhold = 0;   // test only: the projection leaves one producer arrival out
+    // register-sum path only: with `sums` set, the last block of each column group to finish
+    // adds the splits' partials to the FP64 running sums (`cnt`: one arrival counter per
+    // column group, zero between launches); with tail_keep > 0, x[tail_from, + tail_keep)
+    // (and y's) are copied to tail_x (tail_y), the next view's carried head
+    double2*        sums = nullptr;
+    int*            cnt = nullptr;
+    int64_t         tail_from = 0, tail_keep = 0;
+    float2*         tail_x = nullptr;
+    float2*         tail_y = nullptr;
 };
 
 // One work item of the tensor-core projection: 128 units of cycle frequencies (up to 256
@@ -193,6 +202,7 @@ size_t      fp32_max_partials(int Au, int ncols, int num_sms);   // float2 eleme
 // a warp-shuffle fold (proj_small.cu).
 bool        small_supported(int Au);
 ProjPlan    small_plan(int Au, int ncols, int64_t nc, int num_sms);
+int         small_groups(int Au, int ncols);   // column groups (blocks per split) of the grid
 cudaError_t small_launch(const ProjArgs& a, cudaStream_t st);
 size_t      small_max_partials(int Au, int ncols, int num_sms);
 
@@ -319,7 +329,10 @@ cudaError_t read_windows(const float2* wout, int64_t cap, int64_t k0, int64_t n,
                          const uint64_t* phi, int F, int A, int L, int Au, int ncols, uint64_t base, int64_t hop,
                          double inv_n, double2* out, cudaStream_t st);
 // out[f][a][l] = sums[amap[a]][l * F + f] / n_eff
+// With err_dst set, the launch also copies the status word *err_src there (a page-locked
+// host word, so that a host read needs no copy besides the one into `out`).
 cudaError_t read_sums(const double2* sums, const int32_t* amap, int F, int A, int L, int ncols,
-                      double inv_n, double2* out, cudaStream_t st);
+                      double inv_n, double2* out, cudaStream_t st, const int* err_src = nullptr,
+                      int* err_dst = nullptr);
 
 }  // namespace cyc

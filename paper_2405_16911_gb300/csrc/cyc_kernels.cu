@@ -55,9 +55,11 @@ __global__ void reduce_partials_kernel(const float2* __restrict__ part, int nspl
 
 // out[f][a][l] = sums[amap[a]][l * F + f] * inv_n   (normalisation by N_eff, Sec. 4)
 __global__ void read_sums_kernel(const double2* __restrict__ sums, const int32_t* __restrict__ amap,
-                                 int F, int A, int L, int ncols, double inv_n, double2* __restrict__ out)
+                                 int F, int A, int L, int ncols, double inv_n, double2* __restrict__ out,
+                                 const int* err_src, int* err_dst)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (err_dst && e == 0) *err_dst = *err_src;
     int64_t total = (int64_t)F * A * L;
     if (e >= total) return;
     int l = (int)(e % L);
@@ -202,11 +204,12 @@ cudaError_t reduce_partials(const float2* part, int nsplit, int n_uc, double2* s
 }
 
 cudaError_t read_sums(const double2* sums, const int32_t* amap, int F, int A, int L, int ncols,
-                      double inv_n, double2* out, cudaStream_t st)
+                      double inv_n, double2* out, cudaStream_t st, const int* err_src, int* err_dst)
 {
     int64_t total = (int64_t)F * A * L;
     if (total <= 0) return cudaSuccess;
-    read_sums_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sums, amap, F, A, L, ncols, inv_n, out);
+    read_sums_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sums, amap, F, A, L, ncols, inv_n, out,
+                                                                      err_src, err_dst);
     return cudaGetLastError();
 }
 
