@@ -261,7 +261,8 @@ CYC_API int cyc_push_xy(cyc_stream* s, const void* x_chunk, const void* y_chunk,
  * `out`, which may be host or device memory of at least F * nalphas * nlags * 16 bytes
  * (device memory 16-byte aligned: CYC_EINVAL otherwise).  A host `out` is filled from a
  * page-locked buffer of F * nalphas * nlags * 16 bytes (up to 64 MB) that the handle keeps
- * after its first host read.
+ * after its first host read; for Set-mode streams the read kernel writes the result there
+ * through the buffer's device address (no separate copy).
  * *n_eff (optional) receives N_eff.  CYC_ENODATA when N_eff == 0 (out untouched).
  */
 CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);
