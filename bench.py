@@ -530,9 +530,11 @@ def cross_leg(pkg, x_dev, T=1 << 24, reps=2):
 def window_leg(pkg, x_dev, T=1 << 24, reps=2):
     """The block's windowed output (Eq. (impl-corr) at every window start k * hop, window-local
     phase) at the config-1 shape: windows of N = 65536 reference samples every 4096 samples,
-    lags 0..127, 1024 cycle frequencies, both forms, BF16x3, 2^16-sample pushes, every window
-    read into device memory after every second push (the ring holds 32); wall time per push
-    next to the running-sum stream, and windows per second."""
+    lags 0..127, 1024 cycle frequencies, both forms, BF16x3, 2^16-sample pushes staged like the
+    main step's (max_chunk 2^20: a windowed stream projects up to 63 hops per pass, and every
+    read of windows ends a pass), every window read into device memory after every second
+    push (the ring holds 32); wall time per push next to the running-sum stream, and windows
+    per second."""
     import torch
     C = CHUNK
     N, H = 1 << 16, 4096
@@ -544,7 +546,7 @@ def window_leg(pkg, x_dev, T=1 << 24, reps=2):
                        "%d samples" % T}
     for name, window in (("windowed", (N, H, cap)), ("running_sums", None)):
         nwin = [0]
-        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=C, window=window) as s:
+        with pkg.Stream(lags, alphas, pkg.CYC_BOTH, precision="bf16x3", max_chunk=PASS, window=window) as s:
             def run():
                 s.reset()
                 nwin[0] = 0
