@@ -305,6 +305,33 @@ def test_fp32_small_and_general_paths(cyc, na):
     assert rel_err(R, Ro, x, 89) < 1e-5
 
 
+@pytest.mark.parametrize("na", [1, 2, 3, 6, 12, 20, 31])
+def test_register_sum_passes(cyc, na):
+    """The register-sum path updates the FP64 sums and copies the carried tail inside its one
+    launch (the last block of each column group adds the splits; its arrival counter is reset
+    for the next launch): many short passes (max_chunk 700, ragged pushes, reads in between),
+    one input and two, every block shape, each read against the oracle."""
+    import torch
+    T = 6000
+    x = synth.white(T, seed=113 + na).astype(np.complex64)
+    y = (0.6 * np.roll(x, 5) + 0.8 * synth.white(T, seed=213 + na)).astype(np.complex64)
+    lags = np.array([-7, 0, 1, 4, 9, 30])
+    alphas = np.random.default_rng(114 + na).uniform(-0.5, 0.5, na)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    yt = torch.from_numpy(y.view(np.float32).copy()).cuda()
+    cuts = [0, 1, 699, 700, 1901, 2500, 4444, T]
+    for cross in (False, True):
+        with cyc.Stream(lags, alphas, BOTH, precision="fp32", max_chunk=700, cross=cross) as s:
+            for k in range(len(cuts) - 1):
+                a, b = cuts[k], cuts[k + 1]
+                s.push(xt[2 * a:2 * b], y=yt[2 * a:2 * b] if cross else None)
+                if b in (1901, 4444, T):
+                    R, n = s.read()
+                    Ro, no = oracle.estimate_xy(x[:b], y[:b] if cross else None, lags, alphas)
+                    nrm = oracle.r00_xy(x[:b], y[:b] if cross else None, 7, 30)
+                    assert n == no and np.max(np.abs(R - Ro)) / nrm < 1e-5, (cross, b)
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16"])
 def test_tensor_core_unit_kinds(cyc, precision):
     """The tensor-core projection takes a and -a together (one pair of weight rows), 0 and
