@@ -72,7 +72,8 @@ const Layout LAY;
 
 // ------------------------------------------------------------------------ features (FFT)
 // The windowed DFT of one segment of one channel into d (shared memory, natural order):
-// d[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), radix-2 decimation in time over tw.
+// d[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), radix-2 decimation in time over tw (the
+// twiddles of each butterfly span stored together, see twiddles()).
 __device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, float2* d, const float2* tw)
 {
     const int tid = threadIdx.x;
@@ -89,19 +90,19 @@ __device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, floa
             const float2 u = xs[(size_t)seg * NFFT + k + lag];      // x[n+d] conj(x[n])
             y = make_float2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);
         }
-        // Hann: 1/2 - 1/2 cos(2 pi k / N), the cosine read from the twiddle table
-        // (cos(2 pi k / N) = -cos(2 pi (k - N/2) / N) in the upper half)
-        const float c = k < NFFT / 2 ? tw[k].x : -tw[k - NFFT / 2].x;
+        // Hann: 1/2 - 1/2 cos(2 pi k / N), the cosine read from the twiddle table (tw[N/2 + k]
+        // = exp(-j 2 pi k / N); cos(2 pi k / N) = -cos(2 pi (k - N/2) / N) in the upper half)
+        const float c = k < NFFT / 2 ? tw[NFFT / 2 + k].x : -tw[k].x;
         float w = 0.5f - 0.5f * c;
         d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
     }
     for (int lh = 0; lh < 12; ++lh) {                 // butterflies of span half = 2^lh
         __syncthreads();
-        const int half = 1 << lh, tstep = NFFT >> (lh + 1);
+        const int half = 1 << lh;
         for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
             const int grp = bf >> lh, pos = bf & (half - 1);
             const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
-            const float2 w = tw[pos * tstep];
+            const float2 w = tw[half + pos];
             const float2 a = d[i0], b = d[i1];
             const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
             d[i0] = make_float2(a.x + bw.x, a.y + bw.y);
@@ -111,12 +112,21 @@ __device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, floa
     __syncthreads();
 }
 
+// tw[h + p] = exp(-j pi p / h) for the spans h = 1, 2, 4, ..., N/2 and p < h (tw[0] unused):
+// the twiddles of one butterfly stage are consecutive, so a warp reads consecutive words (one
+// table exp(-j 2 pi k / N) read at k = p N / 2h put a stage's twiddles N / 2h entries apart,
+// in one shared-memory bank for the middle stages).
 __device__ void twiddles(float2* tw)
 {
-    for (int k = threadIdx.x; k < NFFT / 2; k += blockDim.x) {
+    for (int m = threadIdx.x; m < NFFT; m += blockDim.x) {
+        if (m == 0) {
+            tw[0] = make_float2(1.f, 0.f);
+            continue;
+        }
+        const int h = 1 << (31 - __clz(m));
         float s, c;
-        sincospif(-2.0f * k / NFFT, &s, &c);              // exp(-j 2 pi k / N)
-        tw[k] = make_float2(c, s);
+        sincospif(-(float)(m - h) / (float)h, &s, &c);
+        tw[m] = make_float2(c, s);
     }
 }
 
@@ -157,8 +167,8 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
 {
     extern __shared__ float fsm[];
     float2* d = reinterpret_cast<float2*>(fsm);          // 4096 complex
-    float2* tw = d + NFFT;                                // 2048 twiddles
-    float* acc = reinterpret_cast<float*>(tw + NFFT / 2); // 4096
+    float2* tw = d + NFFT;                                // 4096 twiddles (twiddles())
+    float* acc = reinterpret_cast<float*>(tw + NFFT);     // 4096
     const int sig = blockIdx.x / NIN, ch = blockIdx.x % NIN, tid = threadIdx.x;
     const float2* xs = x + (size_t)sig * T;
     twiddles(tw);
@@ -172,11 +182,14 @@ __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict_
 }
 
 // One signal, latency first: one CTA per (channel, segment) writes its periodogram to
-// pg [NIN][NSEG][NFFT]; features_finish_kernel then sums the segments in order (the same
-// sums, in the same order, as features_kernel) and finishes each channel.
-__global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restrict__ x, float* __restrict__ pg)
+// pg [NIN][NSEG][NFFT]; the last CTA of a channel to finish (arrival counter cnt[ch], reset
+// by that CTA) sums the channel's segments in order (the same sums, in the same order, as
+// features_kernel) and finishes the channel.
+__global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restrict__ x, float* __restrict__ pg,
+                                                          int* __restrict__ cnt, __half* __restrict__ out)
 {
     extern __shared__ float fsm[];
+    __shared__ int last;
     float2* d = reinterpret_cast<float2*>(fsm);
     float2* tw = d + NFFT;
     const int ch = blockIdx.x / NSEG, seg = blockIdx.x % NSEG;
@@ -184,24 +197,25 @@ __global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restri
     segment_dft(x, ch, seg, d, tw);
     float* o = pg + ((size_t)ch * NSEG + seg) * NFFT;
     for (int k = threadIdx.x; k < NFFT; k += blockDim.x) o[k] = d[k].x * d[k].x + d[k].y * d[k].y;
-}
-
-__global__ void __launch_bounds__(512) features_finish_kernel(const float* __restrict__ pg, __half* __restrict__ out)
-{
-    __shared__ float acc[NFFT];
-    __shared__ float v[NFFT];
-    const int ch = blockIdx.x;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&cnt[ch], 1) == NSEG - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    float* acc = fsm;                                     // d is free: [NFFT] sums, [NFFT] scratch
     for (int k = threadIdx.x; k < NFFT; k += blockDim.x) {
         float q[NSEG];
 #pragma unroll
-        for (int seg = 0; seg < NSEG; ++seg) q[seg] = pg[((size_t)ch * NSEG + seg) * NFFT + k];
+        for (int sg = 0; sg < NSEG; ++sg) q[sg] = __ldcg(&pg[((size_t)ch * NSEG + sg) * NFFT + k]);
         float a = 0.f;
 #pragma unroll
-        for (int seg = 0; seg < NSEG; ++seg) a += q[seg];
+        for (int sg = 0; sg < NSEG; ++sg) a += q[sg];
         acc[k] = a;
     }
     __syncthreads();
-    finish_channel(acc, v, out + (size_t)ch * NFFT);
+    finish_channel(acc, acc + NFFT, out + (size_t)ch * NFFT);
+    if (threadIdx.x == 0) cnt[ch] = 0;                    // ready for the next signal
 }
 
 // ------------------------------------------------------------------------ convolution
@@ -509,8 +523,11 @@ __global__ void to_half_kernel(const float* __restrict__ p, int n, __half* __res
 // Top-K per form by logit: a bitonic sort of the 512 (logit, bin) pairs in shared memory,
 // larger logit first and the lower bin first among equal logits.  Confidence of a form:
 // 1 - sigmoid of the best bin left out, i.e. how sure the net is that no line was left behind.
+// With hres set (page-locked host memory laid out like idx: proposals at [f k + r], the
+// confidences at [2 NBIN + f], the status word at [2 NBIN + 2]) the results, and the status
+// word *derr, are written there as well.
 __global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
-                                                   float* __restrict__ conf)
+                                                   float* __restrict__ conf, int* hres, const int* derr)
 {
     __shared__ float val[NBIN];
     __shared__ int bin[NBIN];
@@ -533,8 +550,14 @@ __global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ log
         }
     }
     __syncthreads();
+    const float cf = k < NBIN ? 1.f - 1.f / (1.f + expf(-val[k])) : 1.f;
     if (t < k) idx[f * k + t] = bin[t];
-    if (t == 0) conf[f] = k < NBIN ? 1.f - 1.f / (1.f + expf(-val[k])) : 1.f;
+    if (t == 0) conf[f] = cf;
+    if (hres) {
+        if (t < k) hres[f * k + t] = bin[t];
+        if (t == 0) hres[2 * NBIN + f] = __float_as_int(cf);
+        if (t == 0 && f == 0) hres[2 * NBIN + 2] = *derr;
+    }
 }
 
 }  // namespace
@@ -563,6 +586,8 @@ struct cyc_net {
     float* conf = nullptr;
     float* pg = nullptr;      // [NIN][NSEG][NFFT] one signal's segment periodograms (cyc_propose)
     int* h_res = nullptr;     // page-locked copy of topi and conf
+    int* h_res_dev = nullptr; // its device address (nullptr: copied into it instead)
+    int* fcnt = nullptr;      // [NIN] arrival counters of periodogram_kernel
     __half* wpk[NL] = {nullptr, nullptr, nullptr, nullptr};   // conv weights packed for the tensor cores
     int* derr = nullptr;      // set by a tensor-core conv whose bounded wait gave up (in topi's buffer)
 
@@ -767,12 +792,18 @@ int cyc_net_create(const float* params, uint64_t seed, int device, cyc_net** out
     for (int l = 0; l < NL; ++l)
         chk(cudaMalloc(&n->wpk[l], (size_t)KW * conv_ch(CHS[l]) * conv_nco(CHS[l + 1]) * 8 * sizeof(__half)));
     chk(cudaMalloc(&n->pg, (size_t)NIN * NSEG * NFFT * sizeof(float)));
+    chk(cudaMalloc(&n->fcnt, NIN * sizeof(int)));
     chk(cudaMallocHost(&n->h_res, (2 * NBIN + 4) * sizeof(int)));
+    if (rc == CYC_OK && cudaHostGetDevicePointer((void**)&n->h_res_dev, n->h_res, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n->h_res_dev = nullptr;
+    }
     if (rc == CYC_OK) {
         chk(cudaMemcpy(n->p, host.data(), LAY.total * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemset(n->m, 0, LAY.total * sizeof(float)));
         chk(cudaMemset(n->v, 0, LAY.total * sizeof(float)));
         chk(cudaMemset(n->topi, 0, (2 * NBIN + 4) * sizeof(int)));
+        chk(cudaMemset(n->fcnt, 0, NIN * sizeof(int)));
         to_half_kernel<<<(LAY.total + 255) / 256, 256>>>(n->p, LAY.total, n->ph);
         chk(pack_weights(n, 0));
         chk(cudaDeviceSynchronize());
@@ -791,7 +822,7 @@ int cyc_net_destroy(cyc_net* n)
     cudaSetDevice(n->device);
     n->free_acts();
     void* ps[] = {n->p, n->ph, n->g, n->m, n->v, n->wt, n->loss, n->labels, n->feats, n->xbuf, n->topi, n->pg,
-                  n->wpk[0], n->wpk[1], n->wpk[2], n->wpk[3]};
+                  n->fcnt, n->wpk[0], n->wpk[1], n->wpk[2], n->wpk[3]};
     for (void* q : ps)
         if (q) cudaFree(q);
     if (n->h_res) cudaFreeHost(n->h_res);
@@ -829,7 +860,7 @@ int cyc_features(const void* x, int64_t T, int nsig, void* feats)
     if (T < (int64_t)NSEG * NFFT + MAXD)
         return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT + MAXD);
     static bool set[64] = {false};                        // the attribute is per device
-    const int smem = NFFT * 8 + NFFT / 2 * 8 + NFFT * 4;
+    const int smem = NFFT * 8 + NFFT * 8 + NFFT * 4;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !set[dev]) {
@@ -909,28 +940,30 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
         PCK(cudaMemcpy(n->xbuf, x, use * sizeof(float2), cudaMemcpyHostToDevice));
         xd = n->xbuf;
     }
-    // features of one signal: a CTA per (channel, segment), then one per channel
+    // features of one signal: a CTA per (channel, segment); the last of each channel finishes it
     {
         static bool set[64] = {false};
-        const int smem = NFFT * 8 + NFFT / 2 * 8;
+        const int smem = NFFT * 8 + NFFT * 8;
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev < 0 || dev >= 64 || !set[dev]) {
             PCK(cudaFuncSetAttribute(periodogram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             if (dev >= 0 && dev < 64) set[dev] = true;
         }
-        periodogram_kernel<<<NIN * NSEG, 512, smem>>>(xd, n->pg);
-        features_finish_kernel<<<NIN, 512>>>(n->pg, n->feats);
+        periodogram_kernel<<<NIN * NSEG, 512, smem>>>(xd, n->pg, n->fcnt, n->feats);
         PCK(cudaGetLastError());
     }
     int rc = net_forward(n, n->feats, 1, 0);
     if (rc) return rc;
     pool_loss_kernel<<<(2 * NBIN + 255) / 256, 256>>>(n->z4, nullptr, 1, 1.f, n->logits, nullptr, nullptr);
-    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf);
+    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf, n->h_res_dev, n->derr);
     PCK(cudaGetLastError());
-    // one synchronisation: the proposals [2][k] and the confidences (stored after them)
-    PCK(cudaMemcpyAsync(n->h_res, n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost, 0));
-    PCK(cudaMemcpyAsync(n->h_res + 2 * NBIN, n->conf, 2 * sizeof(float) + sizeof(int), cudaMemcpyDeviceToHost, 0));
+    // one synchronisation: the proposals [2][k] and the confidences (stored after them), written
+    // into page-locked memory by the top-k kernel itself (else copied there)
+    if (!n->h_res_dev) {
+        PCK(cudaMemcpyAsync(n->h_res, n->topi, 2 * k * sizeof(int), cudaMemcpyDeviceToHost, 0));
+        PCK(cudaMemcpyAsync(n->h_res + 2 * NBIN, n->conf, 2 * sizeof(float) + sizeof(int), cudaMemcpyDeviceToHost, 0));
+    }
     PCK(cudaStreamSynchronize(0));
     if ((rc = net_status(n, n->h_res[2 * NBIN + 2]))) return rc;
     const int* idx = n->h_res;
