@@ -71,10 +71,16 @@ struct Layout {
 const Layout LAY;
 
 // ------------------------------------------------------------------------ features (FFT)
-// The windowed DFT of one segment of one channel into d (shared memory, natural order):
-// d[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), radix-2 decimation in time over tw (the
-// twiddles of each butterfly span stored together, see twiddles()).
-__device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, float2* d, const float2* tw)
+// The windowed DFT of one segment of one channel (shared memory, natural order):
+// X[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), by the self-sorting (Stockham) radix-2 form:
+// stage p (p = 1, 2, ..., N/2) combines the length-p transforms held at src[i] and
+// src[i + N/2] into the length-2p transforms dst[2i - k] and dst[2i - k + p] (k = i mod p)
+// with the twiddle exp(-j pi k / p) = tw[p + k] (see twiddles()).  Input and output are in
+// natural order, so no bit-reversed (bank-conflicted) permutation is needed; a warp reads
+// and writes consecutive entries from stage 32 on.  d0 and d1 alternate as source and
+// destination; the result's buffer is returned.
+__device__ float2* segment_dft(const float2* __restrict__ xs, int ch, int seg, float2* d0, float2* d1,
+                               const float2* tw)
 {
     const int tid = threadIdx.x;
     const int lag = ch >= 2 ? c_lagch[ch - 2] : 0;
@@ -94,22 +100,27 @@ __device__ void segment_dft(const float2* __restrict__ xs, int ch, int seg, floa
         // = exp(-j 2 pi k / N); cos(2 pi k / N) = -cos(2 pi (k - N/2) / N) in the upper half)
         const float c = k < NFFT / 2 ? tw[NFFT / 2 + k].x : -tw[k].x;
         float w = 0.5f - 0.5f * c;
-        d[__brev(k) >> 20] = make_float2(y.x * w, y.y * w);   // bit-reversed order (12 bits)
+        d0[k] = make_float2(y.x * w, y.y * w);
     }
-    for (int lh = 0; lh < 12; ++lh) {                 // butterflies of span half = 2^lh
+    float2* src = d0;
+    float2* dst = d1;
+    for (int p = 1; p < NFFT; p <<= 1) {
         __syncthreads();
-        const int half = 1 << lh;
-        for (int bf = tid; bf < NFFT / 2; bf += blockDim.x) {
-            const int grp = bf >> lh, pos = bf & (half - 1);
-            const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
-            const float2 w = tw[half + pos];
-            const float2 a = d[i0], b = d[i1];
+        for (int i = tid; i < NFFT / 2; i += blockDim.x) {
+            const int k = i & (p - 1);
+            const float2 w = tw[p + k];
+            const float2 a = src[i], b = src[i + NFFT / 2];
             const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
-            d[i0] = make_float2(a.x + bw.x, a.y + bw.y);
-            d[i1] = make_float2(a.x - bw.x, a.y - bw.y);
+            const int j = 2 * i - k;
+            dst[j] = make_float2(a.x + bw.x, a.y + bw.y);
+            dst[j + p] = make_float2(a.x - bw.x, a.y - bw.y);
         }
+        float2* t = src;
+        src = dst;
+        dst = t;
     }
     __syncthreads();
+    return src;
 }
 
 // tw[h + p] = exp(-j pi p / h) for the spans h = 1, 2, 4, ..., N/2 and p < h (tw[0] unused):
@@ -166,19 +177,20 @@ __device__ void finish_channel(const float* acc, float* v, __half* o)
 __global__ void __launch_bounds__(512) features_kernel(const float2* __restrict__ x, int64_t T, __half* __restrict__ out)
 {
     extern __shared__ float fsm[];
-    float2* d = reinterpret_cast<float2*>(fsm);          // 4096 complex
-    float2* tw = d + NFFT;                                // 4096 twiddles (twiddles())
+    float2* d0 = reinterpret_cast<float2*>(fsm);         // 2 x 4096 complex (FFT ping-pong)
+    float2* d1 = d0 + NFFT;
+    float2* tw = d1 + NFFT;                               // 4096 twiddles (twiddles())
     float* acc = reinterpret_cast<float*>(tw + NFFT);     // 4096
     const int sig = blockIdx.x / NIN, ch = blockIdx.x % NIN, tid = threadIdx.x;
     const float2* xs = x + (size_t)sig * T;
     twiddles(tw);
     for (int k = tid; k < NFFT; k += blockDim.x) acc[k] = 0.f;
     for (int seg = 0; seg < NSEG; ++seg) {
-        segment_dft(xs, ch, seg, d, tw);
+        const float2* d = segment_dft(xs, ch, seg, d0, d1, tw);
         for (int k = tid; k < NFFT; k += blockDim.x) acc[k] += d[k].x * d[k].x + d[k].y * d[k].y;
     }
     __syncthreads();
-    finish_channel(acc, reinterpret_cast<float*>(d), out + ((size_t)sig * NIN + ch) * NFFT);
+    finish_channel(acc, reinterpret_cast<float*>(d0), out + ((size_t)sig * NIN + ch) * NFFT);
 }
 
 // One signal, latency first: one CTA per (channel, segment) writes its periodogram to
@@ -190,11 +202,12 @@ __global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restri
 {
     extern __shared__ float fsm[];
     __shared__ int last;
-    float2* d = reinterpret_cast<float2*>(fsm);
-    float2* tw = d + NFFT;
+    float2* d0 = reinterpret_cast<float2*>(fsm);
+    float2* d1 = d0 + NFFT;
+    float2* tw = d1 + NFFT;
     const int ch = blockIdx.x / NSEG, seg = blockIdx.x % NSEG;
     twiddles(tw);
-    segment_dft(x, ch, seg, d, tw);
+    const float2* d = segment_dft(x, ch, seg, d0, d1, tw);
     float* o = pg + ((size_t)ch * NSEG + seg) * NFFT;
     for (int k = threadIdx.x; k < NFFT; k += blockDim.x) o[k] = d[k].x * d[k].x + d[k].y * d[k].y;
     __threadfence();
@@ -203,7 +216,7 @@ __global__ void __launch_bounds__(512) periodogram_kernel(const float2* __restri
     __syncthreads();
     if (!last) return;
     __threadfence();
-    float* acc = fsm;                                     // d is free: [NFFT] sums, [NFFT] scratch
+    float* acc = fsm;                                     // d0, d1 are free: [NFFT] sums, [NFFT] scratch
     for (int k = threadIdx.x; k < NFFT; k += blockDim.x) {
         float q[NSEG];
 #pragma unroll
@@ -860,7 +873,7 @@ int cyc_features(const void* x, int64_t T, int nsig, void* feats)
     if (T < (int64_t)NSEG * NFFT + MAXD)
         return pfail(CYC_EINVAL, "cyc_features: signals need at least %d samples", NSEG * NFFT + MAXD);
     static bool set[64] = {false};                        // the attribute is per device
-    const int smem = NFFT * 8 + NFFT * 8 + NFFT * 4;
+    const int smem = 2 * NFFT * 8 + NFFT * 8 + NFFT * 4;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !set[dev]) {
@@ -943,7 +956,7 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
     // features of one signal: a CTA per (channel, segment); the last of each channel finishes it
     {
         static bool set[64] = {false};
-        const int smem = NFFT * 8 + NFFT * 8;
+        const int smem = 2 * NFFT * 8 + NFFT * 8;
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev < 0 || dev >= 64 || !set[dev]) {
