@@ -533,44 +533,45 @@ __global__ void to_half_kernel(const float* __restrict__ p, int n, __half* __res
     if (e < n) h[e] = __float2half_rn(p[e]);
 }
 
-// Top-K per form by logit: a bitonic sort of the 512 (logit, bin) pairs in shared memory,
-// larger logit first and the lower bin first among equal logits.  Confidence of a form:
-// 1 - sigmoid of the best bin left out, i.e. how sure the net is that no line was left behind.
-// With hres set (page-locked host memory laid out like idx: proposals at [f k + r], the
-// confidences at [2 NBIN + f], the status word at [2 NBIN + 2]) the results, and the status
-// word *derr, are written there as well.
-__global__ void __launch_bounds__(512) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
-                                                   float* __restrict__ conf, int* hres, const int* derr)
+// Top-K per form by logit, as ranks: the rank of bin e is the number of bins whose logit is
+// larger, or equal with a lower bin (NaN counts as -inf), so the ranks are a permutation in
+// the order larger logit first, lower bin first among equal logits, and the bin of rank r < k
+// is proposal r.  Confidence of a form: 1 - sigmoid of the logit of rank k (the best bin left
+// out), i.e. how sure the net is that no line was left behind.  Block (form, part) ranks 64
+// bins, 8 threads per bin.  With hres set (page-locked host memory laid out like idx:
+// proposals at [f k + r], the confidences at [2 NBIN + f], the status word at [2 NBIN + 2])
+// the results, and the status word *derr, are written there as well.
+constexpr int TK_BLOCKS = 8, TK_BINS = NBIN / TK_BLOCKS, TK_LANES = NBIN / TK_BINS;
+static_assert(TK_BINS * TK_LANES == NBIN && TK_LANES == 8, "top-k layout");
+
+__global__ void __launch_bounds__(NBIN) topk_kernel(const float* __restrict__ logits, int k, int* __restrict__ idx,
+                                                    float* __restrict__ conf, int* hres, const int* derr)
 {
     __shared__ float val[NBIN];
-    __shared__ int bin[NBIN];
-    const int f = blockIdx.x, t = threadIdx.x;
-    val[t] = logits[f * NBIN + t];
-    bin[t] = t;
-    for (int size = 2; size <= NBIN; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncthreads();
-            const int j = t ^ stride;
-            if (j > t) {
-                const float va = val[t], vb = val[j];
-                const int ia = bin[t], ib = bin[j];
-                const bool a_first = va > vb || (va == vb && ia < ib);
-                if (a_first != ((t & size) == 0)) {
-                    val[t] = vb; val[j] = va;
-                    bin[t] = ib; bin[j] = ia;
-                }
-            }
-        }
-    }
+    const int f = blockIdx.x / TK_BLOCKS, part = blockIdx.x % TK_BLOCKS, t = threadIdx.x;
+    const float v = logits[f * NBIN + t];
+    val[t] = isnan(v) ? -INFINITY : v;
     __syncthreads();
-    const float cf = k < NBIN ? 1.f - 1.f / (1.f + expf(-val[k])) : 1.f;
-    if (t < k) idx[f * k + t] = bin[t];
-    if (t == 0) conf[f] = cf;
-    if (hres) {
-        if (t < k) hres[f * k + t] = bin[t];
-        if (t == 0) hres[2 * NBIN + f] = __float_as_int(cf);
-        if (t == 0 && f == 0) hres[2 * NBIN + 2] = *derr;
+    const int e = part * TK_BINS + t / TK_LANES, q = t % TK_LANES;
+    const float ve = val[e];
+    int r = 0;
+    for (int j = q; j < NBIN; j += TK_LANES) {
+        const float vj = val[j];
+        r += (vj > ve || (vj == ve && j < e)) ? 1 : 0;
     }
+#pragma unroll
+    for (int o = 1; o < TK_LANES; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (q == 0 && r < k) {
+        idx[f * k + r] = e;
+        if (hres) hres[f * k + r] = e;
+    }
+    const bool put_conf = k < NBIN ? (q == 0 && r == k) : (part == 0 && t == 0);
+    if (put_conf) {
+        const float cf = k < NBIN ? 1.f - 1.f / (1.f + expf(-ve)) : 1.f;
+        conf[f] = cf;
+        if (hres) hres[2 * NBIN + f] = __float_as_int(cf);
+    }
+    if (hres && blockIdx.x == 0 && t == 0) hres[2 * NBIN + 2] = *derr;
 }
 
 }  // namespace
@@ -969,7 +970,7 @@ int cyc_propose(cyc_net* n, const void* x, int64_t T, int on_device, int k, floa
     int rc = net_forward(n, n->feats, 1, 0);
     if (rc) return rc;
     pool_loss_kernel<<<(2 * NBIN + 255) / 256, 256>>>(n->z4, nullptr, 1, 1.f, n->logits, nullptr, nullptr);
-    topk_kernel<<<2, NBIN>>>(n->logits, k, n->topi, n->conf, n->h_res_dev, n->derr);
+    topk_kernel<<<2 * TK_BLOCKS, NBIN>>>(n->logits, k, n->topi, n->conf, n->h_res_dev, n->derr);
     PCK(cudaGetLastError());
     // one synchronisation: the proposals [2][k] and the confidences (stored after them), written
     // into page-locked memory by the top-k kernel itself (else copied there)
