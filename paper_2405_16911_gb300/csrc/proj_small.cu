@@ -72,25 +72,36 @@ __global__ void __launch_bounds__(NT) proj_small_kernel(ProjArgs a, int ncb)
 
     const float2* yv = a.y ? a.y : a.x;          // reference input (y = x for the auto forms)
     const float2 zero = make_float2(0.f, 0.f);
+    // the block's columns in registers: lag offsets (a column past ncols reads lag 0's sample
+    // and its sums are never written) and the CONJ flags as a bit mask
+    int lg[CB];
+    unsigned cjm = 0;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+        lg[j] = lag[j];
+        cjm |= cj[j] ? 1u << j : 0u;
+    }
     int64_t n = n_beg + tid;
-    float2 ny = zero, nx[CB];                    // the thread's next sample (columns past ncols: 0)
+    const float2* xn = a.x + n;                  // x[n], y[n + D]: advanced by NT per sample
+    const float2* yn = yv + n + a.D;
+    float2 ny = zero, nx[CB];                    // the thread's next sample
 #pragma unroll
     for (int j = 0; j < CB; ++j) nx[j] = zero;
     if (n < n_end) {
-        ny = __ldg(&yv[n + a.D]);
+        ny = __ldg(yn);
 #pragma unroll
-        for (int j = 0; j < CB; ++j)
-            if (okc[j]) nx[j] = __ldg(&a.x[n + lag[j]]);
+        for (int j = 0; j < CB; ++j) nx[j] = __ldg(xn + lg[j]);
     }
     for (int k = 0; n < n_end; n += NT, ++k) {
         float2 p[CB];
 #pragma unroll
-        for (int j = 0; j < CB; ++j) p[j] = lag_product(nx[j], ny, cj[j]);
+        for (int j = 0; j < CB; ++j) p[j] = lag_product(nx[j], ny, (cjm >> j) & 1u);
+        xn += NT;
+        yn += NT;
         if (n + NT < n_end) {
-            ny = __ldg(&yv[n + NT + a.D]);
+            ny = __ldg(yn);
 #pragma unroll
-            for (int j = 0; j < CB; ++j)
-                if (okc[j]) nx[j] = __ldg(&a.x[n + NT + lag[j]]);
+            for (int j = 0; j < CB; ++j) nx[j] = __ldg(xn + lg[j]);
         }
         if (k % RESEED == 0) {
             const uint64_t nabs = a.nbase + (uint64_t)n;
