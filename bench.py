@@ -644,12 +644,57 @@ def full_leg(pkg, x_dev, reps=2):
         big = full_big_pushes(pkg, x_dev, out, T, CB, reps)
     return {"spectrum_ms": t_spec * 1e3,
             "pushes_2^20": big,
+            "windows": full_windows(pkg, x_dev, min(T, 1 << 24), reps),
             "spectrum": "cyc_read_spectrum: 2 x 1024 cycle frequencies x 256 frequencies over 128 lags, Hann, FP64",
             "workload": "cfg1 stream, Full mode: a = -0.5 + k/1024 by folding mod 1024, lags 0..127, CONV+CONJ, "
                         "%d samples in 2^16 pushes, fp32 products, float-float fold, fp64 DFT" % T,
             "ms": m, "msamples_s": T / (m * 1e-3) / 1e6, "us_per_push": m * 1e3 / (T // C),
             "direct_equivalent_gmac_s": cmac_per_step(T) / (m * 1e-3) / 1e9,
             "err_rel_r00": stored_error(R, "cfg1", T), "err_tol": TOL["fp32"]}
+
+
+def full_windows(pkg, x_dev, T, reps):
+    """Full mode per window (Sec. 4 Full mode: every a = -1/2 + k/N of each window by one
+    N-point FFT per lag, window-local phase) at the config-1 shape: windows of N = 1024
+    reference samples every 1024 samples, lags 0..127, both forms, 2^16-sample device pushes
+    (64 windows each), every window read into device memory after every second push.  Each
+    window is 2 x 1024 x 128 complex values: 2 MB in the FP32 ring, 4 MB read out in FP64, so
+    the mode is bound by writing and reading those (8 MB of HBM traffic per window)."""
+    import torch
+    C = CHUNK
+    A = H = NALPHAS
+    cap = 2 * (C // H)
+    out = torch.empty((cap, NFORMS, A, NLAGS, 2), dtype=torch.float64, device="cuda")
+    nwin = [0]
+    with pkg.Stream(np.arange(NLAGS), None, pkg.CYC_BOTH, full=A, window=(A, H, cap)) as s:
+        def run():
+            s.reset()
+            nwin[0] = 0
+            for c in range(T // C):
+                s.push(x_dev[2 * c * C:2 * (c + 1) * C])
+                if c % 2 == 1:
+                    W, _ = s.read_windows(cap, out)
+                    nwin[0] += W.shape[0]
+            W, _ = s.read_windows(cap, out)
+            nwin[0] += W.shape[0]
+            s.sync()
+        run()
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    m = statistics.median(ms)
+    win_bytes = NFORMS * A * NLAGS * (8 + 8 + 16)          # ring write, ring read, FP64 out
+    return {"workload": "Full mode per window: N = 1024 every 1024 samples, lags 0..127, CONV+CONJ, "
+                        "%d samples in 2^16 pushes, windows read into device memory every second push" % T,
+            "ms": m, "us_per_push": m * 1e3 / (T // C), "windows": nwin[0],
+            "windows_per_s": nwin[0] / (m * 1e-3),
+            "ring_and_out_gb_s": nwin[0] * win_bytes / (m * 1e-3) / 1e9}
 
 
 # --------------------------------------------------------------------------- reference arm

@@ -149,7 +149,7 @@ struct cyc_stream {
     std::vector<Pend> fpend;
     int64_t fpend_total = 0;
     bool fpend_host = false;        // a host copy on the copy stream feeds the pending fold
-    float2* d_ftw = nullptr;        // windowed Full mode: FFT twiddles exp(-j 2 pi j / A), j < A / 2
+    float2* d_ftw = nullptr;        // windowed Full mode: FFT twiddles by span, [h + p] = exp(-j pi p / h)
     int64_t carry = 0;              // samples carried from pass to pass (M; A + M - 1 for Full windows)
     // windowed output (cyc_create_window): window k covers committed n in [k hop, k hop + N)
     bool win = false;
@@ -347,11 +347,15 @@ int alloc_state(cyc_stream* s)
     CK(dev_malloc((void**)&s->part, s->part_elems * sizeof(float2)));
     if (s->win && s->full) {          // Full-mode windows: the ring of spectra and the twiddles
         CK(dev_malloc((void**)&s->w_out, (size_t)s->win_cap * s->ncols * s->A * sizeof(float2)));
-        std::vector<float2> tw(s->A / 2);
-        for (int j = 0; j < s->A / 2; ++j) {
-            const double ang = -2.0 * M_PI * (double)j / (double)s->A;
-            tw[j] = make_float2((float)cos(ang), (float)sin(ang));
-        }
+        // the FFT's twiddles by butterfly span: tw[h + p] = exp(-j pi p / h) = exp(-j 2 pi
+        // (p A / 2h) / A) for h = 1, 2, ..., A/2 and p < h (tw[0] unused)
+        std::vector<float2> tw(s->A);
+        tw[0] = make_float2(1.f, 0.f);
+        for (int h = 1; h < s->A; h <<= 1)
+            for (int q = 0; q < h; ++q) {
+                const double ang = -2.0 * M_PI * (double)(q * (s->A / (2 * h))) / (double)s->A;
+                tw[h + q] = make_float2((float)cos(ang), (float)sin(ang));
+            }
         CK(dev_malloc((void**)&s->d_ftw, tw.size() * sizeof(float2)));
         CK(cudaMemcpy(s->d_ftw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
     } else if (s->win) {

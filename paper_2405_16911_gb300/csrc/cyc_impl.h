@@ -257,7 +257,7 @@ struct FullWinArgs {
     int64_t k0 = 0, hop = 0, vbase0 = 0, cap = 0;
     int N = 0, logN = 0, ncols = 0;
     const int32_t* col_lag = nullptr;    // [ncols] shifted lag of column l F + f
-    const float2* tw = nullptr;          // [N / 2] exp(-j 2 pi j / N), FP32
+    const float2* tw = nullptr;          // [N] FFT twiddles by span: [h + p] = exp(-j pi p / h), FP32
     float2* ring = nullptr;              // [cap][ncols][N]
 };
 cudaError_t full_windows(const FoldArgs& a, const FullWinArgs& w, int nwin, cudaStream_t st);

@@ -377,13 +377,14 @@ __global__ void __launch_bounds__(FT, 1) fold_kernel(FoldArgs a)
 
 // Windowed Full mode.  Block (l, w): window k = k0 + w of lag l, whose reference samples
 // are view samples base + n, n < N (base = vbase0 + w hop), for both forms: the products
-// P(n) = x[base + n + m] c_f(y[base + n + D]) (m the shifted lag) times (-1)^n go in
-// bit-reversed order into shared memory, an in-place radix-2 FFT (FP32, twiddles from a
-// table) gives sum_n P(n) exp(-j 2 pi (-1/2 + kk/N) n), and the spectrum divided by N goes to
-// ring slot (k mod cap) as [column][kk].
+// P(n) = x[base + n + m] c_f(y[base + n + D]) (m the shifted lag) times (-1)^n go in natural
+// order into shared memory, the self-sorting radix-4 FFT (fft_stockham, FP32, both forms
+// side by side) gives sum_n P(n) exp(-j 2 pi (-1/2 + kk/N) n) in natural order, and the
+// spectrum divided by N goes to ring slot (k mod cap) as [column][kk].  No bit-reversed
+// permutation, and a stage's twiddles are consecutive (none that share a bank).
 __global__ void __launch_bounds__(256) window_fft_kernel(FoldArgs a, FullWinArgs w)
 {
-    extern __shared__ __align__(16) float2 fw[];             // [2][N] then the twiddles [N / 2]
+    extern __shared__ __align__(16) float2 fw[];             // V, J twice ([4][N]), twiddles [N]
     __shared__ SrcTab tab;
     if (threadIdx.x == 0) tab.n = a.nsrc;
     if (threadIdx.x <= kFoldSrc) tab.start[threadIdx.x] = a.start[threadIdx.x];
@@ -392,10 +393,12 @@ __global__ void __launch_bounds__(256) window_fft_kernel(FoldArgs a, FullWinArgs
         tab.y[threadIdx.x] = a.sy[threadIdx.x];
     }
     const int N = w.N, l = blockIdx.x;
-    float2* V = fw;
-    float2* J = fw + N;
-    float2* tw = fw + 2 * N;
-    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) tw[j] = w.tw[j];
+    float2* Vs = fw;
+    float2* Js = fw + N;
+    float2* Vd = fw + 2 * N;
+    float2* Jd = fw + 3 * N;
+    float2* tw = fw + 4 * N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) tw[j] = w.tw[j];
     __syncthreads();
     const int m = w.col_lag[l * a.F];                         // shifted lag of lag index l
     const int base = (int)(w.vbase0 + (int64_t)blockIdx.y * w.hop);
@@ -408,36 +411,21 @@ __global__ void __launch_bounds__(256) window_fft_kernel(FoldArgs a, FullWinArgs
         const float2 y = tab.y[cy][vy - tab.start[cy]];
         const float sg = (n & 1) ? -1.f : 1.f;
         const float ar = xm.x * y.x, bi = xm.y * y.y, cr = xm.y * y.x, di = xm.x * y.y;
-        const unsigned r = __brev((unsigned)n) >> (32 - w.logN);
-        V[r] = make_float2(sg * (ar + bi), sg * (cr - di));    // x conj(y)
-        J[r] = make_float2(sg * (ar - bi), sg * (cr + di));    // x y
+        Vs[n] = make_float2(sg * (ar + bi), sg * (cr - di));   // x conj(y)
+        Js[n] = make_float2(sg * (ar - bi), sg * (cr + di));   // x y
     }
-    __syncthreads();
-    for (int len = 2; len <= N; len <<= 1) {
-        const int half = len >> 1, step = N / len;
-        for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
-            const int j = t & (half - 1);
-            const int i0 = (t - j) * 2 + j, i1 = i0 + half;
-            const float2 z = tw[j * step];                      // exp(-j 2 pi j / len)
-            float2 b = V[i1], u = V[i0];
-            float2 q = make_float2(b.x * z.x - b.y * z.y, b.x * z.y + b.y * z.x);
-            V[i0] = make_float2(u.x + q.x, u.y + q.y);
-            V[i1] = make_float2(u.x - q.x, u.y - q.y);
-            b = J[i1];
-            u = J[i0];
-            q = make_float2(b.x * z.x - b.y * z.y, b.x * z.y + b.y * z.x);
-            J[i0] = make_float2(u.x + q.x, u.y + q.y);
-            J[i1] = make_float2(u.x - q.x, u.y - q.y);
-        }
-        __syncthreads();
-    }
+    float2* src[2] = {Vs, Js};
+    float2* dst[2] = {Vd, Jd};
+    fft_stockham<2>(src, dst, N, tw);
+    Vs = src[0];
+    Js = src[1];
     const int64_t slot = (w.k0 + blockIdx.y) % w.cap;
     const float inv = 1.f / (float)N;                          // a power of two: exact
     float2* rV = a.fV >= 0 ? w.ring + ((size_t)slot * w.ncols + l * a.F + a.fV) * N : nullptr;
     float2* rJ = a.fJ >= 0 ? w.ring + ((size_t)slot * w.ncols + l * a.F + a.fJ) * N : nullptr;
     for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
-        if (rV) rV[kk] = make_float2(V[kk].x * inv, V[kk].y * inv);
-        if (rJ) rJ[kk] = make_float2(J[kk].x * inv, J[kk].y * inv);
+        if (rV) rV[kk] = make_float2(Vs[kk].x * inv, Vs[kk].y * inv);
+        if (rJ) rJ[kk] = make_float2(Js[kk].x * inv, Js[kk].y * inv);
     }
 }
 
@@ -570,11 +558,11 @@ cudaError_t full_windows(const FoldArgs& a, const FullWinArgs& w, int nwin, cuda
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(window_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(4096 * 5 / 2 * sizeof(float2)));
+                                             (int)(4096 * 5 * sizeof(float2)));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    const size_t smem = (size_t)w.N * 5 / 2 * sizeof(float2);
+    const size_t smem = (size_t)w.N * 5 * sizeof(float2);
     for (int i0 = 0; i0 < nwin; i0 += 65535) {             // grid.y holds 65535 windows
         FullWinArgs wi = w;
         wi.k0 = w.k0 + i0;

@@ -22,6 +22,7 @@
 
 #include <vector>
 
+#include "cyc_device.cuh"
 #include "cyc_impl.h"
 #include "tc_ptx.cuh"
 
@@ -72,13 +73,10 @@ const Layout LAY;
 
 // ------------------------------------------------------------------------ features (FFT)
 // The windowed DFT of one segment of one channel (shared memory, natural order):
-// X[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), by the self-sorting (Stockham) radix-2 form:
-// stage p (p = 1, 2, ..., N/2) combines the length-p transforms held at src[i] and
-// src[i + N/2] into the length-2p transforms dst[2i - k] and dst[2i - k + p] (k = i mod p)
-// with the twiddle exp(-j pi k / p) = tw[p + k] (see twiddles()).  Input and output are in
-// natural order, so no bit-reversed (bank-conflicted) permutation is needed; a warp reads
-// and writes consecutive entries from stage 32 on.  d0 and d1 alternate as source and
-// destination; the result's buffer is returned.
+// X[k] = sum_n y[n] w[n] exp(-j 2 pi k n / N), by the self-sorting radix-4 form
+// (fft_stockham, twiddles by span from twiddles()).  Input and output are in natural order,
+// so no bit-reversed (bank-conflicted) permutation is needed.  d0 and d1 alternate as source
+// and destination; the result's buffer is returned.
 __device__ float2* segment_dft(const float2* __restrict__ xs, int ch, int seg, float2* d0, float2* d1,
                                const float2* tw)
 {
@@ -102,25 +100,10 @@ __device__ float2* segment_dft(const float2* __restrict__ xs, int ch, int seg, f
         float w = 0.5f - 0.5f * c;
         d0[k] = make_float2(y.x * w, y.y * w);
     }
-    float2* src = d0;
-    float2* dst = d1;
-    for (int p = 1; p < NFFT; p <<= 1) {
-        __syncthreads();
-        for (int i = tid; i < NFFT / 2; i += blockDim.x) {
-            const int k = i & (p - 1);
-            const float2 w = tw[p + k];
-            const float2 a = src[i], b = src[i + NFFT / 2];
-            const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
-            const int j = 2 * i - k;
-            dst[j] = make_float2(a.x + bw.x, a.y + bw.y);
-            dst[j + p] = make_float2(a.x - bw.x, a.y - bw.y);
-        }
-        float2* t = src;
-        src = dst;
-        dst = t;
-    }
-    __syncthreads();
-    return src;
+    float2* src[1] = {d0};
+    float2* dst[1] = {d1};
+    cyc::fft_stockham<1>(src, dst, NFFT, tw);
+    return src[0];
 }
 
 // tw[h + p] = exp(-j pi p / h) for the spans h = 1, 2, 4, ..., N/2 and p < h (tw[0] unused):
