@@ -13,9 +13,10 @@
 // instead of a sine and cosine), restarted from the exact phase every RESEED samples.
 //
 // The grid is one wave (splits x column groups <= the blocks the SMs hold at once).  For a
-// running-sum pass the last block of a column group to finish adds the group's partials,
-// split by split, to the FP64 sums (the same update as reduce_partials, without a second
-// launch), and one block copies the view's carried tail for the next pass.
+// running-sum pass the last block of a column group to finish adds the group's partials to
+// the FP64 sums (the splits summed in FP32 in a fixed order, the total added once in FP64:
+// the update of reduce_partials, without a second launch), and one block copies the view's
+// carried tail for the next pass.
 #include "cyc_device.cuh"
 #include "cyc_impl.h"
 
