@@ -271,7 +271,10 @@ CYC_API int cyc_read(cyc_stream* s, double* out, int64_t* n_eff);
 CYC_API int cyc_sync(cyc_stream* s);
 
 /* cyc_reset: drop all samples and sums (parameters kept).  The zeroing of the sums is
- * queued on the stream's CUDA stream; the call does not wait for it. */
+ * queued on the stream's CUDA stream; the call does not wait for it.  FP32 streams with at
+ * most 32 distinct cycle frequencies (and no windows, no Full mode) queue nothing here: their
+ * next projection writes its totals instead of adding them, or the first call that reads the
+ * sums (cyc_read, cyc_sums, cyc_save, ...) zeroes them first. */
 CYC_API int cyc_reset(cyc_stream* s);
 
 /* cyc_destroy: free the handle and its device memory (NULL is a no-op). */

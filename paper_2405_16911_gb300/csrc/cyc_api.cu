@@ -202,6 +202,7 @@ struct cyc_stream {
     void* h_stage = nullptr;    // page-locked landing buffer of cyc_read into host memory (first use)
     void* h_stage_dev = nullptr;   // its address on the device (nullptr: copied into it instead)
     int* d_cnt = nullptr;       // register-sum passes: arrival counter per column group
+    bool zero_sums = false;     // a reset's zeroing of the sums is still to be done (see cyc_reset)
     // host pushes: chunks are copied on a stream of their own, so that the copy of one pass
     // overlaps the projection of the previous one (created at the first host push)
     cudaStream_t xst = nullptr;
@@ -424,6 +425,8 @@ int project(cyc_stream* s, int64_t nc, int64_t tail_from, int64_t keep, bool* ta
         if (!s->win) {
             a.sums = s->sums;
             a.cnt = s->d_cnt;
+            a.replace = s->zero_sums ? 1 : 0;   // a reset's zeroing folded into this update
+            s->zero_sums = false;
         }
         if (keep > 0) {
             a.tail_from = tail_from;
@@ -662,10 +665,19 @@ int set_flush(cyc_stream* s)
 // anything reads or replaces its state.
 int settle(cyc_stream* s)
 {
-    if (s->full ? s->fpend.empty() : s->fpend_total == 0) return CYC_OK;
+    const bool pending = s->full ? !s->fpend.empty() : s->fpend_total != 0;
+    if (!pending && !s->zero_sums) return CYC_OK;
     DeviceGuard g(s->device);
     if (!g.ok) return fail(CYC_ECUDA, "cudaSetDevice failed");
-    return s->full ? full_flush(s) : set_flush(s);
+    if (pending) {
+        const int rc = s->full ? full_flush(s) : set_flush(s);
+        if (rc) return rc;
+    }
+    if (s->zero_sums) {               // a reset that no pass has folded in yet
+        CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+        s->zero_sums = false;
+    }
+    return CYC_OK;
 }
 
 // After a stream synchronisation: did a kernel's bounded wait give up?  The status word has
@@ -1156,7 +1168,13 @@ int cyc_reset(cyc_stream* s)
     if (!s) return fail(CYC_EINVAL, "cyc_reset: handle is NULL");
     if (int rc0 = settle(s)) return rc0;
     DeviceGuard g(s->device);
-    CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
+    // FP32 streams on the register-sum path (no windows, no Full mode) leave the zeroing to
+    // their next pass, which writes its totals instead of adding them (or to settle(), if
+    // anything reads the sums first); the others zero the sums here
+    if (s->precision == CYC_P_FP32 && small_supported(s->Au) && !s->win && !s->full)
+        s->zero_sums = true;
+    else
+        CK(cudaMemsetAsync(s->sums, 0, (size_t)s->Au * s->ncols * sizeof(double2), s->st));
     if (s->win && !s->full) {
         CK(cudaMemsetAsync(s->w_sum, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));
         CK(cudaMemsetAsync(s->w_pend, 0, (size_t)s->Au * s->ncols * sizeof(float4), s->st));

@@ -54,6 +54,7 @@ struct ProjArgs {
     // (and y's) are copied to tail_x (tail_y), the next view's carried head
     double2*        sums = nullptr;
     int*            cnt = nullptr;
+    int             replace = 0;    // with sums: write the pass's totals (sums zeroed by a reset)
     int64_t         tail_from = 0, tail_keep = 0;
     float2*         tail_x = nullptr;
     float2*         tail_y = nullptr;

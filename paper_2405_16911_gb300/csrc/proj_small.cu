@@ -181,8 +181,12 @@ __global__ void __launch_bounds__(NT) proj_small_kernel(ProjArgs a, int ncb)
             vr += fin[q * E + e].x;
             vi += fin[q * E + e].y;
         }
-        const double2 o = a.sums[idx];
-        a.sums[idx] = make_double2(o.x + (double)vr, o.y + (double)vi);
+        if (a.replace) {
+            a.sums[idx] = make_double2((double)vr, (double)vi);
+        } else {
+            const double2 o = a.sums[idx];
+            a.sums[idx] = make_double2(o.x + (double)vr, o.y + (double)vi);
+        }
     }
     if (tid == 0) a.cnt[blockIdx.x] = 0;                       // ready for the next launch
 }

@@ -332,6 +332,49 @@ def test_register_sum_passes(cyc, na):
                     assert n == no and np.max(np.abs(R - Ro)) / nrm < 1e-5, (cross, b)
 
 
+def test_reset_on_the_register_sum_path(cyc):
+    """A reset of a register-sum stream leaves the zeroing of the sums to its next pass (which
+    writes its totals instead of adding them) or to whatever reads the sums first: after
+    resets, reads, raw sums, save/load and pushes too short to commit a term see exactly the
+    samples pushed since the last reset."""
+    import torch
+    T = 5000
+    x = synth.white(T, seed=118).astype(np.complex64)
+    lags = np.array([0, 2, 5, 11])
+    alphas = np.array([0.0, 0.125, -0.3, 0.41, 0.07])
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+
+    def want(lo, hi):
+        Ro, no = oracle.estimate(x[lo:hi], lags, alphas, n0=0)
+        return Ro, no, oracle.r00(x[lo:hi], 11)
+
+    with cyc.Stream(lags, alphas, BOTH, precision="fp32", max_chunk=1500) as s:
+        s.push(xt[:2 * 2000])
+        R, n = s.read()
+        Ro, no, r0 = want(0, 2000)
+        assert n == no and np.max(np.abs(R - Ro)) / r0 < 1e-5
+        s.reset()                                   # the next pass writes its totals
+        s.push(xt[2 * 2000:2 * 4500])               # two passes (max_chunk 1500)
+        R, n = s.read()
+        Ro, no, r0 = want(2000, 4500)
+        assert n == no and np.max(np.abs(R - Ro)) / r0 < 1e-5
+        s.reset()                                   # read before any pass: zeroed by the read
+        raw, n = s.sums()
+        assert n == 0 and float(raw.abs().max()) == 0.0
+        s.push(xt[2 * 4500:2 * 4505])               # 5 samples: fewer than max(lags) + 1
+        with pytest.raises(cyc.CycError) as e:
+            s.read()
+        assert e.value.code == cyc.CYC_ENODATA
+        s.reset()
+        blob = s.save()                             # save right after a reset: zero sums
+        s.push(xt[:2 * 3000])
+        s.load(blob)
+        s.push(xt[2 * 1000:2 * 2500])
+        R, n = s.read()
+        Ro, no, r0 = want(1000, 2500)
+        assert n == no and np.max(np.abs(R - Ro)) / r0 < 1e-5
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16"])
 def test_tensor_core_unit_kinds(cyc, precision):
     """The tensor-core projection takes a and -a together (one pair of weight rows), 0 and
