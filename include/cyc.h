@@ -55,7 +55,7 @@ extern "C" {
 #define CYC_EAGAIN    (-4)   /* server: stream not admitted (memory budget / slots), retry later */
 #define CYC_ETIMEDOUT (-5)   /* a bounded device wait gave up */
 #define CYC_ENODATA   (-6)   /* N_eff == 0: nothing to read; the output is left untouched */
-#define CYC_ENOTSUP   (-7)   /* valid request that this build does not implement */
+#define CYC_ENOTSUP   (-7)   /* valid request that the library does not implement */
 
 /* ---- forms (bitmask) ---- */
 #define CYC_CONV 1           /* x[n+m] conj(x[n]) */
