@@ -5,7 +5,7 @@ The tensor-core path forms the weights W = exp(-j 2 pi a n) and the lag products
 P = x[n+m] c(x[n]) in FP32, rounds them to 16-bit operands and accumulates in FP32:
 
 * FP16 single pass: W16 = fp16_rn(W), P16 = fp16_rn(P); term W16 * P16.
-* BF16x3 split (the reading of the task's "3-term split BF16"): v = hi + lo with
+* BF16x3 split (the 3-term BF16 split): v = hi + lo with
   hi = bf16_rn(v), lo = bf16_rn(v - hi); term hi_W hi_P + hi_W lo_P + lo_W hi_P (the
   lo_W lo_P product dropped).
 
